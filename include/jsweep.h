@@ -1,0 +1,227 @@
+/*
+ * jsweep.h — C ABI of a GB300 (sm_103a) library for the data-driven S_n
+ * transport sweep of JSweep (arXiv 1803.09876).
+ *
+ * The method (Sec. II-C, Sec. V-A, Listing 1, and the source-iteration
+ * algorithm of the appendix): for every ordinate direction Omega_m the mesh
+ * induces a dependency graph on its cells — a cell may be solved only after
+ * all of its upwind neighbours — and a sweep is a topological traversal of
+ * that graph with a per-cell upwind solve at each vertex; the scalar flux
+ * phi = sum_m w_m psi_m feeds the scattering source of the next source
+ * iteration.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: JSWEEP_OK (0) or a negative
+ *     JSWEEP_ERR_* code.  jsweep_last_error() returns a message describing the
+ *     last failure of the calling thread (thread-local; valid until the next
+ *     call on that thread).
+ *   - Handles (mesh, quadrature, dags, batch) are opaque, owned by the library,
+ *     and released by their *_destroy function.  Destroying NULL is a no-op.
+ *   - Host input arrays are copied during the call; the caller keeps them.
+ *   - "device" arrays are CUDA device pointers on the current device (for
+ *     example torch.Tensor.data_ptr()); the caller allocates and owns them.
+ *     Their element type is double for JSWEEP_F64 and float for JSWEEP_F32.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is queued on it; calls that return host-visible results (counts,
+ *     iteration numbers) synchronise that stream before returning.
+ *   - Sizes and indices are int64 at the ABI; internally cell and face ids are
+ *     int32, so n_cells and n_faces must be below 2^31.
+ *   - Device memory the library needs for itself comes from the allocator set
+ *     with jsweep_set_allocator (cudaMalloc/cudaFree by default).
+ */
+#ifndef JSWEEP_H
+#define JSWEEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define JSWEEP_OK 0
+#define JSWEEP_ERR_INVALID_ARG (-1)    /* bad pointer, size or option */
+#define JSWEEP_ERR_MESH_INVALID (-2)   /* mesh failed validation (message names the id) */
+#define JSWEEP_ERR_OOM (-3)            /* a device or host allocation failed */
+#define JSWEEP_ERR_NOT_CONVERGED (-4)  /* source iteration hit max_iters (outputs filled) */
+#define JSWEEP_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait ran out */
+#define JSWEEP_ERR_CUDA (-6)           /* a CUDA runtime call failed */
+#define JSWEEP_ERR_UNIMPLEMENTED (-7)  /* input outside what this build supports */
+#define JSWEEP_ERR_CYCLE (-8)          /* a dependency cycle could not be broken */
+
+/* ---- precisions ------------------------------------------------------- */
+#define JSWEEP_F64 0 /* psi, phi, sources in double */
+#define JSWEEP_F32 1 /* psi in float, phi in float with compensated sums; FP64 residual */
+
+/* ---- sweep schedules (jsweep_options.sweep_mode) ----------------------- */
+#define JSWEEP_MODE_AUTO 0       /* library picks */
+#define JSWEEP_MODE_LEVEL_SYNC 1 /* one launch per level index, replayed from a CUDA graph */
+#define JSWEEP_MODE_PERSISTENT 2 /* one grid-resident launch driven by dependency counters */
+
+/* ---- work-unit orderings for the persistent schedule (jsweep_options.priority) */
+#define JSWEEP_PRIO_LEVEL 0     /* by level index, all directions together */
+#define JSWEEP_PRIO_DEPTH 1     /* by remaining depth: long directions start first */
+#define JSWEEP_PRIO_OCTANT 2    /* level index staggered by octant */
+
+typedef struct jsweep_mesh_s *jsweep_mesh_t;
+typedef struct jsweep_quad_s *jsweep_quad_t;
+typedef struct jsweep_dags_s *jsweep_dags_t;
+typedef struct jsweep_batch_s *jsweep_batch_t;
+
+/* Options of the dependency-graph build and of the sweeps.  Zero or negative
+ * numeric fields mean "default".  struct_size must be sizeof(jsweep_options). */
+typedef struct {
+    int struct_size;
+    int sweep_mode;        /* JSWEEP_MODE_* */
+    int priority;          /* JSWEEP_PRIO_*, persistent schedule only */
+    int cluster_cells;     /* cells per work unit (vertex clustering grain, Sec. V-C); 1..32, default 32 */
+    int blocks_per_sm;     /* persistent schedule: resident blocks per SM (default: occupancy) */
+    int octant_stagger;    /* JSWEEP_PRIO_OCTANT: levels between octant starts (default: auto) */
+    double spin_timeout_s; /* bounded device waits give up after this long (default 2 s) */
+    int cycle_search_max;  /* cells a local cycle search may visit (default 256, max 1024) */
+    int debug_block_waits; /* test hook, 0 in normal use: when nonzero every dependency wait of the
+                              persistent schedule needs one more finished unit than can exist, so
+                              the waits run out and the call returns JSWEEP_ERR_DEVICE_TIMEOUT */
+    int reserved[7];
+} jsweep_options;
+
+/* Fill *opt with defaults. */
+int jsweep_options_default(jsweep_options *opt);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *jsweep_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int jsweep_version(void);
+
+/* Route the library's own device allocations through the caller's allocator
+ * (for example PyTorch's caching allocator).  alloc returns a device pointer
+ * or NULL; free releases one.  Both are called on the host thread making the
+ * library call; stream is the stream the memory will first be used on.
+ * Passing NULL for both restores cudaMalloc/cudaFree.  Memory obtained before
+ * the switch is released with the allocator that produced it. */
+typedef void *(*jsweep_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*jsweep_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int jsweep_set_allocator(jsweep_alloc_fn alloc, jsweep_free_fn free_fn, void *ctx);
+
+/* ---- mesh ----------------------------------------------------------------
+ * A mesh of n_cells polyhedral cells and n_faces faces (Sec. II-B: the patch
+ * holds cells and their adjacency; here one patch holds the whole mesh).
+ *   face_cells [n_faces][2] (host): cell0, cell1 of each face; cell1 = -1 marks
+ *     a boundary face.  The face id is the row index; it is the tie-break key
+ *     of the cycle rule and the summation order of a cell's faces.
+ *   normals [n_faces][3] (host): unit normal pointing from cell0 into cell1
+ *     (outward from cell0 on a boundary face).
+ *   areas [n_faces], volumes [n_cells] (host): positive.
+ * Validation (JSWEEP_ERR_MESH_INVALID, message names the first offending id):
+ * ids in range, cell0 != cell1, positive areas and volumes, unit normals
+ * (|1-|n|| <= 1e-6), at most 7 faces per cell, at least one face per cell,
+ * and closed cells: |sum_f +-a_f n_f| <= 1e-8 * sum_f a_f.
+ * Boundary faces are numbered 0..n_bfaces-1 in increasing face id; inflow
+ * arrays use that numbering. */
+int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cells,
+                       const double *normals, const double *areas, const double *volumes,
+                       jsweep_mesh_t *out);
+int jsweep_mesh_destroy(jsweep_mesh_t mesh);
+int jsweep_mesh_info(jsweep_mesh_t mesh, int64_t *n_cells, int64_t *n_faces, int64_t *n_bfaces,
+                     int *max_faces_per_cell);
+
+/* ---- quadrature ------------------------------------------------------------
+ * jsweep_quadrature_product (host only) fills the product set "n_polar
+ * Gauss-Legendre polar cosines x n_azim azimuths per octant" (M = 8 n_polar
+ * n_azim directions; weights sum to 4 pi):
+ *   mu_i = the positive nodes, ascending, of the 2 n_polar-point
+ *   Gauss-Legendre rule, weight w_i; phi_j = (j + 1/2)(pi/2)/n_azim, weight
+ *   pi/(2 n_azim); Omega = (s_x sqrt(1-mu^2) cos phi, s_y sqrt(1-mu^2) sin phi,
+ *   s_z mu); index m = octant*n_polar*n_azim + i*n_azim + j with octant bits
+ *   (1, 2, 4) set for negative (x, y, z).
+ *   dirs [M][3], weights [M] (host, caller-allocated).  1 <= n_polar, n_azim <= 64.
+ * jsweep_quadrature_create copies any direction set (host arrays): directions
+ * must be finite and non-zero (they need not be unit vectors: a 1D slab test
+ * uses (mu, 0, 0)); weights finite. */
+int jsweep_quadrature_product(int n_polar, int n_azim, double *dirs, double *weights);
+int jsweep_quadrature_create(int64_t n_dirs, const double *dirs, const double *weights,
+                             jsweep_quad_t *out);
+int jsweep_quadrature_destroy(jsweep_quad_t quad);
+
+/* ---- dependency graphs (Sec. V-A, Listing 1 init; cycle rule) -------------
+ * Builds, on the device, for every direction m:
+ *   - the upwind classification of every cell face from the FP64 sign of
+ *     ((n_x O_x) + (n_y O_y)) + (n_z O_z) (no fused multiply-add);
+ *   - the longest-path level of every cell (0 = no upwind neighbour);
+ *   - cycle breaking: in every strongly connected component of two or more
+ *     cells the active interior face of smallest id inside the component is
+ *     lagged (its upwind value comes from the previous sweep), repeated until
+ *     the graph is acyclic;
+ *   - the level-major order (cells sorted by (level, cell id)) and the
+ *     work-unit schedules of the sweeps.
+ * The result is resident on the device and stays valid while mesh and quad
+ * live (the handle keeps its own references).  Errors: JSWEEP_ERR_CYCLE if a
+ * strongly connected component exceeds opt->cycle_search_max cells. */
+int jsweep_build_dags(jsweep_mesh_t mesh, jsweep_quad_t quad, const jsweep_options *opt,
+                      void *stream, jsweep_dags_t *out);
+int jsweep_dags_destroy(jsweep_dags_t dags);
+/* n_dirs, the largest level count over directions, total lagged (face, dir) pairs. */
+int jsweep_dags_info(jsweep_dags_t dags, int64_t *n_dirs, int64_t *max_levels, int64_t *n_lag_total);
+int jsweep_dags_nlevels(jsweep_dags_t dags, int64_t m, int64_t *nlevels);
+/* level_of_cell [n_cells] (host). */
+int jsweep_dags_levels(jsweep_dags_t dags, int64_t m, int32_t *level_of_cell);
+/* order [n_cells], level_ptr [nlevels+1] (host). */
+int jsweep_dags_order(jsweep_dags_t dags, int64_t m, int32_t *order, int32_t *level_ptr);
+/* Lagged faces of direction m sorted by face id, rows (face, upwind cell,
+ * downwind cell) into rows [*n][3] (host; may be NULL to query *n only). */
+int jsweep_dags_lagged(jsweep_dags_t dags, int64_t m, int64_t *rows, int64_t *n);
+/* Zero the lagged upwind values (the state a source iteration starts from). */
+int jsweep_dags_reset_lag(jsweep_dags_t dags);
+/* Replace the sweep options (mode, priority, grain, ...) of a built handle. */
+int jsweep_dags_set_options(jsweep_dags_t dags, const jsweep_options *opt);
+
+/* ---- one transport sweep (Listing 1 compute/solve; Sec. V-B) -------------
+ * Sweeps all directions for nrhs right-hand sides with the step (upwind
+ * finite-volume) scheme: for cell c and direction m, with mu_f a_f =
+ * (Omega_m . n_f) a_f taken outward from c,
+ *    psi = (S V + sum_{incoming f} |mu_f| a_f psi_up(f)) /
+ *          (sigma_t V + sum_{outgoing f} mu_f a_f),
+ * psi_up being the upwind cell's psi, the lagged value on a lagged face, or
+ * the boundary inflow.  Then phi = sum_m w_m psi_m (FP32: compensated sum in
+ * a fixed order, so results do not depend on the schedule).
+ *   sigma_t [n_cells] (device), ang_source [nrhs][n_cells] (device, angular
+ *   source per steradian), inflow [nrhs][n_bfaces] (device, isotropic boundary
+ *   angular flux) or NULL for vacuum, phi_out [nrhs][n_cells] (device),
+ *   psi_out [nrhs][n_dirs][n_cells] (device) or NULL.
+ * Uses the handle's lagged values and then replaces them by this sweep's.
+ * 1 <= nrhs <= 8.  Device-side waits are bounded (JSWEEP_ERR_DEVICE_TIMEOUT). */
+int jsweep_sweep(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+                 const void *ang_source, const void *inflow, void *phi_out, void *psi_out,
+                 void *stream);
+
+/* ---- source iteration (appendix algorithm "Source iterative Sn solver") ---
+ * phi^0 = 0, lagged values 0; repeat { S = (c sigma_t phi + q) / (4 pi);
+ * sweep; residual r = max_c |phi_new - phi| / max_c |phi_new| per right-hand
+ * side, in FP64 on the device } until r < tol for all right-hand sides.
+ *   sigma_t, c_ratio [n_cells] (device; sigma_s = c_ratio * sigma_t),
+ *   q [nrhs][n_cells] (device, total isotropic source), inflow as in
+ *   jsweep_sweep, phi_out [nrhs][n_cells] (device).
+ *   iters_out, resid_out (host, may be NULL): sweeps done, final residual.
+ * Returns JSWEEP_ERR_NOT_CONVERGED (phi_out filled) after max_iters sweeps. */
+int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+                          const void *c_ratio, const void *q, const void *inflow, double tol,
+                          int max_iters, void *phi_out, int *iters_out, double *resid_out,
+                          void *stream);
+
+/* ---- timing of the last sweep call on a handle (phase breakdown, Sec. VI-C) */
+typedef struct {
+    double build_ms;        /* last jsweep_build_dags: device time of the whole build */
+    double sweep_ms;        /* last sweep kernel(s) only */
+    double phi_ms;          /* last phi reduction */
+    int64_t sweep_launches; /* kernels launched by the last sweep (graph nodes included) */
+    int64_t build_launches; /* kernels launched by the last jsweep_build_dags */
+    int64_t call_launches;  /* kernels launched by the last jsweep_sweep / jsweep_source_iterate */
+} jsweep_timing;
+int jsweep_dags_timing(jsweep_dags_t dags, jsweep_timing *t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JSWEEP_H */

@@ -1,0 +1,178 @@
+// Internal declarations shared by the library's translation units: status
+// handling, the pluggable device allocator, handle layouts.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/jsweep.h"
+
+namespace js {
+
+// ---- status ------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+
+struct Status {
+    int code = JSWEEP_OK;
+    bool ok() const { return code == JSWEEP_OK; }
+};
+
+#define JS_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::js::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                            __FILE__, __LINE__);                                        \
+            return e_ == cudaErrorMemoryAllocation ? JSWEEP_ERR_OOM : JSWEEP_ERR_CUDA;  \
+        }                                                                               \
+    } while (0)
+
+#define JS_TRY(expr)              \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != JSWEEP_OK)     \
+            return rc_;           \
+    } while (0)
+
+// Kernel launches made by this library (reported per call in jsweep_timing).
+extern std::atomic<int64_t> g_kernel_launches;
+inline void note_launches(int64_t n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Check the launch just made and count it.
+#define JS_LAUNCH_CHECK() \
+    do {                  \
+        ::js::note_launches(1); \
+        JS_CUDA(cudaGetLastError()); \
+    } while (0)
+
+// ---- device memory ------------------------------------------------------------
+void *dev_alloc(size_t bytes, cudaStream_t s);   // NULL on failure (error message set)
+void dev_free(void *p, size_t bytes, cudaStream_t s);
+
+// Owning device buffer routed through the library allocator.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    jsweep_free_fn free_fn = nullptr;  // allocator that produced p (nullptr = cudaFree)
+    void *free_ctx = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    int alloc(size_t nbytes, cudaStream_t s);     // frees the old buffer first
+    int ensure(size_t nbytes, cudaStream_t s);    // grow only
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ---- handles ------------------------------------------------------------------
+constexpr int kMaxFaces = 7;  // faces per cell; bit 7 of the incoming mask flags a lagged face
+
+struct Mesh {
+    std::atomic<int> refs{1};
+    int64_t N = 0, F = 0, Fb = 0;
+    int FS = 0;  // face slots per cell = max faces per cell
+    DevBuf sface;    // int32 [N][FS]: (face id << 1) | (cell is cell1), -1 = empty slot
+    DevBuf nbr;      // int32 [N][FS]: neighbour id, -(b+1) for boundary face b, INT32_MIN empty
+    DevBuf normal;   // double [F][3]
+    DevBuf geo32;    // float4 [N][FS]: outward vector area (a n, oriented out of the cell), w = nbr bits
+    DevBuf geo64;    // double4 [N][FS]: outward vector area, w = nbr as double bits
+    DevBuf vol64;    // double [N]
+    DevBuf vol32;    // float [N]
+};
+
+struct Quad {
+    std::atomic<int> refs{1};
+    int64_t M = 0;
+    std::vector<double> dirs, w;  // host copies
+    DevBuf dirs64;  // double [M][3]
+    DevBuf dirs32;  // float4 [M]
+    DevBuf w64;     // double [M]
+    DevBuf w32;     // float [M]
+};
+
+struct UnitTable {
+    int mode = -1, priority = -1, cluster = -1, stagger = -1;
+    DevBuf units;                  // int4 [n_units]: (m, pos0, ncells, wait target)
+    int64_t n_units = 0;
+    std::vector<int64_t> slot_ptr; // level-sync: units of level l are [slot_ptr[l], slot_ptr[l+1])
+};
+
+struct Dags {
+    Mesh *mesh = nullptr;
+    Quad *quad = nullptr;
+    jsweep_options opt{};
+    int64_t N = 0, M = 0, Lmax = 0, T = 0;  // T = lagged (face, dir) pairs
+    std::vector<int64_t> nlevels;  // [M]
+    std::vector<int64_t> lp_off;   // [M+1] offsets of each direction's level_ptr in lp
+    std::vector<int64_t> lag_ptr_h;  // [M+1]
+    DevBuf level;   // int32 [M][N] (cell order)
+    DevBuf order;   // int32 [M][N]
+    DevBuf mask;    // uint8 [M][N] (level order): incoming-face bits, bit 7 = a lagged face
+    DevBuf lp;      // int32 [sum (L_m + 1)]
+    DevBuf lag_ptr; // int32 [M+1]
+    DevBuf lag_m, lag_face, lag_up, lag_dn;  // int32 [T], sorted by (m, face)
+    // lagged upwind values: [T][R] in the precision of the last sweep
+    DevBuf psi_lag;
+    int lag_R = 0, lag_prec = -1;
+    // sweep workspaces
+    DevBuf psi;      // [M][N][R]
+    DevBuf srcv;     // [N][R]: S V
+    DevBuf sigv;     // [N]: sigma_t V
+    DevBuf inflow;   // [R][Fb] copy (stable pointer for graphs)
+    DevBuf phi_a, phi_b;  // [R][N] (SI ping-pong)
+    DevBuf red;      // residual accumulators / flags
+    DevBuf counters; // persistent schedule: ticket, done[M], error
+    DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
+    UnitTable ut;
+    // CUDA graph of the level-synchronous sweep
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_key;
+    cudaStream_t capture_stream = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    jsweep_timing timing{};
+    ~Dags();
+};
+
+void mesh_release(Mesh *m);
+void quad_release(Quad *q);
+
+// dag build (dag_build.cu)
+int build_dags(Dags *d, cudaStream_t s);
+
+// unit schedules and sweeps (sweep.cu)
+int ensure_units(Dags *d, int mode, cudaStream_t s);
+int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source,
+              const void *inflow, void *phi_out, void *psi_out, cudaStream_t s);
+int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio,
+                         const void *q, const void *inflow, double tol, int max_iters,
+                         void *phi_out, int *iters_out, double *resid_out, cudaStream_t s);
+
+// shared device helpers
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len, int key_bits,
+                        const int32_t *vals_in, int32_t *vals_out, uint32_t *keys_out,
+                        cudaStream_t s);
+
+inline int grid_for(int64_t n, int block, int64_t cap = 1 << 20) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+int device_sm_count();
+
+}  // namespace js
+
+// The opaque handles of the C ABI point at these objects.
+inline js::Mesh *impl(jsweep_mesh_t h) { return reinterpret_cast<js::Mesh *>(h); }
+inline js::Quad *impl(jsweep_quad_t h) { return reinterpret_cast<js::Quad *>(h); }
+inline js::Dags *impl(jsweep_dags_t h) { return reinterpret_cast<js::Dags *>(h); }

@@ -1,0 +1,872 @@
+// Per-direction dependency-graph build on the device (Sec. V-A; Listing 1
+// init/input/compute readiness), with cycle breaking and the level-major
+// reorder.
+//
+// Data layout: every per-(direction, cell) array is [M][N] with the cell index
+// fastest, so a direction's cells are contiguous.
+//
+// Steps:
+//   1. classify  (one thread per (m, c)): upwind/downwind role of each face of
+//      c from the FP64 sign of ((n_x O_x) + (n_y O_y)) + (n_z O_z) with
+//      round-to-nearest multiplies and adds (no FMA contraction), so that the
+//      signs are bit-identical to any IEEE evaluation in that order.  Yields
+//      the incoming-face mask, the outgoing active-edge mask and the count of
+//      unfinished upwind cells (Listing 1, init).
+//   2. peel      (frontier per direction): a ready cell gets
+//      level = 1 + max(level of its active upwind cells) and decrements its
+//      downwind cells' counts; a count reaching zero makes that cell ready
+//      (Listing 1, compute/input).  Levels are longest-path levels.
+//   3. resolve   (only for a direction whose frontier ran empty while cells
+//      remain, i.e. the rest is blocked by cycles): from cells that were
+//      touched since the last stall, follow "first unfinished upwind cell"
+//      pointers until they close a loop; that loop lies in a strongly
+//      connected component S.  The set of unfinished cells that reach the loop
+//      backwards is gathered under a size cap; when it closes, S is computed
+//      exactly inside it and the active face of smallest id inside S is
+//      lagged.  Lags found in one step are applied after the step, so every
+//      search sees the same graph.  Any order of lagging components gives the
+//      same final lag set as "lag the smallest face in every component, then
+//      recompute components, until acyclic": the components of the graph after
+//      a lag refine the components before it, and each component's own
+//      recursion depends only on the edges inside it.
+//   4. sort      cells of each direction by (level, cell id) with a stable
+//      LSD radix sort; level_ptr from the sorted keys; the incoming mask is
+//      gathered into level order (bit 7 flags a cell with a lagged face).
+#include <climits>
+
+#include "common.cuh"
+
+namespace js {
+
+namespace {
+
+constexpr int kWarp = 32;
+
+__device__ __forceinline__ double dot_rn(const double *n, const double *o) {
+    double a = __dmul_rn(n[0], o[0]);
+    double b = __dmul_rn(n[1], o[1]);
+    double c = __dmul_rn(n[2], o[2]);
+    return __dadd_rn(__dadd_rn(a, b), c);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+struct BuildCtx {
+    int64_t N, M;
+    int FS;
+    const int32_t *sface, *nbr;
+    const double *normal, *dirs;
+    int32_t *cnt, *lvl, *stamp, *claim;
+    uint8_t *inm, *outm, *lagm;
+    int32_t *front;   // [2][M][N]
+    int32_t *nfront;  // [2][M]
+    int32_t *cand;    // [2][M][N]
+    int32_t *ncand;   // [2][M]
+    int32_t *cidx, *epoch, *nproc;  // [M]
+    int4 *pend;
+    int32_t *npend;
+    int64_t pend_cap;
+    int4 *lagall;
+    int32_t *nlag;
+    int64_t lag_cap;
+    int32_t *status;  // [0] error code, [1] error info, [2] remaining (clamped), [3] step counter
+};
+
+__device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, int64_t cap,
+                                     int32_t *status) {
+    int32_t i = atomicAdd(count, 1);
+    if (i < cap) {
+        list[i] = v;
+    } else {
+        atomicCAS(&status[0], 0, JSWEEP_ERR_OOM);
+    }
+}
+
+__global__ void k_classify(BuildCtx c) {
+    const int64_t total = c.N * c.M;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = idx / c.N;
+        int32_t v = (int32_t)(idx - m * c.N);
+        const double *o = c.dirs + 3 * m;
+        unsigned in = 0, out = 0;
+        int count = 0;
+        bool bin = false;
+        for (int k = 0; k < c.FS; ++k) {
+            int32_t sf = c.sface[(int64_t)v * c.FS + k];
+            if (sf < 0) break;
+            int32_t f = sf >> 1;
+            double d = dot_rn(c.normal + 3 * (int64_t)f, o);
+            double s = (sf & 1) ? -d : d;  // outward from v
+            int32_t nb = c.nbr[(int64_t)v * c.FS + k];
+            if (s < 0.0) {
+                in |= 1u << k;
+                if (nb >= 0) ++count; else bin = true;
+            } else if (s > 0.0 && nb >= 0) {
+                out |= 1u << k;
+            }
+        }
+        c.inm[idx] = (uint8_t)in;
+        c.outm[idx] = (uint8_t)out;
+        c.cnt[idx] = count;
+        if (count == 0) {
+            push(c.front + m * c.N, c.nfront + m, v, c.N, c.status);
+        } else if (bin) {
+            c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
+            push(c.cand + m * c.N, c.ncand + m, v, c.N, c.status);
+        }
+    }
+}
+
+// One frontier step for every direction: blockIdx.y = direction.
+__global__ void k_peel(BuildCtx c, int cur) {
+    const int64_t m = blockIdx.y;
+    const int nxt = cur ^ 1;
+    const int32_t n = c.nfront[cur * c.M + m];
+    const int64_t base = m * c.N;
+    const int32_t *fr = c.front + (int64_t)cur * c.M * c.N + base;
+    int32_t *fn = c.front + (int64_t)nxt * c.M * c.N + base;
+    int32_t *nfn = c.nfront + nxt * c.M + m;
+    const int ci = c.cidx[m];
+    int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
+    int32_t *ncl = c.ncand + ci * c.M + m;
+    const int32_t ep = c.epoch[m];
+    int processed = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int32_t v = fr[i];
+        unsigned inb = c.inm[base + v], lg = c.lagm[base + v];
+        int lev = 0;
+        for (int k = 0; k < c.FS; ++k) {
+            if (((inb & ~lg) >> k) & 1u) {
+                int32_t u = c.nbr[(int64_t)v * c.FS + k];
+                if (u >= 0) lev = max(lev, c.lvl[base + u] + 1);
+            }
+        }
+        c.lvl[base + v] = lev;
+        unsigned ob = c.outm[base + v];
+        for (int k = 0; k < c.FS; ++k) {
+            if ((ob >> k) & 1u) {
+                int32_t w = c.nbr[(int64_t)v * c.FS + k];
+                int32_t old = atomicSub(&c.cnt[base + w], 1);
+                if (old == 1) {
+                    push(fn, nfn, w, c.N, c.status);
+                } else if (atomicExch(&c.stamp[base + w], ep) != ep) {
+                    push(cl, ncl, w, c.N, c.status);
+                }
+            }
+        }
+        ++processed;
+    }
+    // block total of processed cells
+    for (int off = 16; off > 0; off >>= 1) processed += __shfl_down_sync(0xffffffffu, processed, off);
+    if ((threadIdx.x & 31) == 0 && processed) atomicAdd(&c.nproc[m], processed);
+}
+
+// First unfinished active upwind cell of x (slots in increasing face id).
+__device__ __forceinline__ int32_t first_open_pred(const BuildCtx &c, int64_t base, int32_t x) {
+    unsigned act = (unsigned)c.inm[base + x] & ~(unsigned)c.lagm[base + x];
+    for (int k = 0; k < c.FS; ++k) {
+        if ((act >> k) & 1u) {
+            int32_t u = c.nbr[(int64_t)x * c.FS + k];
+            if (u >= 0 && c.lvl[base + u] < 0) return u;
+        }
+    }
+    return -1;
+}
+
+// Index of value v in X[0..size), or -1 (warp-cooperative).
+__device__ __forceinline__ int warp_find(const int32_t *X, int size, int32_t v, int lane) {
+    for (int j0 = 0; j0 < size; j0 += kWarp) {
+        int j = j0 + lane;
+        unsigned hit = __ballot_sync(0xffffffffu, j < size && X[j] == v);
+        if (hit) return j0 + __ffs(hit) - 1;
+    }
+    return -1;
+}
+
+constexpr int kResolveWarps = 8;
+
+// Cycle resolution for stalled directions: blockIdx.x = direction.
+// Dynamic shared memory: per warp, X[B] (int32), Sidx[B] (int32), inS[B] (uint8).
+__global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
+    const int64_t m = blockIdx.x;
+    if (c.nfront[nxt * c.M + m] != 0 || c.nproc[m] >= c.N) return;  // not stalled
+    extern __shared__ int32_t sh[];
+    __shared__ int32_t new_lags;
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    int32_t *X = sh + warp * (2 * B + (B + 3) / 4);
+    int32_t *Sidx = X + B;
+    uint8_t *inS = reinterpret_cast<uint8_t *>(Sidx + B);
+    if (threadIdx.x == 0) new_lags = 0;
+    __syncthreads();
+    const int64_t base = m * c.N;
+    const int ci = c.cidx[m];
+    const int32_t nc = min(c.ncand[ci * c.M + m], (int32_t)c.N);
+    const int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
+    int32_t *cn = c.cand + (int64_t)(ci ^ 1) * c.M * c.N + base;
+    int32_t *ncn = c.ncand + (ci ^ 1) * c.M + m;
+    const int32_t ep = c.epoch[m];
+    int my_lags = 0;
+
+    for (int32_t i = warp; i < nc; i += kResolveWarps) {
+        // ---- walk to a loop of "first unfinished upwind" pointers (lane 0)
+        int32_t seed = -1;
+        if (lane == 0) {
+            int32_t v = cl[i];
+            if (c.lvl[base + v] < 0 && c.cnt[base + v] > 0) {
+                // Brent's cycle detection on x -> first_open_pred(x)
+                int32_t tort = v, hare = first_open_pred(c, base, v);
+                int power = 1, lam = 1, steps = 1;
+                bool ok = hare >= 0;
+                while (ok && tort != hare) {
+                    if (power == lam) {
+                        tort = hare;
+                        power <<= 1;
+                        lam = 0;
+                    }
+                    hare = first_open_pred(c, base, hare);
+                    ++lam;
+                    if (hare < 0 || ++steps > walk_max) ok = false;
+                }
+                if (ok) {
+                    int32_t x = hare, mn = hare;
+                    for (int s = 1; s < lam; ++s) {
+                        x = first_open_pred(c, base, x);
+                        mn = min(mn, x);
+                    }
+                    seed = mn;
+                }
+            }
+        }
+        seed = __shfl_sync(0xffffffffu, seed, 0);
+        if (seed < 0) continue;
+
+        // ---- backward closure of the seed over unfinished cells, capped at B
+        if (lane == 0) X[0] = seed;
+        __syncwarp();
+        int size = 1, head = 0;
+        bool closed = true;
+        while (head < size && closed) {
+            int32_t x = X[head++];
+            int32_t u = -1;
+            if (lane < c.FS) {
+                unsigned act = (unsigned)c.inm[base + x] & ~(unsigned)c.lagm[base + x];
+                if ((act >> lane) & 1u) {
+                    int32_t nb = c.nbr[(int64_t)x * c.FS + lane];
+                    if (nb >= 0 && c.lvl[base + nb] < 0) u = nb;
+                }
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, u >= 0);
+            while (todo) {
+                int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                int32_t uu = __shfl_sync(0xffffffffu, u, src);
+                if (warp_find(X, size, uu, lane) < 0) {
+                    if (size == B) {
+                        closed = false;
+                        break;
+                    }
+                    if (lane == 0) X[size] = uu;
+                    __syncwarp();
+                    ++size;
+                }
+            }
+        }
+        if (!closed) continue;
+
+        // ---- strongly connected component of the seed inside the closure:
+        // every cell of X reaches the seed, so the cells reached from the seed
+        // within X form its component.
+        for (int j = lane; j < size; j += kWarp) inS[j] = 0;
+        __syncwarp();
+        if (lane == 0) {
+            inS[0] = 1;
+            Sidx[0] = 0;
+        }
+        __syncwarp();
+        int ns = 1, h = 0;
+        while (h < ns) {
+            int32_t y = X[Sidx[h++]];
+            int32_t w = -1;
+            if (lane < c.FS && ((c.outm[base + y] >> lane) & 1u)) w = c.nbr[(int64_t)y * c.FS + lane];
+            unsigned todo = __ballot_sync(0xffffffffu, w >= 0);
+            while (todo) {
+                int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                int32_t ww = __shfl_sync(0xffffffffu, w, src);
+                int j = warp_find(X, size, ww, lane);
+                if (j >= 0 && !inS[j]) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        inS[j] = 1;
+                        Sidx[ns] = j;
+                    }
+                    __syncwarp();
+                    ++ns;
+                }
+            }
+        }
+        if (ns < 2) continue;
+
+        // ---- smallest active face inside the component, and its smallest cell
+        int32_t best_f = INT_MAX, best_u = -1, best_v = -1, smin = INT_MAX;
+        for (int t = 0; t < ns; ++t) {
+            int32_t y = X[Sidx[t]];
+            smin = min(smin, y);
+            int32_t w = -1, f = INT_MAX;
+            if (lane < c.FS && ((c.outm[base + y] >> lane) & 1u)) {
+                w = c.nbr[(int64_t)y * c.FS + lane];
+                f = c.sface[(int64_t)y * c.FS + lane] >> 1;
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, w >= 0);
+            while (todo) {
+                int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                int32_t ww = __shfl_sync(0xffffffffu, w, src);
+                int32_t ff = __shfl_sync(0xffffffffu, f, src);
+                int j = warp_find(X, size, ww, lane);
+                if (j >= 0 && inS[j] && ff < best_f) {
+                    best_f = ff;
+                    best_u = y;
+                    best_v = ww;
+                }
+            }
+        }
+        // ---- one warp per component records the lag (claimed by its smallest cell)
+        if (lane == 0 && best_f != INT_MAX) {
+            if (atomicExch(&c.claim[base + smin], ep) != ep) {
+                int32_t k = atomicAdd(c.npend, 1);
+                if (k < c.pend_cap) {
+                    c.pend[k] = make_int4((int)m, best_f, best_u, best_v);
+                    ++my_lags;
+                } else {
+                    atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+                }
+            } else {
+                best_f = INT_MAX;  // someone else owns this component
+            }
+        }
+        best_f = __shfl_sync(0xffffffffu, best_f, 0);
+        if (best_f != INT_MAX) {
+            // members become candidates of the next stall
+            for (int t = lane; t < ns; t += kWarp) {
+                int32_t y = X[Sidx[t]];
+                if (atomicExch(&c.stamp[base + y], ep + 1) != ep + 1) push(cn, ncn, y, c.N, c.status);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && my_lags) atomicAdd(&new_lags, my_lags);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (new_lags == 0) {
+            // stalled and nothing found: a component larger than the search cap
+            if (atomicCAS(&c.status[0], 0, JSWEEP_ERR_CYCLE) == 0) c.status[1] = (int32_t)m;
+        }
+        c.ncand[ci * c.M + m] = 0;
+        c.cidx[m] = ci ^ 1;
+        c.epoch[m] = ep + 1;
+    }
+}
+
+__device__ __forceinline__ int slot_of(const BuildCtx &c, int32_t cell, int32_t f) {
+    for (int k = 0; k < c.FS; ++k)
+        if ((c.sface[(int64_t)cell * c.FS + k] >> 1) == f) return k;
+    return -1;
+}
+
+__global__ void k_commit(BuildCtx c, int nxt) {
+    const int32_t n = min(*c.npend, (int32_t)c.pend_cap);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int4 e = c.pend[i];
+        int64_t m = e.x;
+        int32_t f = e.y, up = e.z, dn = e.w;
+        int64_t base = m * c.N;
+        int kd = slot_of(c, dn, f), ku = slot_of(c, up, f);
+        if (kd < 0 || ku < 0) {
+            atomicCAS(&c.status[0], 0, JSWEEP_ERR_CYCLE);
+            continue;
+        }
+        c.lagm[base + dn] |= (uint8_t)(1u << kd);
+        c.outm[base + up] &= (uint8_t)~(1u << ku);
+        int32_t old = atomicSub(&c.cnt[base + dn], 1);
+        if (old == 1) push(c.front + (int64_t)nxt * c.M * c.N + base, c.nfront + nxt * c.M + m, dn, c.N, c.status);
+        int32_t k = atomicAdd(c.nlag, 1);
+        if (k < c.lag_cap) c.lagall[k] = e; else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+    }
+}
+
+// End of a step: clear the consumed frontier and the pending list; count the
+// cells still to be processed.
+__global__ void k_step_end(BuildCtx c, int cur) {
+    __shared__ unsigned long long rem;
+    if (threadIdx.x == 0) rem = 0;
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) {
+        c.nfront[cur * c.M + m] = 0;
+        mine += (unsigned long long)(c.N - c.nproc[m]);
+    }
+    atomicAdd(&rem, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *c.npend = 0;
+        c.status[2] = (int32_t)min(rem, (unsigned long long)INT_MAX);
+        c.status[3] += 1;
+    }
+}
+
+__global__ void k_level_max(const int32_t *lvl, int64_t N, int64_t M, int32_t *lmax) {
+    int64_t m = blockIdx.y;
+    int best = -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, lvl[m * N + i]);
+    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&lmax[m], best);
+}
+
+// level_ptr of direction m from its sorted keys.
+__global__ void k_level_ptr(const uint32_t *skeys, int64_t N, int64_t M, const int64_t *lp_off,
+                            const int32_t *nlev, int32_t *lp) {
+    int64_t m = blockIdx.y;
+    int32_t *out = lp + lp_off[m];
+    const uint32_t *k = skeys + m * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t prev = i == 0 ? 0xffffffffu : k[i - 1];
+        uint32_t cur = k[i];
+        if (i == 0 || cur != prev) {
+            uint32_t lo = i == 0 ? 0u : prev + 1;
+            for (uint32_t l = lo; l <= cur; ++l) out[l] = (int32_t)i;
+        }
+        if (i == N - 1) out[nlev[m]] = (int32_t)N;
+    }
+}
+
+__global__ void k_mask_level_order(const uint8_t *inm, const uint8_t *lagm, const int32_t *order,
+                                   int64_t N, int64_t M, uint8_t *mask) {
+    const int64_t total = N * M;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = idx / N;
+        int32_t c = order[idx];
+        int64_t src = m * N + c;
+        mask[idx] = (uint8_t)(inm[src] | (lagm[src] ? 0x80u : 0u));
+    }
+}
+
+__global__ void k_lag_keys(const int4 *lagall, int32_t T, uint32_t *kf, uint32_t *km) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        kf[i] = (uint32_t)lagall[i].y;
+        km[i] = (uint32_t)lagall[i].x;
+    }
+}
+
+__global__ void k_gather_u32(const uint32_t *src, const int32_t *perm, int32_t n, uint32_t *dst) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+
+__global__ void k_lag_scatter(const int4 *lagall, const int32_t *perm, int32_t T, int32_t *lm,
+                              int32_t *lf, int32_t *lu, int32_t *ld) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < T; i += gridDim.x * blockDim.x) {
+        int4 e = lagall[perm[i]];
+        lm[i] = e.x;
+        lf[i] = e.y;
+        lu[i] = e.z;
+        ld[i] = e.w;
+    }
+}
+
+__global__ void k_lag_ptr(const int32_t *lm, int32_t T, int64_t M, int32_t *lag_ptr) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= T; i += gridDim.x * blockDim.x) {
+        int32_t prev = i == 0 ? -1 : lm[i - 1];
+        int32_t cur = i == T ? (int32_t)M : lm[i];
+        for (int32_t mm = prev + 1; mm <= cur; ++mm) lag_ptr[mm] = i;
+    }
+}
+
+// ---- exclusive scan of int64 (three-phase, recursive over block sums) ------------
+constexpr int kScanThreads = 1024, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+    __shared__ int64_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    int64_t before = warp ? wsum[warp - 1] : 0;
+    if (total) *total = wsum[(blockDim.x >> 5) - 1];
+    int64_t r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_sums(const int64_t *in, int64_t n, int64_t *sums) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_apply(const int64_t *in, int64_t n, const int64_t *offs, int64_t *out) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int64_t pre = block_exclusive_scan(s, nullptr) + (offs ? offs[blockIdx.x] : 0);
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = pre;
+        pre += v[k];
+    }
+}
+
+// ---- stable LSD radix sort of equal-length segments (8-bit digits) -----------------
+constexpr int kRsTile = 1024;  // elements per tile; one warp per tile
+
+__global__ void k_rs_hist(const uint32_t *keys, int64_t seg_len, int shift, int32_t *hist, int64_t tiles) {
+    __shared__ int32_t h[256];
+    const int64_t s = blockIdx.y, t = blockIdx.x;
+    for (int b = threadIdx.x; b < 256; b += 32) h[b] = 0;
+    __syncwarp();
+    for (int i = 0; i < kRsTile / 32; ++i) {
+        int64_t e = t * kRsTile + i * 32 + threadIdx.x;
+        if (e < seg_len) atomicAdd(&h[(keys[s * seg_len + e] >> shift) & 255u], 1);
+    }
+    __syncwarp();
+    for (int b = threadIdx.x; b < 256; b += 32) hist[(s * 256 + b) * tiles + t] = h[b];
+}
+
+// In-place exclusive scan of each segment's [256][tiles] histogram (one block per segment).
+__global__ void k_rs_scan(int32_t *hist, int64_t len) {
+    int32_t *h = hist + blockIdx.x * len;
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < len; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < len ? h[i] : 0;
+        int64_t tot;
+        int64_t ex = block_exclusive_scan(v, &tot);
+        if (i < len) h[i] = (int32_t)(carry + ex);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_rs_scatter(const uint32_t *keys, const int32_t *vals, int64_t seg_len, int shift,
+                             const int32_t *hist, int64_t tiles, uint32_t *keys_out,
+                             int32_t *vals_out) {
+    __shared__ int32_t run[256];
+    const int64_t s = blockIdx.y, t = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int b = lane; b < 256; b += 32) run[b] = hist[(s * 256 + b) * tiles + t];
+    __syncwarp();
+    for (int i = 0; i < kRsTile / 32; ++i) {
+        int64_t e = t * kRsTile + i * 32 + lane;
+        bool valid = e < seg_len;
+        uint32_t key = valid ? keys[s * seg_len + e] : 0u;
+        int32_t val = valid ? (vals ? vals[s * seg_len + e] : (int32_t)e) : 0;
+        unsigned d = valid ? ((key >> shift) & 255u) : (256u + lane);
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lanemask_lt());
+        int pos = valid ? run[d] + rank : 0;
+        __syncwarp();
+        if (valid && rank == 0) run[d] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            keys_out[s * seg_len + pos] = key;
+            vals_out[s * seg_len + pos] = val;
+        }
+    }
+}
+
+}  // namespace
+
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return JSWEEP_OK;
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 1) {
+        k_scan_apply<<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+        JS_LAUNCH_CHECK();
+        return JSWEEP_OK;
+    }
+    DevBuf sums, offs;
+    JS_TRY(sums.alloc(nb * 8, s));
+    JS_TRY(offs.alloc(nb * 8, s));
+    k_scan_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(scan_exclusive_i64(sums.as<int64_t>(), offs.as<int64_t>(), nb, s));
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, offs.as<int64_t>(), out);
+    JS_LAUNCH_CHECK();
+    JS_CUDA(cudaStreamSynchronize(s));  // sums/offs are released on return
+    return JSWEEP_OK;
+}
+
+int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len, int key_bits,
+                        const int32_t *vals_in, int32_t *vals_out, uint32_t *keys_out,
+                        cudaStream_t s) {
+    if (n_seg <= 0 || seg_len <= 0) return JSWEEP_OK;
+    const int64_t tiles = (seg_len + kRsTile - 1) / kRsTile;
+    int passes = key_bits <= 0 ? 1 : (key_bits + 7) / 8;
+    DevBuf hist, kb[2], vb[2];
+    JS_TRY(hist.alloc((size_t)n_seg * 256 * tiles * 4, s));
+    size_t ne = (size_t)n_seg * seg_len;
+    JS_TRY(kb[0].alloc(ne * 4, s));
+    JS_TRY(kb[1].alloc(ne * 4, s));
+    JS_TRY(vb[0].alloc(ne * 4, s));
+    JS_TRY(vb[1].alloc(ne * 4, s));
+    const uint32_t *kin = keys_in;
+    const int32_t *vin = vals_in;
+    dim3 grid((unsigned)tiles, (unsigned)n_seg);
+    for (int p = 0; p < passes; ++p) {
+        uint32_t *ko = kb[p & 1].as<uint32_t>();
+        int32_t *vo = vb[p & 1].as<int32_t>();
+        k_rs_hist<<<grid, 32, 0, s>>>(kin, seg_len, 8 * p, hist.as<int32_t>(), tiles);
+        JS_LAUNCH_CHECK();
+        k_rs_scan<<<(unsigned)n_seg, 1024, 0, s>>>(hist.as<int32_t>(), 256 * tiles);
+        JS_LAUNCH_CHECK();
+        k_rs_scatter<<<grid, 32, 0, s>>>(kin, vin, seg_len, 8 * p, hist.as<int32_t>(), tiles, ko, vo);
+        JS_LAUNCH_CHECK();
+        kin = ko;
+        vin = vo;
+    }
+    JS_CUDA(cudaMemcpyAsync(vals_out, vin, ne * 4, cudaMemcpyDeviceToDevice, s));
+    if (keys_out) JS_CUDA(cudaMemcpyAsync(keys_out, kin, ne * 4, cudaMemcpyDeviceToDevice, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    return JSWEEP_OK;
+}
+
+int build_dags(Dags *d, cudaStream_t s) {
+    Mesh *mesh = d->mesh;
+    Quad *quad = d->quad;
+    const int64_t N = d->N, M = d->M, MN = N * M;
+    if (!d->ev[0])
+        for (auto &e : d->ev) JS_CUDA(cudaEventCreate(&e));
+    JS_CUDA(cudaEventRecord(d->ev[0], s));
+
+    // ---- scratch
+    DevBuf cnt, stamp, claim, inm, outm, lagm, front, cand, small, pend, lagall;
+    JS_TRY(d->level.alloc(MN * 4, s));
+    JS_TRY(cnt.alloc(MN * 4, s));
+    JS_TRY(stamp.alloc(MN * 4, s));
+    JS_TRY(claim.alloc(MN * 4, s));
+    JS_TRY(inm.alloc(MN, s));
+    JS_TRY(outm.alloc(MN, s));
+    JS_TRY(lagm.alloc(MN, s));
+    JS_TRY(front.alloc(2 * MN * 4, s));
+    JS_TRY(cand.alloc(2 * MN * 4, s));
+    // small: nfront[2M] ncand[2M] cidx[M] epoch[M] nproc[M] npend nlag status[4]
+    const int64_t n_small = 7 * M + 16;
+    JS_TRY(small.alloc(n_small * 4, s));
+    const int64_t pend_cap = std::max<int64_t>(1 << 16, std::min<int64_t>(MN, 1 << 22));
+    const int64_t lag_cap = std::max<int64_t>(1 << 16, std::min<int64_t>(MN, std::max<int64_t>(1 << 20, MN / 64)));
+    JS_TRY(pend.alloc(pend_cap * 16, s));
+    JS_TRY(lagall.alloc(lag_cap * 16, s));
+
+    BuildCtx c;
+    c.N = N;
+    c.M = M;
+    c.FS = mesh->FS;
+    c.sface = mesh->sface.as<int32_t>();
+    c.nbr = mesh->nbr.as<int32_t>();
+    c.normal = mesh->normal.as<double>();
+    c.dirs = quad->dirs64.as<double>();
+    c.cnt = cnt.as<int32_t>();
+    c.lvl = d->level.as<int32_t>();
+    c.stamp = stamp.as<int32_t>();
+    c.claim = claim.as<int32_t>();
+    c.inm = inm.as<uint8_t>();
+    c.outm = outm.as<uint8_t>();
+    c.lagm = lagm.as<uint8_t>();
+    c.front = front.as<int32_t>();
+    c.cand = cand.as<int32_t>();
+    int32_t *sm = small.as<int32_t>();
+    c.nfront = sm;
+    c.ncand = sm + 2 * M;
+    c.cidx = sm + 4 * M;
+    c.epoch = sm + 5 * M;
+    c.nproc = sm + 6 * M;
+    c.npend = sm + 7 * M;
+    c.nlag = sm + 7 * M + 1;
+    c.status = sm + 7 * M + 4;
+    c.pend = pend.as<int4>();
+    c.pend_cap = pend_cap;
+    c.lagall = lagall.as<int4>();
+    c.lag_cap = lag_cap;
+
+    JS_CUDA(cudaMemsetAsync(c.lvl, 0xff, MN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.stamp, 0, MN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.claim, 0, MN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.lagm, 0, MN, s));
+    JS_CUDA(cudaMemsetAsync(sm, 0, n_small * 4, s));
+    {
+        std::vector<int32_t> ones(M, 1);
+        JS_CUDA(cudaMemcpyAsync(c.epoch, ones.data(), M * 4, cudaMemcpyHostToDevice, s));
+        JS_CUDA(cudaStreamSynchronize(s));
+    }
+    k_classify<<<grid_for(MN, 256, 152 * 64), 256, 0, s>>>(c);
+    JS_LAUNCH_CHECK();
+
+    // ---- frontier loop with stall resolution
+    const int B = d->opt.cycle_search_max;
+    const int walk_max = 4 * B + 64;
+    const size_t shmem = (size_t)kResolveWarps * (2 * B + (B + 3) / 4) * 4;
+    if (shmem > 48 * 1024)
+        JS_CUDA(cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (256 * 32)), 16);
+    const int64_t max_steps = 4 * N + 1024;
+    int32_t status[4] = {0, 0, 1, 0};
+    int64_t step = 0;
+    const int check_every = 8;
+    int32_t last_remaining = -1;
+    int no_progress_checks = 0;
+    while (true) {
+        int cur = (int)(step & 1);
+        k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
+        k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B, walk_max);
+        k_commit<<<64, 256, 0, s>>>(c, cur ^ 1);
+        k_step_end<<<1, 256, 0, s>>>(c, cur);
+        note_launches(3);  // peel, resolve, commit; the check below counts step_end
+        JS_LAUNCH_CHECK();
+        ++step;
+        if (step % check_every == 0) {
+            JS_CUDA(cudaMemcpyAsync(status, c.status, 16, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaStreamSynchronize(s));
+            if (status[0] != 0) {
+                if (status[0] == JSWEEP_ERR_CYCLE)
+                    set_error("dependency cycle in direction %d could not be broken within the search "
+                              "cap of %d cells (raise jsweep_options.cycle_search_max)", status[1], B);
+                else
+                    set_error("dag build: internal list capacity exceeded (status %d)", status[0]);
+                return status[0];
+            }
+            if (status[2] == 0) break;
+            // every step either processes cells or lags faces whose cells are
+            // processed in the next one; a long run without progress is a bug
+            no_progress_checks = status[2] == last_remaining ? no_progress_checks + 1 : 0;
+            last_remaining = status[2];
+            if (no_progress_checks > 16 || step > max_steps) {
+                set_error("dag build did not finish after %lld steps", (long long)step);
+                return JSWEEP_ERR_CYCLE;
+            }
+        }
+    }
+
+    // ---- levels per direction
+    DevBuf lmax;
+    JS_TRY(lmax.alloc(M * 4, s));
+    JS_CUDA(cudaMemsetAsync(lmax.p, 0xff, M * 4, s));
+    k_level_max<<<dim3(std::min<int64_t>(64, (N + 255) / 256), (unsigned)M), 256, 0, s>>>(c.lvl, N, M, lmax.as<int32_t>());
+    JS_LAUNCH_CHECK();
+    std::vector<int32_t> lm(M);
+    JS_CUDA(cudaMemcpyAsync(lm.data(), lmax.p, M * 4, cudaMemcpyDeviceToHost, s));
+    int32_t nlag_total = 0;
+    JS_CUDA(cudaMemcpyAsync(&nlag_total, c.nlag, 4, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    d->nlevels.resize(M);
+    d->lp_off.resize(M + 1);
+    d->lp_off[0] = 0;
+    d->Lmax = 0;
+    for (int64_t m = 0; m < M; ++m) {
+        d->nlevels[m] = (int64_t)lm[m] + 1;
+        d->Lmax = std::max(d->Lmax, d->nlevels[m]);
+        d->lp_off[m + 1] = d->lp_off[m] + d->nlevels[m] + 1;
+    }
+    if (d->Lmax >= (1ll << 24)) {
+        set_error("too many levels (%lld)", (long long)d->Lmax);
+        return JSWEEP_ERR_UNIMPLEMENTED;
+    }
+
+    // ---- level-major order (stable by cell id) and level_ptr
+    int key_bits = 1;
+    while ((1ll << key_bits) < d->Lmax) ++key_bits;
+    DevBuf skeys;
+    JS_TRY(d->order.alloc(MN * 4, s));
+    JS_TRY(skeys.alloc(MN * 4, s));
+    JS_TRY(radix_sort_segments(reinterpret_cast<const uint32_t *>(c.lvl), M, N, key_bits, nullptr,
+                               d->order.as<int32_t>(), skeys.as<uint32_t>(), s));
+    DevBuf lpoff_d, nlev_d;
+    JS_TRY(d->lp.alloc(d->lp_off[M] * 4, s));
+    JS_TRY(lpoff_d.alloc((M + 1) * 8, s));
+    JS_TRY(nlev_d.alloc(M * 4, s));
+    std::vector<int32_t> nl32(M);
+    for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)d->nlevels[m];
+    JS_CUDA(cudaMemcpyAsync(lpoff_d.p, d->lp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(nlev_d.p, nl32.data(), M * 4, cudaMemcpyHostToDevice, s));
+    k_level_ptr<<<dim3(std::min<int64_t>(64, (N + 255) / 256), (unsigned)M), 256, 0, s>>>(
+        skeys.as<uint32_t>(), N, M, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), d->lp.as<int32_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(d->mask.alloc(MN, s));
+    k_mask_level_order<<<grid_for(MN, 256, 152 * 64), 256, 0, s>>>(c.inm, c.lagm, d->order.as<int32_t>(), N, M,
+                                                                    d->mask.as<uint8_t>());
+    JS_LAUNCH_CHECK();
+
+    // ---- lag list sorted by (direction, face id)
+    const int32_t T = std::min<int32_t>(nlag_total, (int32_t)lag_cap);
+    d->T = T;
+    JS_TRY(d->lag_ptr.alloc((M + 1) * 4, s));
+    JS_TRY(d->lag_m.alloc(std::max<int64_t>(T, 1) * 4, s));
+    JS_TRY(d->lag_face.alloc(std::max<int64_t>(T, 1) * 4, s));
+    JS_TRY(d->lag_up.alloc(std::max<int64_t>(T, 1) * 4, s));
+    JS_TRY(d->lag_dn.alloc(std::max<int64_t>(T, 1) * 4, s));
+    if (T > 0) {
+        DevBuf kf, km, km2, p1, p2;
+        JS_TRY(kf.alloc(T * 4, s));
+        JS_TRY(km.alloc(T * 4, s));
+        JS_TRY(km2.alloc(T * 4, s));
+        JS_TRY(p1.alloc(T * 4, s));
+        JS_TRY(p2.alloc(T * 4, s));
+        k_lag_keys<<<grid_for(T, 256), 256, 0, s>>>(c.lagall, T, kf.as<uint32_t>(), km.as<uint32_t>());
+        JS_LAUNCH_CHECK();
+        JS_TRY(radix_sort_segments(kf.as<uint32_t>(), 1, T, 31, nullptr, p1.as<int32_t>(), nullptr, s));
+        k_gather_u32<<<grid_for(T, 256), 256, 0, s>>>(km.as<uint32_t>(), p1.as<int32_t>(), T, km2.as<uint32_t>());
+        JS_LAUNCH_CHECK();
+        int mbits = 1;
+        while ((1ll << mbits) < M) ++mbits;
+        JS_TRY(radix_sort_segments(km2.as<uint32_t>(), 1, T, mbits, p1.as<int32_t>(), p2.as<int32_t>(), nullptr, s));
+        k_lag_scatter<<<grid_for(T, 256), 256, 0, s>>>(c.lagall, p2.as<int32_t>(), T, d->lag_m.as<int32_t>(),
+                                                      d->lag_face.as<int32_t>(), d->lag_up.as<int32_t>(),
+                                                      d->lag_dn.as<int32_t>());
+        JS_LAUNCH_CHECK();
+    }
+    k_lag_ptr<<<grid_for(T + 1, 256), 256, 0, s>>>(d->lag_m.as<int32_t>(), T, M, d->lag_ptr.as<int32_t>());
+    JS_LAUNCH_CHECK();
+    std::vector<int32_t> lp32(M + 1);
+    JS_CUDA(cudaMemcpyAsync(lp32.data(), d->lag_ptr.p, (M + 1) * 4, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaEventRecord(d->ev[1], s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    d->lag_ptr_h.assign(lp32.begin(), lp32.end());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]);
+    d->timing.build_ms = ms;
+    d->psi_lag.release();
+    d->lag_R = 0;
+    d->lag_prec = -1;
+    return JSWEEP_OK;
+}
+
+}  // namespace js

@@ -1,0 +1,810 @@
+// Sweeps and source iteration on the device.
+//
+// Work unit: up to `cluster_cells` (<= 32) consecutive cells of one level of
+// one direction in the level-major order (vertex clustering, Sec. V-C); one
+// warp processes a unit, one lane per cell.  Cells of one level never depend
+// on each other, so a unit needs no internal ordering.
+//
+// Two schedules (Sec. V-B patch-angle parallelism: all directions progress
+// together):
+//   level-synchronous: one launch per level index covering that level of all
+//     directions; the launches are captured once into a CUDA graph and
+//     replayed.
+//   persistent: one launch of resident warps that take units from a global
+//     ticket counter in a precomputed priority order (a topological order of
+//     the units); a unit waits until its direction has completed every unit
+//     of the levels before its own (per-direction done counter; acquire/
+//     release ordering), with a bounded spin that reports
+//     JSWEEP_ERR_DEVICE_TIMEOUT instead of hanging.  Tickets are dispensed in
+//     order and a warp finishes its unit before taking the next, so the
+//     oldest unfinished unit never waits on anything: no deadlock, whatever
+//     the number of resident warps.
+//
+// Per-cell solve (step scheme):  psi = (S V + sum_in |Omega.A_f| psi_up) /
+// (sigma_t V + sum_out Omega.A_f), with A_f the outward vector area; the
+// incoming faces are the ones the FP64 classification marked (never a
+// recomputed low-precision sign), so a grazing face cannot read an upwind
+// value that is not written yet.
+//
+// Layouts: psi [M][N][R] (the R right-hand sides of one cell-direction are
+// contiguous: one 32-byte sector for R = 8 in FP32), sources [N][R]
+// premultiplied by the cell volume, lagged values [T][R].
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace js {
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+template <class T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+template <class T> struct SweepArgs {
+    int64_t N;
+    int M, FS, Fb;
+    const int32_t *order;
+    const uint8_t *mask;
+    const typename V4<T>::type *geo;
+    const T *dirs;  // [M][4] (x, y, z, 0)
+    const T *srcv;  // [N][R]
+    const T *sigv;  // [N]
+    const T *inflow;  // [R][Fb] or null
+    T *psi;           // [M][N][R]
+    const T *psi_lag; // [Tl][R]
+    const int32_t *lag_ptr, *lag_face, *sface;
+    const int4 *units;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+template <class T> __device__ __forceinline__ int nbr_bits(const typename V4<T>::type &g);
+template <> __device__ __forceinline__ int nbr_bits<float>(const float4 &g) { return __float_as_int(g.w); }
+template <> __device__ __forceinline__ int nbr_bits<double>(const double4 &g) {
+    return (int)__double_as_longlong(g.w);
+}
+
+// R contiguous values through L2 (bypassing L1: values written by other SMs
+// during a persistent sweep must not be served from a stale L1 line).
+template <class T, int R> __device__ __forceinline__ void load_cg(const T *p, T (&v)[R]) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+            memcpy(reinterpret_cast<char *>(v) + 16 * i, &x, 16);
+        }
+    } else if constexpr (sizeof(T) * R == 8) {
+        float2 x = __ldcg(reinterpret_cast<const float2 *>(p));
+        memcpy(v, &x, 8);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldcg(p + r);
+    }
+}
+
+template <class T, int R> __device__ __forceinline__ void load_ro(const T *p, T (&v)[R]) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            memcpy(reinterpret_cast<char *>(v) + 16 * i, &x, 16);
+        }
+    } else if constexpr (sizeof(T) * R == 8) {
+        float2 x = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(v, &x, 8);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldg(p + r);
+    }
+}
+
+template <class T, int R> __device__ __forceinline__ void store_cg(T *p, const T (&v)[R]) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x;
+            memcpy(&x, reinterpret_cast<const char *>(v) + 16 * i, 16);
+            __stcg(reinterpret_cast<float4 *>(p) + i, x);
+        }
+    } else if constexpr (sizeof(T) * R == 8) {
+        float2 x;
+        memcpy(&x, v, 8);
+        __stcg(reinterpret_cast<float2 *>(p), x);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcg(p + r, v[r]);
+    }
+}
+
+// Index of the lagged face f of direction m in the lag list, or -1.
+__device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *lag_face, int m, int32_t f) {
+    int lo = lag_ptr[m], hi = lag_ptr[m + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (lag_face[mid] < f) lo = mid + 1; else hi = mid;
+    }
+    return (lo < lag_ptr[m + 1] && lag_face[lo] == f) ? lo : -1;
+}
+
+template <class T, int R>
+__device__ __forceinline__ void solve_cell(const SweepArgs<T> &a, int m, int64_t pos) {
+    const int64_t idx = (int64_t)m * a.N + pos;
+    const int c = a.order[idx];
+    const unsigned msk = a.mask[idx];
+    const T ox = a.dirs[4 * m], oy = a.dirs[4 * m + 1], oz = a.dirs[4 * m + 2];
+    T num[R];
+    load_ro<T, R>(a.srcv + (int64_t)c * R, num);
+    T den = a.sigv[c];
+    const typename V4<T>::type *g = a.geo + (int64_t)c * a.FS;
+#pragma unroll 1
+    for (int k = 0; k < a.FS; ++k) {
+        typename V4<T>::type gk = g[k];
+        T d = ox * gk.x + oy * gk.y + oz * gk.z;
+        if ((msk >> k) & 1u) {
+            T wf = fabs(d);
+            int nb = nbr_bits<T>(gk);
+            T up[R];
+            if (nb >= 0) {
+                int j = -1;
+                if (msk & 0x80u) j = lag_index(a.lag_ptr, a.lag_face, m, a.sface[(int64_t)c * a.FS + k] >> 1);
+                if (j >= 0) {
+                    load_ro<T, R>(a.psi_lag + (int64_t)j * R, up);
+                } else {
+                    load_cg<T, R>(a.psi + ((int64_t)m * a.N + nb) * R, up);
+                }
+            } else {
+                int b = -nb - 1;
+#pragma unroll
+                for (int r = 0; r < R; ++r) up[r] = a.inflow ? a.inflow[(int64_t)r * a.Fb + b] : T(0);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) num[r] = num[r] + wf * up[r];
+        } else {
+            den += d > T(0) ? d : T(0);
+        }
+    }
+    T out[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = num[r] / den;
+    store_cg<T, R>(a.psi + ((int64_t)m * a.N + c) * R, out);
+}
+
+template <class T, int R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T> a, int64_t u0, int64_t nu) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (t >= nu) return;
+    const int4 u = a.units[u0 + t];
+    if (lane < u.z) solve_cell<T, R>(a, u.x, (int64_t)u.y + lane);
+}
+
+template <class T, int R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sweep_persistent(SweepArgs<T> a, int64_t n_units, unsigned long long *ticket, int *done, int *err,
+                       long long timeout_cycles, int extra_wait) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned long long)n_units) break;
+        const int4 u = a.units[t];
+        int bad = 0;
+        if (lane == 0) {
+            const int *cnt = done + u.x;
+            const int target = u.w + (u.w > 0 ? extra_wait : 0);
+            if (ld_acquire(cnt) < target) {
+                const long long t0 = clock64();
+                while (ld_acquire(cnt) < target) {
+                    if (ld_volatile(err) != 0) { bad = 1; break; }
+                    if (clock64() - t0 > timeout_cycles) {
+                        atomicCAS(err, 0, 1);
+                        bad = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+        }
+        bad = __shfl_sync(0xffffffffu, bad, 0);
+        if (bad) break;
+        if (lane < u.z) solve_cell<T, R>(a, u.x, (int64_t)u.y + lane);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(done + u.x, 1);
+    }
+}
+
+// ---- unit schedule ------------------------------------------------------------------
+__global__ void k_unit_counts(const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, int64_t M,
+                              int64_t Lmax, int U, int64_t *ucnt) {
+    const int64_t total = M * Lmax;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = i / Lmax, l = i - m * Lmax;
+        int64_t n = 0;
+        if (l < nlev[m]) n = lp[lp_off[m] + l + 1] - lp[lp_off[m] + l];
+        ucnt[i] = (n + U - 1) / U;
+    }
+}
+
+__global__ void k_unit_slots(const int64_t *ucnt, const int32_t *off, int64_t M, int64_t Lmax, int64_t Tmax,
+                             int64_t *cnt2) {
+    const int64_t total = M * Lmax;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = i / Lmax, l = i - m * Lmax;
+        int64_t t = l + off[m];
+        if (t < Tmax) cnt2[t * M + m] = ucnt[i];
+    }
+}
+
+__global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, const int64_t *ucnt,
+                            const int64_t *wscan, const int64_t *base2, const int32_t *off, int64_t M,
+                            int64_t Lmax, int U, int4 *units) {
+    const int64_t total = M * Lmax;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = i / Lmax, l = i - m * Lmax;
+        if (l >= nlev[m]) continue;
+        int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
+        int64_t nu = ucnt[i];
+        int64_t b = base2[(l + off[m]) * M + m];
+        int32_t wait = (int32_t)(wscan[i] - wscan[m * Lmax]);
+        for (int64_t j = 0; j < nu; ++j) {
+            int32_t s = p0 + (int32_t)(j * U);
+            units[b + j] = make_int4((int)m, s, min(U, p1 - s), wait);
+        }
+    }
+}
+
+// ---- emission, phi, residual, lag update ----------------------------------------------
+template <class T, int R>
+__global__ void k_emission(const T *sig, const T *cr, const T *q, const T *phi, const T *vol, int64_t N,
+                           int nrhs, T *srcv, T *sigv) {
+    const T four_pi = T(4.0 * 3.141592653589793);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        T V = vol[c], s = sig[c];
+        sigv[c] = s * V;
+        T cs = cr ? cr[c] * s : T(0);
+        T out[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T val = T(0);
+            if (r < nrhs) {
+                T p = phi ? phi[(int64_t)r * N + c] : T(0);
+                val = ((cs * p + q[(int64_t)r * N + c]) / four_pi) * V;
+            }
+            out[r] = val;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) srcv[c * R + r] = out[r];
+    }
+}
+
+// Angular source given directly: srcv = S V.
+template <class T, int R>
+__global__ void k_source_prep(const T *sig, const T *src, const T *vol, int64_t N, int nrhs, T *srcv, T *sigv) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        T V = vol[c];
+        sigv[c] = sig[c] * V;
+#pragma unroll
+        for (int r = 0; r < R; ++r) srcv[c * R + r] = r < nrhs ? src[(int64_t)r * N + c] * V : T(0);
+    }
+}
+
+// phi[r][c] = sum_m w_m psi[m][c][r], in direction order; FP32 with Kahan compensation.
+template <class T, int R>
+__global__ void k_phi(const T *psi, const T *w, int64_t N, int M, int nrhs, T *phi) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        T s[R], comp[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[r] = comp[r] = T(0);
+        for (int m = 0; m < M; ++m) {
+            T x[R];
+            load_cg<T, R>(psi + ((int64_t)m * N + c) * R, x);
+            const T wm = w[m];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if constexpr (sizeof(T) == 4) {
+                    T y = wm * x[r] - comp[r];
+                    T t = s[r] + y;
+                    comp[r] = (t - s[r]) - y;
+                    s[r] = t;
+                } else {
+                    s[r] = s[r] + wm * x[r];
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r < nrhs) phi[(int64_t)r * N + c] = s[r];
+    }
+}
+
+template <class T, int R>
+__global__ void k_lag_update(const T *psi, const int32_t *lag_m, const int32_t *lag_up, int64_t Tl, int64_t N,
+                             T *psi_lag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Tl; j += (int64_t)gridDim.x * blockDim.x) {
+        T v[R];
+        load_cg<T, R>(psi + ((int64_t)lag_m[j] * N + lag_up[j]) * R, v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) psi_lag[j * R + r] = v[r];
+    }
+}
+
+// FP64 residual accumulators: acc[2r] = max |phi_new - phi_old|, acc[2r+1] = max |phi_new|
+// (non-negative doubles compare like their bit patterns).
+template <class T>
+__global__ void k_resid(const T *pn, const T *po, int64_t N, unsigned long long *acc) {
+    const int r = blockIdx.y;
+    double dmax = 0.0, pmax = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        double a = (double)pn[(int64_t)r * N + c];
+        double b = po ? (double)po[(int64_t)r * N + c] : 0.0;
+        dmax = fmax(dmax, fabs(a - b));
+        pmax = fmax(pmax, fabs(a));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, off));
+        pmax = fmax(pmax, __shfl_down_sync(0xffffffffu, pmax, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(acc + 2 * r, (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(acc + 2 * r + 1, (unsigned long long)__double_as_longlong(pmax));
+    }
+}
+
+__global__ void k_resid_final(const unsigned long long *acc, int nrhs, double *resid) {
+    if (threadIdx.x != 0) return;
+    double worst = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+        double d = __longlong_as_double((long long)acc[2 * r]);
+        double p = __longlong_as_double((long long)acc[2 * r + 1]);
+        double v = p > 0.0 ? d / p : (d > 0.0 ? INFINITY : 0.0);
+        resid[r] = v;
+        worst = fmax(worst, v);
+    }
+    resid[nrhs] = worst;
+}
+
+template <class T, int R>
+__global__ void k_psi_out(const T *psi, int64_t N, int M, int nrhs, T *out) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        T v[R];
+        load_cg<T, R>(psi + i * R, v);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r < nrhs) out[(int64_t)r * total + i] = v[r];
+    }
+}
+
+int pad_rhs(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8; }
+
+}  // namespace
+
+// ---- unit tables ------------------------------------------------------------------------
+int ensure_units(Dags *d, int mode, cudaStream_t s) {
+    const int U = d->opt.cluster_cells;
+    const int prio = mode == JSWEEP_MODE_LEVEL_SYNC ? JSWEEP_PRIO_LEVEL : d->opt.priority;
+    int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Lmax / 4);
+    if (prio != JSWEEP_PRIO_OCTANT) stagger = 0;
+    UnitTable &ut = d->ut;
+    if (ut.mode == mode && ut.priority == prio && ut.cluster == U && ut.stagger == stagger) return JSWEEP_OK;
+    const int64_t M = d->M, Lmax = d->Lmax;
+    std::vector<int32_t> off(M, 0);
+    for (int64_t m = 0; m < M; ++m) {
+        if (prio == JSWEEP_PRIO_DEPTH) off[m] = (int32_t)(Lmax - d->nlevels[m]);
+        else if (prio == JSWEEP_PRIO_OCTANT) off[m] = (M % 8 == 0) ? (int32_t)((m / (M / 8)) * stagger) : 0;
+    }
+    int64_t Tmax = 0;
+    for (int64_t m = 0; m < M; ++m) Tmax = std::max<int64_t>(Tmax, d->nlevels[m] + off[m]);
+    DevBuf ucnt, wscan, cnt2, base2, off_d, lpoff_d, nlev_d;
+    JS_TRY(ucnt.alloc(M * Lmax * 8, s));
+    JS_TRY(wscan.alloc(M * Lmax * 8, s));
+    JS_TRY(cnt2.alloc(Tmax * M * 8, s));
+    JS_TRY(base2.alloc((Tmax * M + 1) * 8, s));
+    JS_TRY(off_d.alloc(M * 4, s));
+    JS_TRY(lpoff_d.alloc((M + 1) * 8, s));
+    JS_TRY(nlev_d.alloc(M * 4, s));
+    std::vector<int32_t> nl32(M);
+    for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)d->nlevels[m];
+    JS_CUDA(cudaMemcpyAsync(off_d.p, off.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(lpoff_d.p, d->lp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(nlev_d.p, nl32.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemsetAsync(cnt2.p, 0, Tmax * M * 8, s));
+    k_unit_counts<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->lp.as<int32_t>(), lpoff_d.as<int64_t>(),
+                                                                nlev_d.as<int32_t>(), M, Lmax, U, ucnt.as<int64_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(scan_exclusive_i64(ucnt.as<int64_t>(), wscan.as<int64_t>(), M * Lmax, s));
+    k_unit_slots<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(ucnt.as<int64_t>(), off_d.as<int32_t>(), M, Lmax,
+                                                               Tmax, cnt2.as<int64_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(scan_exclusive_i64(cnt2.as<int64_t>(), base2.as<int64_t>(), Tmax * M, s));
+    // total units = base2[last] + cnt2[last]
+    int64_t last_base = 0, last_cnt = 0;
+    JS_CUDA(cudaMemcpyAsync(&last_base, base2.as<int64_t>() + Tmax * M - 1, 8, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaMemcpyAsync(&last_cnt, cnt2.as<int64_t>() + Tmax * M - 1, 8, cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> b2h;
+    if (mode == JSWEEP_MODE_LEVEL_SYNC) {
+        b2h.resize(Tmax * M);
+        JS_CUDA(cudaMemcpyAsync(b2h.data(), base2.p, Tmax * M * 8, cudaMemcpyDeviceToHost, s));
+    }
+    JS_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_units = last_base + last_cnt;
+    JS_TRY(ut.units.alloc(std::max<int64_t>(n_units, 1) * 16, s));
+    k_unit_fill<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->lp.as<int32_t>(), lpoff_d.as<int64_t>(),
+                                                              nlev_d.as<int32_t>(), ucnt.as<int64_t>(),
+                                                              wscan.as<int64_t>(), base2.as<int64_t>(),
+                                                              off_d.as<int32_t>(), M, Lmax, U, ut.units.as<int4>());
+    JS_LAUNCH_CHECK();
+    ut.slot_ptr.clear();
+    if (mode == JSWEEP_MODE_LEVEL_SYNC) {
+        ut.slot_ptr.resize(Tmax + 1);
+        for (int64_t t = 0; t < Tmax; ++t) ut.slot_ptr[t] = b2h[t * M];
+        ut.slot_ptr[Tmax] = n_units;
+    }
+    JS_CUDA(cudaStreamSynchronize(s));
+    ut.n_units = n_units;
+    ut.mode = mode;
+    ut.priority = prio;
+    ut.cluster = U;
+    ut.stagger = stagger;
+    // the graph refers to the unit table
+    if (d->graph) {
+        cudaGraphExecDestroy(d->graph);
+        d->graph = nullptr;
+        d->graph_key.clear();
+    }
+    return JSWEEP_OK;
+}
+
+namespace {
+
+int resolve_mode(const Dags *d) {
+    int mode = d->opt.sweep_mode;
+    if (mode == JSWEEP_MODE_AUTO) mode = JSWEEP_MODE_LEVEL_SYNC;
+    return mode;
+}
+
+template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
+    SweepArgs<T> a;
+    a.N = d->N;
+    a.M = (int)d->M;
+    a.FS = d->mesh->FS;
+    a.Fb = (int)d->mesh->Fb;
+    a.order = d->order.as<int32_t>();
+    a.mask = d->mask.as<uint8_t>();
+    if constexpr (sizeof(T) == 4) {
+        a.geo = d->mesh->geo32.as<float4>();
+        a.dirs = reinterpret_cast<const T *>(d->quad->dirs32.p);
+    } else {
+        a.geo = d->mesh->geo64.as<double4>();
+        a.dirs = nullptr;  // set from the padded copy below
+    }
+    a.srcv = d->srcv.as<T>();
+    a.sigv = d->sigv.as<T>();
+    a.inflow = has_inflow ? d->inflow.as<T>() : nullptr;
+    a.psi = d->psi.as<T>();
+    a.psi_lag = d->psi_lag.as<T>();
+    a.lag_ptr = d->lag_ptr.as<int32_t>();
+    a.lag_face = d->lag_face.as<int32_t>();
+    a.sface = d->mesh->sface.as<int32_t>();
+    a.units = d->ut.units.as<int4>();
+    (void)Rp;
+    return a;
+}
+
+// Workspaces for (precision, padded rhs count).
+int ensure_workspace(Dags *d, int prec, int Rp, int nrhs, cudaStream_t s) {
+    const size_t es = prec == JSWEEP_F64 ? 8 : 4;
+    const int64_t N = d->N, M = d->M;
+    size_t before = (size_t)d->psi.p + (size_t)d->srcv.p + (size_t)d->sigv.p + (size_t)d->inflow.p;
+    JS_TRY(d->psi.ensure((size_t)M * N * Rp * es, s));
+    JS_TRY(d->srcv.ensure((size_t)N * Rp * es, s));
+    JS_TRY(d->sigv.ensure((size_t)N * es, s));
+    JS_TRY(d->inflow.ensure((size_t)std::max<int64_t>(d->mesh->Fb, 1) * Rp * es, s));
+    JS_TRY(d->phi_a.ensure((size_t)N * nrhs * es, s));
+    JS_TRY(d->phi_b.ensure((size_t)N * nrhs * es, s));
+    JS_TRY(d->red.ensure(64 * 8, s));
+    JS_TRY(d->counters.ensure((size_t)(M + 8) * 8, s));
+    if (d->lag_R != Rp || d->lag_prec != prec || !d->psi_lag.p) {
+        JS_TRY(d->psi_lag.alloc((size_t)std::max<int64_t>(d->T, 1) * Rp * es, s));
+        JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
+        d->lag_R = Rp;
+        d->lag_prec = prec;
+    }
+    size_t after = (size_t)d->psi.p + (size_t)d->srcv.p + (size_t)d->sigv.p + (size_t)d->inflow.p;
+    if (before != after && d->graph) {
+        cudaGraphExecDestroy(d->graph);
+        d->graph = nullptr;
+        d->graph_key.clear();
+    }
+    return JSWEEP_OK;
+}
+
+// dirs as [M][4] in the working precision
+int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s) {
+    if (buf.p) return JSWEEP_OK;
+    std::vector<double> v(4 * d->M);
+    for (int64_t m = 0; m < d->M; ++m) {
+        for (int k = 0; k < 3; ++k) v[4 * m + k] = d->quad->dirs[3 * m + k];
+        v[4 * m + 3] = 0.0;
+    }
+    JS_TRY(buf.alloc(v.size() * 8, s));
+    JS_CUDA(cudaMemcpyAsync(buf.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    return JSWEEP_OK;
+}
+
+template <class T, int R>
+int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
+    const int64_t M = d->M;
+    if (mode == JSWEEP_MODE_LEVEL_SYNC) {
+        char key[512];
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%p/%lld", (int)sizeof(T), R, (const void *)a.srcv,
+                 (const void *)a.sigv, (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
+                 (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units);
+        if (!d->graph || d->graph_key != key) {
+            if (d->graph) {
+                cudaGraphExecDestroy(d->graph);
+                d->graph = nullptr;
+            }
+            if (!d->capture_stream) JS_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
+            cudaStream_t cs = d->capture_stream;
+            JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const auto &sp = d->ut.slot_ptr;
+            for (size_t l = 0; l + 1 < sp.size(); ++l) {
+                int64_t nu = sp[l + 1] - sp[l];
+                if (nu <= 0) continue;
+                int64_t blocks = (nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
+                k_sweep_level<T, R><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, cs>>>(a, sp[l], nu);
+            }
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamEndCapture(cs, &g);
+            if (e != cudaSuccess) {
+                set_error("graph capture failed: %s", cudaGetErrorString(e));
+                return JSWEEP_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&d->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+                d->graph = nullptr;
+                return JSWEEP_ERR_CUDA;
+            }
+            d->graph_key = key;
+        }
+        JS_CUDA(cudaGraphLaunch(d->graph, s));
+        int64_t nodes = 0;
+        for (size_t l = 0; l + 1 < d->ut.slot_ptr.size(); ++l) nodes += d->ut.slot_ptr[l + 1] > d->ut.slot_ptr[l];
+        note_launches(nodes);
+        d->timing.sweep_launches = nodes;
+        return JSWEEP_OK;
+    }
+    // persistent
+    unsigned long long *ticket = reinterpret_cast<unsigned long long *>(d->counters.p);
+    int *err = reinterpret_cast<int *>(ticket + 1);
+    int *done = err + 2;
+    JS_CUDA(cudaMemsetAsync(d->counters.p, 0, (size_t)(M + 8) * 8, s));
+    int bps = d->opt.blocks_per_sm;
+    if (bps <= 0) {
+        JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_persistent<T, R>, kWarpsPerBlock * 32, 0));
+        if (bps < 1) bps = 1;
+    }
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (khz <= 0) khz = 2000000;
+    long long timeout = (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
+    int64_t grid = (int64_t)device_sm_count() * bps;
+    int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > maxg) grid = std::max<int64_t>(1, maxg);
+    // debug_block_waits: a wait for one unit more than its direction has makes
+    // every wait run out (test of the bounded-wait error path)
+    const int extra = d->opt.debug_block_waits ? (int)std::min<int64_t>(d->ut.n_units + 1, INT32_MAX / 2) : 0;
+    k_sweep_persistent<T, R><<<(unsigned)grid, kWarpsPerBlock * 32, 0, s>>>(a, d->ut.n_units, ticket, done, err,
+                                                                           timeout, extra);
+    JS_LAUNCH_CHECK();
+    d->timing.sweep_launches = 1;
+    return JSWEEP_OK;
+}
+
+int check_sweep_error(Dags *d, cudaStream_t s, int mode) {
+    if (mode != JSWEEP_MODE_PERSISTENT) return JSWEEP_OK;
+    int err = 0;
+    JS_CUDA(cudaMemcpyAsync(&err, reinterpret_cast<unsigned long long *>(d->counters.p) + 1, 4,
+                            cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    if (err) {
+        set_error("persistent sweep: a dependency wait exceeded %.3g s", d->opt.spin_timeout_s);
+        return JSWEEP_ERR_DEVICE_TIMEOUT;
+    }
+    return JSWEEP_OK;
+}
+
+template <class T, int R>
+int one_sweep(Dags *d, int mode, bool has_inflow, const T *wts, T *phi_dst, int nrhs, cudaStream_t s,
+              const T *dirs_override) {
+    SweepArgs<T> a = make_args<T>(d, R, has_inflow);
+    if (dirs_override) a.dirs = dirs_override;
+    JS_CUDA(cudaEventRecord(d->ev[0], s));
+    JS_TRY((sweep_core<T, R>(d, a, mode, s)));
+    JS_CUDA(cudaEventRecord(d->ev[1], s));
+    if (d->T > 0) {
+        k_lag_update<T, R><<<grid_for(d->T, 256), 256, 0, s>>>(d->psi.as<T>(), d->lag_m.as<int32_t>(),
+                                                              d->lag_up.as<int32_t>(), d->T, d->N, d->psi_lag.as<T>());
+        JS_LAUNCH_CHECK();
+    }
+    JS_CUDA(cudaEventRecord(d->ev[2], s));
+    k_phi<T, R><<<grid_for(d->N, 256, 152 * 16), 256, 0, s>>>(d->psi.as<T>(), wts, d->N, (int)d->M, nrhs, phi_dst);
+    JS_LAUNCH_CHECK();
+    JS_CUDA(cudaEventRecord(d->ev[3], s));
+    return JSWEEP_OK;
+}
+
+}  // namespace
+
+// FP64 directions in [M][4] layout (the FP32 copy lives in the quadrature).
+static int dirs64x4(Dags *d, cudaStream_t s, const double **out) {
+    JS_TRY(ensure_dirs64x4(d, d->dirs4_64, s));
+    *out = d->dirs4_64.as<double>();
+    return JSWEEP_OK;
+}
+
+template <class T, int R>
+static int run_sweep_t(Dags *d, int nrhs, const void *sigma_t, const void *ang_source, const void *inflow,
+                       void *phi_out, void *psi_out, cudaStream_t s) {
+    const int mode = resolve_mode(d);
+    JS_TRY(ensure_units(d, mode, s));
+    JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
+    const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
+                                  : reinterpret_cast<const T *>(d->mesh->vol32.p);
+    const T *w = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->quad->w64.p)
+                                : reinterpret_cast<const T *>(d->quad->w32.p);
+    const double *d64 = nullptr;
+    if (sizeof(T) == 8) JS_TRY(dirs64x4(d, s, &d64));
+    k_source_prep<T, R><<<grid_for(d->N, 256, 152 * 16), 256, 0, s>>>(
+        (const T *)sigma_t, (const T *)ang_source, vol, d->N, nrhs, d->srcv.as<T>(), d->sigv.as<T>());
+    JS_LAUNCH_CHECK();
+    const bool has_inflow = inflow != nullptr;
+    if (has_inflow) {
+        const size_t es = sizeof(T);
+        JS_CUDA(cudaMemsetAsync(d->inflow.p, 0, d->inflow.bytes, s));
+        JS_CUDA(cudaMemcpyAsync(d->inflow.p, inflow, (size_t)nrhs * d->mesh->Fb * es, cudaMemcpyDeviceToDevice, s));
+    }
+    JS_TRY((one_sweep<T, R>(d, mode, has_inflow, w, (T *)phi_out, nrhs, s, (const T *)d64)));
+    if (psi_out) {
+        k_psi_out<T, R><<<grid_for(d->N * d->M, 256, 152 * 32), 256, 0, s>>>(d->psi.as<T>(), d->N, (int)d->M, nrhs,
+                                                                            (T *)psi_out);
+        JS_LAUNCH_CHECK();
+    }
+    JS_TRY(check_sweep_error(d, s, mode));
+    JS_CUDA(cudaStreamSynchronize(s));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, d->ev[0], d->ev[1]);
+    cudaEventElapsedTime(&b, d->ev[2], d->ev[3]);
+    d->timing.sweep_ms = a;
+    d->timing.phi_ms = b;
+    return JSWEEP_OK;
+}
+
+template <class T, int R>
+static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, const void *q, const void *inflow,
+                    double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
+    const int mode = resolve_mode(d);
+    JS_TRY(ensure_units(d, mode, s));
+    JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
+    JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
+    const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
+                                  : reinterpret_cast<const T *>(d->mesh->vol32.p);
+    const T *w = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->quad->w64.p)
+                                : reinterpret_cast<const T *>(d->quad->w32.p);
+    const double *d64 = nullptr;
+    if (sizeof(T) == 8) JS_TRY(dirs64x4(d, s, &d64));
+    const bool has_inflow = inflow != nullptr;
+    if (has_inflow) {
+        JS_CUDA(cudaMemsetAsync(d->inflow.p, 0, d->inflow.bytes, s));
+        JS_CUDA(cudaMemcpyAsync(d->inflow.p, inflow, (size_t)nrhs * d->mesh->Fb * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    T *phi_old = nullptr;  // phi^0 = 0
+    T *bufs[2] = {d->phi_a.as<T>(), d->phi_b.as<T>()};
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(d->red.p);
+    double *resid_d = reinterpret_cast<double *>(acc + 32);
+    double resid_h[9] = {0};
+    int it = 0;
+    bool conv = false;
+    T *phi_new = bufs[0];
+    for (it = 1; it <= max_iters; ++it) {
+        phi_new = bufs[(it - 1) & 1];
+        k_emission<T, R><<<grid_for(d->N, 256, 152 * 16), 256, 0, s>>>(
+            (const T *)sigma_t, (const T *)c_ratio, (const T *)q, phi_old, vol, d->N, nrhs, d->srcv.as<T>(),
+            d->sigv.as<T>());
+        JS_LAUNCH_CHECK();
+        JS_TRY((one_sweep<T, R>(d, mode, has_inflow, w, phi_new, nrhs, s, (const T *)d64)));
+        JS_CUDA(cudaMemsetAsync(acc, 0, 2 * 8 * 8, s));
+        k_resid<T><<<dim3(grid_for(d->N, 256, 152 * 4), nrhs), 256, 0, s>>>(phi_new, phi_old, d->N, acc);
+        JS_LAUNCH_CHECK();
+        k_resid_final<<<1, 32, 0, s>>>(acc, nrhs, resid_d);
+        JS_LAUNCH_CHECK();
+        JS_CUDA(cudaMemcpyAsync(resid_h, resid_d, (nrhs + 1) * 8, cudaMemcpyDeviceToHost, s));
+        JS_CUDA(cudaStreamSynchronize(s));
+        JS_TRY(check_sweep_error(d, s, mode));
+        phi_old = phi_new;
+        if (resid_h[nrhs] < tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    JS_CUDA(cudaMemcpyAsync(phi_out, phi_new, (size_t)nrhs * d->N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, d->ev[0], d->ev[1]);
+    cudaEventElapsedTime(&b, d->ev[2], d->ev[3]);
+    d->timing.sweep_ms = a;
+    d->timing.phi_ms = b;
+    if (iters_out) *iters_out = it;
+    if (resid_out) *resid_out = resid_h[nrhs];
+    if (!conv) {
+        set_error("source iteration did not reach tol %g in %d iterations (residual %g)", tol, max_iters,
+                  resid_h[nrhs]);
+        return JSWEEP_ERR_NOT_CONVERGED;
+    }
+    return JSWEEP_OK;
+}
+
+int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source, const void *inflow,
+              void *phi_out, void *psi_out, cudaStream_t s) {
+    const int Rp = pad_rhs(nrhs);
+    if (prec == JSWEEP_F64) {
+        switch (Rp) {
+            case 1: return run_sweep_t<double, 1>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+            case 2: return run_sweep_t<double, 2>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+            case 4: return run_sweep_t<double, 4>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+            default: return run_sweep_t<double, 8>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+        }
+    }
+    switch (Rp) {
+        case 1: return run_sweep_t<float, 1>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+        case 2: return run_sweep_t<float, 2>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+        case 4: return run_sweep_t<float, 4>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+        default: return run_sweep_t<float, 8>(d, nrhs, sigma_t, ang_source, inflow, phi_out, psi_out, s);
+    }
+}
+
+int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio, const void *q,
+                         const void *inflow, double tol, int max_iters, void *phi_out, int *iters_out,
+                         double *resid_out, cudaStream_t s) {
+    const int Rp = pad_rhs(nrhs);
+#define JS_SI(T, R) run_si_t<T, R>(d, nrhs, sigma_t, c_ratio, q, inflow, tol, max_iters, phi_out, iters_out, resid_out, s)
+    if (prec == JSWEEP_F64) {
+        switch (Rp) {
+            case 1: return JS_SI(double, 1);
+            case 2: return JS_SI(double, 2);
+            case 4: return JS_SI(double, 4);
+            default: return JS_SI(double, 8);
+        }
+    }
+    switch (Rp) {
+        case 1: return JS_SI(float, 1);
+        case 2: return JS_SI(float, 2);
+        case 4: return JS_SI(float, 4);
+        default: return JS_SI(float, 8);
+    }
+#undef JS_SI
+}
+
+}  // namespace js

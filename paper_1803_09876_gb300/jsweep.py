@@ -1,0 +1,403 @@
+"""Thin Python binding of the jsweep C ABI (``include/jsweep.h``).
+
+Argument marshalling only: every step of the sweep path runs in the CUDA
+library ``libjsweep.so``.  Host arrays are numpy arrays; device arrays are
+CUDA torch tensors (their ``data_ptr()`` is passed through) and the stream is
+torch's current stream.  PyTorch also provides the library's own device
+memory (its caching allocator is installed with ``jsweep_set_allocator``).
+
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+
+from __future__ import annotations
+
+import atexit
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjsweep.so")
+
+JSWEEP_OK = 0
+JSWEEP_ERR_INVALID_ARG = -1
+JSWEEP_ERR_MESH_INVALID = -2
+JSWEEP_ERR_OOM = -3
+JSWEEP_ERR_NOT_CONVERGED = -4
+JSWEEP_ERR_DEVICE_TIMEOUT = -5
+JSWEEP_ERR_CUDA = -6
+JSWEEP_ERR_UNIMPLEMENTED = -7
+JSWEEP_ERR_CYCLE = -8
+
+JSWEEP_F64 = 0
+JSWEEP_F32 = 1
+
+JSWEEP_MODE_AUTO = 0
+JSWEEP_MODE_LEVEL_SYNC = 1
+JSWEEP_MODE_PERSISTENT = 2
+
+JSWEEP_PRIO_LEVEL = 0
+JSWEEP_PRIO_DEPTH = 1
+JSWEEP_PRIO_OCTANT = 2
+
+# every symbol include/jsweep.h declares
+EXPORTED = [
+    "jsweep_options_default", "jsweep_last_error", "jsweep_version", "jsweep_set_allocator",
+    "jsweep_mesh_create", "jsweep_mesh_destroy", "jsweep_mesh_info",
+    "jsweep_quadrature_product", "jsweep_quadrature_create", "jsweep_quadrature_destroy",
+    "jsweep_build_dags", "jsweep_dags_destroy", "jsweep_dags_info", "jsweep_dags_nlevels",
+    "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
+    "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
+]
+
+
+class JsweepError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"jsweep error {code}: {msg}")
+        self.code = code
+
+
+class jsweep_options(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int),
+        ("sweep_mode", ctypes.c_int),
+        ("priority", ctypes.c_int),
+        ("cluster_cells", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int),
+        ("octant_stagger", ctypes.c_int),
+        ("spin_timeout_s", ctypes.c_double),
+        ("cycle_search_max", ctypes.c_int),
+        ("debug_block_waits", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
+    ]
+
+
+class jsweep_timing(ctypes.Structure):
+    _fields_ = [
+        ("build_ms", ctypes.c_double),
+        ("sweep_ms", ctypes.c_double),
+        ("phi_ms", ctypes.c_double),
+        ("sweep_launches", ctypes.c_int64),
+        ("build_launches", ctypes.c_int64),
+        ("call_launches", ctypes.c_int64),
+    ]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+_callbacks = None
+_exiting = False
+
+
+def _at_exit():
+    # Handles still alive at interpreter exit are left to the process teardown:
+    # releasing them would call back into Python (torch's allocator) while it
+    # shuts down.
+    global _exiting
+    _exiting = True
+
+
+atexit.register(_at_exit)
+
+
+def _live():
+    return _lib is not None and not _exiting
+
+
+def load(path: str = LIB_PATH):
+    """Load libjsweep.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_1803_09876_gb300.build.build() "
+                              "(nvcc, sm_103a); there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        sig = {
+            "jsweep_options_default": (I, [P]),
+            "jsweep_last_error": (ctypes.c_char_p, []),
+            "jsweep_version": (I, []),
+            "jsweep_set_allocator": (I, [P, P, P]),
+            "jsweep_mesh_create": (I, [I64, I64, P, P, P, P, P]),
+            "jsweep_mesh_destroy": (I, [P]),
+            "jsweep_mesh_info": (I, [P, P, P, P, P]),
+            "jsweep_quadrature_product": (I, [I, I, P, P]),
+            "jsweep_quadrature_create": (I, [I64, P, P, P]),
+            "jsweep_quadrature_destroy": (I, [P]),
+            "jsweep_build_dags": (I, [P, P, P, P, P]),
+            "jsweep_dags_destroy": (I, [P]),
+            "jsweep_dags_info": (I, [P, P, P, P]),
+            "jsweep_dags_nlevels": (I, [P, I64, P]),
+            "jsweep_dags_levels": (I, [P, I64, P]),
+            "jsweep_dags_order": (I, [P, I64, P, P]),
+            "jsweep_dags_lagged": (I, [P, I64, P, P]),
+            "jsweep_dags_reset_lag": (I, [P]),
+            "jsweep_dags_set_options": (I, [P, P]),
+            "jsweep_sweep": (I, [P, I, I, P, P, P, P, P, P]),
+            "jsweep_source_iterate": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
+            "jsweep_dags_timing": (I, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def lib():
+    return load()
+
+
+def _check(code, what=""):
+    if code != JSWEEP_OK:
+        msg = lib().jsweep_last_error().decode(errors="replace")
+        raise JsweepError(code, f"{what}: {msg}" if what else msg)
+    return code
+
+
+def use_torch_allocator():
+    """Route the library's own device allocations through torch's caching allocator."""
+    global _callbacks
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          torch.cuda.current_stream()))
+        except Exception:  # out of memory: the library reports JSWEEP_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(lib().jsweep_set_allocator(ctypes.cast(cbs[0], ctypes.c_void_p),
+                                      ctypes.cast(cbs[1], ctypes.c_void_p), None), "set_allocator")
+    _callbacks = cbs
+
+
+def jsweep_options_default(**overrides) -> jsweep_options:
+    o = jsweep_options()
+    _check(lib().jsweep_options_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def jsweep_version() -> int:
+    return int(lib().jsweep_version())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype, n, what):
+    """Device pointer of a contiguous CUDA tensor with exactly n elements."""
+    if t is None:
+        return None
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{what}: need a contiguous {dtype} tensor of {n} elements, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """Handle of a mesh on the device (jsweep_mesh_create)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        n, f, b, fs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().jsweep_mesh_info(self._h, ctypes.byref(n), ctypes.byref(f), ctypes.byref(b), ctypes.byref(fs)))
+        self.n_cells, self.n_faces, self.n_bfaces, self.max_faces = n.value, f.value, b.value, fs.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _live():
+            _lib.jsweep_mesh_destroy(self._h)
+            self._h = None
+
+
+class Quad:
+    """Handle of a direction set (jsweep_quadrature_create)."""
+
+    def __init__(self, handle, dirs, weights):
+        self._h = handle
+        self.dirs = dirs
+        self.weights = weights
+        self.n_dirs = dirs.shape[0]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _live():
+            _lib.jsweep_quadrature_destroy(self._h)
+            self._h = None
+
+
+class Dags:
+    """Per-direction dependency graphs resident on the device (jsweep_build_dags)."""
+
+    def __init__(self, handle, mesh, quad):
+        self._h = handle
+        self.mesh = mesh
+        self.quad = quad
+        M, L, T = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().jsweep_dags_info(self._h, ctypes.byref(M), ctypes.byref(L), ctypes.byref(T)))
+        self.n_dirs, self.max_levels, self.n_lag_total = M.value, L.value, T.value
+        self.n_cells = mesh.n_cells
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _live():
+            _lib.jsweep_dags_destroy(self._h)
+            self._h = None
+
+    def nlevels(self, m: int) -> int:
+        out = ctypes.c_int64()
+        _check(lib().jsweep_dags_nlevels(self._h, int(m), ctypes.byref(out)))
+        return out.value
+
+    def levels(self, m: int) -> np.ndarray:
+        out = np.empty(self.n_cells, dtype=np.int32)
+        _check(lib().jsweep_dags_levels(self._h, int(m), _ptr(out)))
+        return out
+
+    def order(self, m: int):
+        order = np.empty(self.n_cells, dtype=np.int32)
+        ptr = np.empty(self.nlevels(m) + 1, dtype=np.int32)
+        _check(lib().jsweep_dags_order(self._h, int(m), _ptr(order), _ptr(ptr)))
+        return order, ptr
+
+    def lagged(self, m: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(lib().jsweep_dags_lagged(self._h, int(m), None, ctypes.byref(n)))
+        rows = np.empty((n.value, 3), dtype=np.int64)
+        if n.value:
+            _check(lib().jsweep_dags_lagged(self._h, int(m), _ptr(rows), ctypes.byref(n)))
+        return rows
+
+    def reset_lag(self):
+        _check(lib().jsweep_dags_reset_lag(self._h))
+
+    def set_options(self, opt: jsweep_options):
+        _check(lib().jsweep_dags_set_options(self._h, ctypes.byref(opt)))
+
+    def timing(self) -> dict:
+        t = jsweep_timing()
+        _check(lib().jsweep_dags_timing(self._h, ctypes.byref(t)))
+        return {"build_ms": t.build_ms, "sweep_ms": t.sweep_ms, "phi_ms": t.phi_ms,
+                "sweep_launches": t.sweep_launches, "build_launches": t.build_launches,
+                "call_launches": t.call_launches}
+
+
+def jsweep_mesh_create(n_cells, n_faces, face_cells, normals, areas, volumes) -> Mesh:
+    fc = _np(face_cells, np.int64).reshape(-1, 2)
+    nr = _np(normals, np.float64).reshape(-1, 3)
+    ar = _np(areas, np.float64).ravel()
+    vo = _np(volumes, np.float64).ravel()
+    if fc.shape[0] != n_faces or nr.shape[0] != n_faces or ar.size != n_faces or vo.size != n_cells:
+        raise ValueError("jsweep_mesh_create: array sizes do not match n_cells / n_faces")
+    h = ctypes.c_void_p()
+    _check(lib().jsweep_mesh_create(int(n_cells), int(n_faces), _ptr(fc), _ptr(nr), _ptr(ar), _ptr(vo),
+                                    ctypes.byref(h)), "jsweep_mesh_create")
+    return Mesh(h)
+
+
+def mesh_from_dict(mesh: dict) -> Mesh:
+    return jsweep_mesh_create(mesh["n_cells"], mesh["n_faces"], mesh["face_cells"], mesh["normals"],
+                              mesh["areas"], mesh["volumes"])
+
+
+def jsweep_quadrature_product(n_polar: int, n_azim: int):
+    M = 8 * n_polar * n_azim
+    d = np.empty((M, 3))
+    w = np.empty(M)
+    _check(lib().jsweep_quadrature_product(int(n_polar), int(n_azim), _ptr(d), _ptr(w)),
+           "jsweep_quadrature_product")
+    return d, w
+
+
+def jsweep_quadrature_create(dirs, weights) -> Quad:
+    d = _np(dirs, np.float64).reshape(-1, 3)
+    w = _np(weights, np.float64).ravel()
+    if w.size != d.shape[0]:
+        raise ValueError("jsweep_quadrature_create: dirs and weights differ in length")
+    h = ctypes.c_void_p()
+    _check(lib().jsweep_quadrature_create(d.shape[0], _ptr(d), _ptr(w), ctypes.byref(h)),
+           "jsweep_quadrature_create")
+    return Quad(h, d, w)
+
+
+def jsweep_build_dags(mesh: Mesh, quad: Quad, options: jsweep_options | None = None, stream=None) -> Dags:
+    h = ctypes.c_void_p()
+    _check(lib().jsweep_build_dags(mesh._h, quad._h, ctypes.byref(options) if options is not None else None,
+                                   _stream(stream), ctypes.byref(h)), "jsweep_build_dags")
+    return Dags(h, mesh, quad)
+
+
+def _prec(dtype):
+    import torch
+    if dtype == torch.float64:
+        return JSWEEP_F64
+    if dtype == torch.float32:
+        return JSWEEP_F32
+    raise TypeError(f"unsupported dtype {dtype} (float64 or float32)")
+
+
+def jsweep_sweep(dags: Dags, sigma_t, ang_source, inflow=None, phi_out=None, psi_out=None, stream=None):
+    """One sweep of all directions; ang_source [R, N] (device).  Returns phi [R, N]."""
+    import torch
+    N, M, Fb = dags.n_cells, dags.n_dirs, dags.mesh.n_bfaces
+    R = ang_source.shape[0] if ang_source.dim() == 2 else 1
+    dt = ang_source.dtype
+    prec = _prec(dt)
+    if phi_out is None:
+        phi_out = torch.empty((R, N), dtype=dt, device=ang_source.device)
+    rc = lib().jsweep_sweep(dags._h, R, prec, _dptr(sigma_t, dt, N, "sigma_t"), _dptr(ang_source, dt, R * N, "ang_source"),
+                            _dptr(inflow, dt, R * Fb, "inflow"), _dptr(phi_out, dt, R * N, "phi_out"),
+                            _dptr(psi_out, dt, R * M * N, "psi_out"), _stream(stream))
+    _check(rc, "jsweep_sweep")
+    return phi_out
+
+
+def jsweep_source_iterate(dags: Dags, sigma_t, c_ratio, q, inflow=None, tol=1e-8, max_iters=1000,
+                          phi_out=None, stream=None, allow_not_converged=False):
+    """Source iteration from phi = 0.  Returns (phi [R, N], iterations, residual, converged)."""
+    import torch
+    N, Fb = dags.n_cells, dags.mesh.n_bfaces
+    R = q.shape[0] if q.dim() == 2 else 1
+    dt = q.dtype
+    prec = _prec(dt)
+    if phi_out is None:
+        phi_out = torch.empty((R, N), dtype=dt, device=q.device)
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    rc = lib().jsweep_source_iterate(dags._h, R, prec, _dptr(sigma_t, dt, N, "sigma_t"), _dptr(c_ratio, dt, N, "c_ratio"),
+                                     _dptr(q, dt, R * N, "q"), _dptr(inflow, dt, R * Fb, "inflow"), float(tol),
+                                     int(max_iters), _dptr(phi_out, dt, R * N, "phi_out"), ctypes.byref(it),
+                                     ctypes.byref(res), _stream(stream))
+    if rc == JSWEEP_ERR_NOT_CONVERGED and allow_not_converged:
+        return phi_out, it.value, res.value, False
+    _check(rc, "jsweep_source_iterate")
+    return phi_out, it.value, res.value, True
