@@ -46,8 +46,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=128, help="hex edge (128 = the benchmark workload)")
-    p.add_argument("--mode", type=int, default=2, help="1 level-synchronous, 2 persistent")
-    p.add_argument("--priority", type=int, default=2)
+    p.add_argument("--mode", type=int, default=1, help="1 level-synchronous (CUDA graph), 2 data-driven persistent")
+    p.add_argument("--priority", type=int, default=0)
+    p.add_argument("--layering", type=int, default=0, help="0 octant-aligned layers, 1 longest-path levels")
     p.add_argument("--cluster", type=int, default=32)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -207,7 +208,8 @@ def run_gpu(args):
     M = len(dirs)
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
-    opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster)
+    opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
+                                   layering=args.layering)
     dev = torch.device("cuda", local)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device=dev)
     cr = torch.as_tensor(wl["c_ratio"], dtype=torch.float32, device=dev)
@@ -276,7 +278,9 @@ def run_gpu(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "sweep (persistent) + phi reduction, one sweep of all directions",
+            "traffic": None,
+            "kernel": ("sweep (level-synchronous CUDA graph)" if args.mode == 1 else "sweep (data-driven persistent)")
+                      + " + phi reduction, one sweep of all directions",
             "alg_bytes_per_cell_dir": B, "sweep_ms": sw_ms, "phi_ms": ph_ms,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
     sweep_rate = N * M * R / ((sw_ms + ph_ms) / 1e3)
@@ -327,7 +331,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.n == 128 else f"hex{args.n}_288dirs_8rhs",
                        "cells": N, "directions": M, "rhs": R, "sweep_mode": args.mode,
-                       "priority": args.priority, "cluster_cells": args.cluster,
+                       "priority": args.priority, "cluster_cells": args.cluster, "layering": args.layering,
                        "l2": "inputs larger than L2 (psi 19.3 GB), no flush",
                        "parallelism": f"replicas x{ws}", "si_iterations_per_step": iters / args.steps},
             "roofline": roof,

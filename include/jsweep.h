@@ -59,6 +59,18 @@ extern "C" {
 #define JSWEEP_MODE_LEVEL_SYNC 1 /* one launch per level index, replayed from a CUDA graph */
 #define JSWEEP_MODE_PERSISTENT 2 /* one grid-resident launch driven by dependency counters */
 
+/* ---- schedule layers (jsweep_options.layering) ------------------------------
+ * Both sweep schedules process the cells of a direction layer by layer; any
+ * layering that increases along every dependency is valid and gives the same
+ * results.  LEVEL uses the longest-path levels.  OCTANT (default) uses
+ * kappa_m(c) = max(floor(rho_o * lambda_o(c)), 1 + max over upwind u of kappa_m(u)),
+ * where lambda_o is the level of c for the diagonal direction of m's octant and
+ * rho_o the largest level count of the octant over the diagonal's: the
+ * directions of an octant then reach a cell at nearly the same time, so its
+ * geometry and sources are fetched once for most of them. */
+#define JSWEEP_LAYERS_OCTANT 0
+#define JSWEEP_LAYERS_LEVEL 1
+
 /* ---- work-unit orderings for the persistent schedule (jsweep_options.priority) */
 #define JSWEEP_PRIO_LEVEL 0     /* by level index, all directions together */
 #define JSWEEP_PRIO_DEPTH 1     /* by remaining depth: long directions start first */
@@ -83,7 +95,9 @@ typedef struct {
     int debug_block_waits; /* test hook, 0 in normal use: when nonzero every dependency wait of the
                               persistent schedule needs one more finished unit than can exist, so
                               the waits run out and the call returns JSWEEP_ERR_DEVICE_TIMEOUT */
-    int reserved[7];
+    int layering;          /* schedule layers (set at jsweep_build_dags): JSWEEP_LAYERS_OCTANT (default)
+                              or JSWEEP_LAYERS_LEVEL; results do not depend on it */
+    int reserved[6];
 } jsweep_options;
 
 /* Fill *opt with defaults. */
@@ -218,6 +232,8 @@ typedef struct {
     int64_t sweep_launches; /* kernels launched by the last sweep (graph nodes included) */
     int64_t build_launches; /* kernels launched by the last jsweep_build_dags */
     int64_t call_launches;  /* kernels launched by the last jsweep_sweep / jsweep_source_iterate */
+    int64_t build_steps;    /* frontier steps of the last build (about the largest level count) */
+    int64_t build_stall_rounds; /* cycle-resolution rounds of the last build, summed over directions */
 } jsweep_timing;
 int jsweep_dags_timing(jsweep_dags_t dags, jsweep_timing *t);
 

@@ -449,6 +449,11 @@ static int check_options(const jsweep_options *opt, jsweep_options *o) {
     if (opt->spin_timeout_s > 0) o->spin_timeout_s = opt->spin_timeout_s;
     if (opt->cycle_search_max > 0) o->cycle_search_max = opt->cycle_search_max;
     o->debug_block_waits = opt->debug_block_waits ? 1 : 0;
+    if (opt->layering < 0 || opt->layering > JSWEEP_LAYERS_LEVEL) {
+        set_error("jsweep_options.layering=%d out of range", opt->layering);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    o->layering = opt->layering;
     return JSWEEP_OK;
 }
 

@@ -119,6 +119,15 @@ struct Dags {
     DevBuf lp;      // int32 [sum (L_m + 1)]
     DevBuf lag_ptr; // int32 [M+1]
     DevBuf lag_m, lag_face, lag_up, lag_dn;  // int32 [T], sorted by (m, face)
+    // schedule layering used by the sweeps (levels, or octant-aligned layers)
+    int layering = JSWEEP_LAYERS_LEVEL;
+    int64_t Smax = 0;                 // largest layer count
+    std::vector<int64_t> slayers;     // [M] layer count per direction
+    std::vector<int64_t> sp_off;      // [M+1] offsets into the layer pointers
+    DevBuf korder, kmask, klp;        // octant layering: order, mask, layer pointers
+    const int32_t *s_order = nullptr; // the order / mask / layer pointers in use
+    const uint8_t *s_mask = nullptr;
+    const int32_t *s_lp = nullptr;
     // lagged upwind values: [T][R] in the precision of the last sweep
     DevBuf psi_lag;
     int lag_R = 0, lag_prec = -1;
@@ -129,7 +138,9 @@ struct Dags {
     DevBuf inflow;   // [R][Fb] copy (stable pointer for graphs)
     DevBuf phi_a, phi_b;  // [R][N] (SI ping-pong)
     DevBuf red;      // residual accumulators / flags
-    DevBuf counters; // persistent schedule: ticket, done[M], error
+    DevBuf counters; // persistent schedule: error word
+    DevBuf flags;    // int32 [M][N]: sweep epoch at which (direction, cell) was last written
+    int epoch = 0;
     DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
     UnitTable ut;
     // CUDA graph of the level-synchronous sweep
@@ -148,7 +159,7 @@ void quad_release(Quad *q);
 int build_dags(Dags *d, cudaStream_t s);
 
 // unit schedules and sweeps (sweep.cu)
-int ensure_units(Dags *d, int mode, cudaStream_t s);
+int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s);
 int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source,
               const void *inflow, void *phi_out, void *psi_out, cudaStream_t s);
 int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio,

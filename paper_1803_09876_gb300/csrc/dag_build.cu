@@ -73,7 +73,9 @@ struct BuildCtx {
     int4 *lagall;
     int32_t *nlag;
     int64_t lag_cap;
-    int32_t *status;  // [0] error code, [1] error info, [2] remaining (clamped), [3] step counter
+    int32_t *status;  // [0] error code, [1] error info, [2] remaining (clamped), [3] step counter,
+                      // [4] stall rounds, [5] cycles found by walks, [6] components lagged
+    unsigned long long *wclaim;  // [M][N]: (epoch << 32) | (walker + 1) of the walk that owns the cell
 };
 
 __device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, int64_t cap,
@@ -135,6 +137,7 @@ __global__ void k_peel(BuildCtx c, int cur) {
     int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
     int32_t *ncl = c.ncand + ci * c.M + m;
     const int32_t ep = c.epoch[m];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.npend = 0;  // read by the last commit
     int processed = 0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int32_t v = fr[i];
@@ -188,20 +191,61 @@ __device__ __forceinline__ int warp_find(const int32_t *X, int size, int32_t v, 
     return -1;
 }
 
-constexpr int kResolveWarps = 8;
+constexpr int kResolveWarps = 16;
+constexpr int kSeedCap = 2048;  // cycles kept per stalled direction and step (more wait for the next stall)
 
-// Cycle resolution for stalled directions: blockIdx.x = direction.
-// Dynamic shared memory: per warp, X[B] (int32), Sidx[B] (int32), inS[B] (uint8).
+// Walk x -> first_open_pred(x) from candidate `i` with claimed cells: a cell
+// owned (this epoch) by a lower walker id stops the walk, a higher id is taken
+// over.  The lowest-id walker that reaches a pointer cycle therefore owns the
+// whole cycle and comes back to a cell it owns: that cell is returned (or -1).
+__device__ int32_t claim_walk(const BuildCtx &c, int64_t base, int32_t v, uint32_t me, int32_t ep,
+                              int walk_max) {
+    const unsigned long long tag = ((unsigned long long)(uint32_t)ep << 32) | me;
+    int32_t x = v;
+    for (int step = 0; step < walk_max && x >= 0; ++step) {
+        unsigned long long *slot = c.wclaim + base + x;
+        unsigned long long old = *((volatile unsigned long long *)slot);
+        while (true) {
+            if ((int32_t)(old >> 32) == ep) {
+                uint32_t owner = (uint32_t)old;
+                if (owner == me) return x;  // closed a cycle of our own
+                if (owner < me) return -1;  // a lower walker owns this path
+            }
+            unsigned long long prev = atomicCAS(slot, old, tag);
+            if (prev == old) break;
+            old = prev;
+        }
+        x = first_open_pred(c, base, x);
+    }
+    return -1;
+}
+
+// Cycle resolution, every step, for every unfinished direction with new
+// candidates (blockIdx.x = direction).  A component is resolved as soon as a
+// walk can close it, not only when the whole direction has stalled, so that
+// the cells behind it are not held back until the rest of the front drains.
+// The closure test only ever accepts a set closed under unfinished upwind
+// cells, which contains the whole component whatever the frontier holds.
+// Phase A: every thread walks candidates (claim_walk) and records the cells at
+// which it closed a pointer cycle.  Phase B: one warp per recorded cycle
+// gathers the unfinished cells that reach it backwards (cap B); when that set
+// closes, the cycle's strongly connected component is computed inside it and
+// its smallest active face is lagged (one lag per component: the component is
+// claimed through its smallest cell).
+// Dynamic shared memory: per warp X[B] (int32), Sidx[B] (int32), inS[B] (uint8).
 __global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
     const int64_t m = blockIdx.x;
-    if (c.nfront[nxt * c.M + m] != 0 || c.nproc[m] >= c.N) return;  // not stalled
+    if (c.nproc[m] >= c.N) return;  // direction finished
+    const bool stalled = c.nfront[nxt * c.M + m] == 0;
+    if (!stalled && c.ncand[c.cidx[m] * c.M + m] == 0) return;  // nothing new to look at
     extern __shared__ int32_t sh[];
-    __shared__ int32_t new_lags;
+    __shared__ int32_t seeds[kSeedCap];
+    __shared__ int32_t nseeds, new_lags;
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    int32_t *X = sh + warp * (2 * B + (B + 3) / 4);
-    int32_t *Sidx = X + B;
-    uint8_t *inS = reinterpret_cast<uint8_t *>(Sidx + B);
-    if (threadIdx.x == 0) new_lags = 0;
+    if (threadIdx.x == 0) {
+        nseeds = 0;
+        new_lags = 0;
+    }
     __syncthreads();
     const int64_t base = m * c.N;
     const int ci = c.cidx[m];
@@ -210,41 +254,27 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
     int32_t *cn = c.cand + (int64_t)(ci ^ 1) * c.M * c.N + base;
     int32_t *ncn = c.ncand + (ci ^ 1) * c.M + m;
     const int32_t ep = c.epoch[m];
-    int my_lags = 0;
 
-    for (int32_t i = warp; i < nc; i += kResolveWarps) {
-        // ---- walk to a loop of "first unfinished upwind" pointers (lane 0)
-        int32_t seed = -1;
-        if (lane == 0) {
-            int32_t v = cl[i];
-            if (c.lvl[base + v] < 0 && c.cnt[base + v] > 0) {
-                // Brent's cycle detection on x -> first_open_pred(x)
-                int32_t tort = v, hare = first_open_pred(c, base, v);
-                int power = 1, lam = 1, steps = 1;
-                bool ok = hare >= 0;
-                while (ok && tort != hare) {
-                    if (power == lam) {
-                        tort = hare;
-                        power <<= 1;
-                        lam = 0;
-                    }
-                    hare = first_open_pred(c, base, hare);
-                    ++lam;
-                    if (hare < 0 || ++steps > walk_max) ok = false;
-                }
-                if (ok) {
-                    int32_t x = hare, mn = hare;
-                    for (int s = 1; s < lam; ++s) {
-                        x = first_open_pred(c, base, x);
-                        mn = min(mn, x);
-                    }
-                    seed = mn;
-                }
-            }
+    // ---- phase A: claimed pointer walks
+    for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+        int32_t v = cl[i];
+        if (c.lvl[base + v] >= 0 || c.cnt[base + v] <= 0) continue;
+        int32_t x = claim_walk(c, base, v, (uint32_t)i + 1u, ep, walk_max);
+        if (x >= 0) {
+            int32_t k = atomicAdd(&nseeds, 1);
+            if (k < kSeedCap) seeds[k] = x;
         }
-        seed = __shfl_sync(0xffffffffu, seed, 0);
-        if (seed < 0) continue;
+    }
+    __syncthreads();
+    const int ns_total = min(nseeds, kSeedCap);
+    if (threadIdx.x == 0) atomicAdd(&c.status[5], ns_total);
 
+    int32_t *X = sh + warp * (2 * B + (B + 3) / 4);
+    int32_t *Sidx = X + B;
+    uint8_t *inS = reinterpret_cast<uint8_t *>(Sidx + B);
+    int my_lags = 0;
+    for (int si = warp; si < ns_total; si += kResolveWarps) {
+        const int32_t seed = seeds[si];
         // ---- backward closure of the seed over unfinished cells, capped at B
         if (lane == 0) X[0] = seed;
         __syncwarp();
@@ -363,9 +393,18 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
     if (lane == 0 && my_lags) atomicAdd(&new_lags, my_lags);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (new_lags == 0) {
+        atomicAdd(&c.status[4], 1);
+        atomicAdd(&c.status[6], new_lags);
+        if (stalled && new_lags == 0 && nseeds <= kSeedCap) {
             // stalled and nothing found: a component larger than the search cap
             if (atomicCAS(&c.status[0], 0, JSWEEP_ERR_CYCLE) == 0) c.status[1] = (int32_t)m;
+        }
+        if (nseeds > kSeedCap) {
+            // seeds were dropped: keep this round's candidates for the next stall
+            for (int32_t i = 0; i < nc; ++i) {
+                int32_t v = cl[i];
+                if (c.lvl[base + v] < 0 && atomicExch(&c.stamp[base + v], ep + 1) != ep + 1) push(cn, ncn, v, c.N, c.status);
+            }
         }
         c.ncand[ci * c.M + m] = 0;
         c.cidx[m] = ci ^ 1;
@@ -379,7 +418,26 @@ __device__ __forceinline__ int slot_of(const BuildCtx &c, int32_t cell, int32_t 
     return -1;
 }
 
-__global__ void k_commit(BuildCtx c, int nxt) {
+// Applies this step's lags; block 0 also clears the consumed frontier and
+// counts the cells still to be processed (the pending list is cleared by the
+// next step's peel, after every block here has read its length).
+__global__ void k_commit(BuildCtx c, int nxt, int cur) {
+    if (blockIdx.x == 0) {
+        __shared__ unsigned long long rem;
+        if (threadIdx.x == 0) rem = 0;
+        __syncthreads();
+        unsigned long long mine = 0;
+        for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) {
+            c.nfront[cur * c.M + m] = 0;
+            mine += (unsigned long long)(c.N - c.nproc[m]);
+        }
+        atomicAdd(&rem, mine);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            c.status[2] = (int32_t)min(rem, (unsigned long long)INT_MAX);
+            c.status[3] += 1;
+        }
+    }
     const int32_t n = min(*c.npend, (int32_t)c.pend_cap);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int4 e = c.pend[i];
@@ -397,26 +455,6 @@ __global__ void k_commit(BuildCtx c, int nxt) {
         if (old == 1) push(c.front + (int64_t)nxt * c.M * c.N + base, c.nfront + nxt * c.M + m, dn, c.N, c.status);
         int32_t k = atomicAdd(c.nlag, 1);
         if (k < c.lag_cap) c.lagall[k] = e; else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
-    }
-}
-
-// End of a step: clear the consumed frontier and the pending list; count the
-// cells still to be processed.
-__global__ void k_step_end(BuildCtx c, int cur) {
-    __shared__ unsigned long long rem;
-    if (threadIdx.x == 0) rem = 0;
-    __syncthreads();
-    unsigned long long mine = 0;
-    for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) {
-        c.nfront[cur * c.M + m] = 0;
-        mine += (unsigned long long)(c.N - c.nproc[m]);
-    }
-    atomicAdd(&rem, mine);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *c.npend = 0;
-        c.status[2] = (int32_t)min(rem, (unsigned long long)INT_MAX);
-        c.status[3] += 1;
     }
 }
 
@@ -486,6 +524,32 @@ __global__ void k_lag_ptr(const int32_t *lm, int32_t T, int64_t M, int32_t *lag_
         int32_t prev = i == 0 ? -1 : lm[i - 1];
         int32_t cur = i == T ? (int32_t)M : lm[i];
         for (int32_t mm = prev + 1; mm <= cur; ++mm) lag_ptr[mm] = i;
+    }
+}
+
+// Octant-aligned schedule layers, one launch per level l (blockIdx.y = direction):
+// kappa(c) = max(floor(rho_o * lambda_o(c)), 1 + max kappa(active upwind cell)).
+// Upwind cells have smaller levels, so their kappa is final when c's level runs.
+__global__ void k_kappa_level(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
+                              const uint8_t *inm, const uint8_t *lagm, const int32_t *nbr, int FS, int64_t N,
+                              const int32_t *oct, const float *rho, const int32_t *lam, int32_t l, int32_t *kap) {
+    const int64_t m = blockIdx.y;
+    if (l >= nlev[m]) return;
+    const int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
+    const int o = oct[m];
+    const float r = rho[o];
+    const int64_t base = m * N;
+    for (int32_t pos = p0 + blockIdx.x * blockDim.x + threadIdx.x; pos < p1; pos += gridDim.x * blockDim.x) {
+        const int32_t c = order[base + pos];
+        int32_t k = (int32_t)(r * (float)lam[(int64_t)o * N + c]);
+        const unsigned act = (unsigned)inm[base + c] & ~(unsigned)lagm[base + c];
+        for (int q = 0; q < FS; ++q) {
+            if ((act >> q) & 1u) {
+                const int32_t u = nbr[(int64_t)c * FS + q];
+                if (u >= 0) k = max(k, kap[base + u] + 1);
+            }
+        }
+        kap[base + c] = k;
     }
 }
 
@@ -660,6 +724,122 @@ int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len,
     return JSWEEP_OK;
 }
 
+// Octant-aligned schedule layers (see jsweep_options.layering).  The levels
+// of the 8 diagonal directions come from a nested build over the same mesh.
+static int octant_layers(Dags *d, const uint8_t *inm, const uint8_t *lagm, const int64_t *lpoff_dev,
+                         const int32_t *nlev_dev, cudaStream_t s) {
+    const int64_t N = d->N, M = d->M;
+    // octant of every direction and the diagonal of each octant
+    std::vector<int32_t> oct(M);
+    for (int64_t m = 0; m < M; ++m) {
+        const double *o = d->quad->dirs.data() + 3 * m;
+        oct[m] = (o[0] < 0 ? 1 : 0) | (o[1] < 0 ? 2 : 0) | (o[2] < 0 ? 4 : 0);
+    }
+    Quad *dq = new Quad();
+    dq->M = 8;
+    std::vector<double> dd(24), dw(8, 1.0);
+    const double inv = 1.0 / std::sqrt(3.0);
+    for (int o = 0; o < 8; ++o) {
+        dd[3 * o] = (o & 1) ? -inv : inv;
+        dd[3 * o + 1] = (o & 2) ? -inv : inv;
+        dd[3 * o + 2] = (o & 4) ? -inv : inv;
+    }
+    dq->dirs = dd;
+    dq->w = dw;
+    int rc = dq->dirs64.alloc(24 * 8, s);
+    if (rc == JSWEEP_OK && cudaMemcpy(dq->dirs64.p, dd.data(), 24 * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = JSWEEP_ERR_CUDA;
+    if (rc != JSWEEP_OK) {
+        delete dq;
+        return rc;
+    }
+    Dags *dg = new Dags();
+    dg->mesh = d->mesh;
+    d->mesh->refs.fetch_add(1);
+    dg->quad = dq;  // owned by dg
+    dg->N = N;
+    dg->M = 8;
+    dg->opt = d->opt;
+    dg->opt.layering = JSWEEP_LAYERS_LEVEL;
+    rc = build_dags(dg, s);
+    if (rc != JSWEEP_OK) {
+        // the layering is only a schedule: keep the longest-path levels
+        delete dg;
+        clear_error();
+        return JSWEEP_OK;
+    }
+    std::vector<float> rho(8, 1.0f);
+    for (int o = 0; o < 8; ++o) {
+        int64_t lmax = 0;
+        for (int64_t m = 0; m < M; ++m)
+            if (oct[m] == o) lmax = std::max(lmax, d->nlevels[m]);
+        if (lmax > 0) rho[o] = (float)((double)lmax / (double)dg->nlevels[o]);
+    }
+    DevBuf oct_d, rho_d, kap, skeys, kmax;
+    JS_TRY(oct_d.alloc(M * 4, s));
+    JS_TRY(rho_d.alloc(8 * 4, s));
+    JS_TRY(kap.alloc(N * M * 4, s));
+    JS_CUDA(cudaMemcpyAsync(oct_d.p, oct.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(rho_d.p, rho.data(), 8 * 4, cudaMemcpyHostToDevice, s));
+    const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (256 * 64)), 8);
+    for (int64_t l = 0; l < d->Lmax; ++l) {
+        k_kappa_level<<<dim3(gx, (unsigned)M), 256, 0, s>>>(d->order.as<int32_t>(), d->lp.as<int32_t>(), lpoff_dev,
+                                                           nlev_dev, inm, lagm, d->mesh->nbr.as<int32_t>(),
+                                                           d->mesh->FS, N, oct_d.as<int32_t>(), rho_d.as<float>(),
+                                                           dg->level.as<int32_t>(), (int32_t)l, kap.as<int32_t>());
+        note_launches(1);
+    }
+    JS_CUDA(cudaGetLastError());
+    delete dg;
+    // layer counts, sort by (layer, cell id), layer pointers, mask in layer order
+    JS_TRY(kmax.alloc(M * 4, s));
+    JS_CUDA(cudaMemsetAsync(kmax.p, 0xff, M * 4, s));
+    k_level_max<<<dim3(std::min<int64_t>(64, (N + 255) / 256), (unsigned)M), 256, 0, s>>>(kap.as<int32_t>(), N, M,
+                                                                                         kmax.as<int32_t>());
+    JS_LAUNCH_CHECK();
+    std::vector<int32_t> km(M);
+    JS_CUDA(cudaMemcpyAsync(km.data(), kmax.p, M * 4, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> nl(M), off(M + 1, 0);
+    int64_t smax = 0;
+    for (int64_t m = 0; m < M; ++m) {
+        nl[m] = (int64_t)km[m] + 1;
+        smax = std::max(smax, nl[m]);
+        off[m + 1] = off[m] + nl[m] + 1;
+    }
+    if (smax >= (1ll << 24)) return JSWEEP_OK;  // keep levels
+    int key_bits = 1;
+    while ((1ll << key_bits) < smax) ++key_bits;
+    JS_TRY(d->korder.alloc(N * M * 4, s));
+    JS_TRY(skeys.alloc(N * M * 4, s));
+    JS_TRY(radix_sort_segments(reinterpret_cast<const uint32_t *>(kap.p), M, N, key_bits, nullptr,
+                               d->korder.as<int32_t>(), skeys.as<uint32_t>(), s));
+    DevBuf off_d, nl_d;
+    std::vector<int32_t> nl32(M);
+    for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)nl[m];
+    JS_TRY(off_d.alloc((M + 1) * 8, s));
+    JS_TRY(nl_d.alloc(M * 4, s));
+    JS_CUDA(cudaMemcpyAsync(off_d.p, off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(nl_d.p, nl32.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_TRY(d->klp.alloc(off[M] * 4, s));
+    k_level_ptr<<<dim3(std::min<int64_t>(64, (N + 255) / 256), (unsigned)M), 256, 0, s>>>(
+        skeys.as<uint32_t>(), N, M, off_d.as<int64_t>(), nl_d.as<int32_t>(), d->klp.as<int32_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(d->kmask.alloc(N * M, s));
+    k_mask_level_order<<<grid_for(N * M, 256, 152 * 64), 256, 0, s>>>(inm, lagm, d->korder.as<int32_t>(), N, M,
+                                                                      d->kmask.as<uint8_t>());
+    JS_LAUNCH_CHECK();
+    JS_CUDA(cudaStreamSynchronize(s));
+    d->layering = JSWEEP_LAYERS_OCTANT;
+    d->s_order = d->korder.as<int32_t>();
+    d->s_mask = d->kmask.as<uint8_t>();
+    d->s_lp = d->klp.as<int32_t>();
+    d->slayers = nl;
+    d->sp_off = off;
+    d->Smax = smax;
+    return JSWEEP_OK;
+}
+
 int build_dags(Dags *d, cudaStream_t s) {
     Mesh *mesh = d->mesh;
     Quad *quad = d->quad;
@@ -669,11 +849,12 @@ int build_dags(Dags *d, cudaStream_t s) {
     JS_CUDA(cudaEventRecord(d->ev[0], s));
 
     // ---- scratch
-    DevBuf cnt, stamp, claim, inm, outm, lagm, front, cand, small, pend, lagall;
+    DevBuf cnt, stamp, claim, wclaim, inm, outm, lagm, front, cand, small, pend, lagall;
     JS_TRY(d->level.alloc(MN * 4, s));
     JS_TRY(cnt.alloc(MN * 4, s));
     JS_TRY(stamp.alloc(MN * 4, s));
     JS_TRY(claim.alloc(MN * 4, s));
+    JS_TRY(wclaim.alloc(MN * 8, s));
     JS_TRY(inm.alloc(MN, s));
     JS_TRY(outm.alloc(MN, s));
     JS_TRY(lagm.alloc(MN, s));
@@ -699,6 +880,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.lvl = d->level.as<int32_t>();
     c.stamp = stamp.as<int32_t>();
     c.claim = claim.as<int32_t>();
+    c.wclaim = wclaim.as<unsigned long long>();
     c.inm = inm.as<uint8_t>();
     c.outm = outm.as<uint8_t>();
     c.lagm = lagm.as<uint8_t>();
@@ -721,6 +903,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     JS_CUDA(cudaMemsetAsync(c.lvl, 0xff, MN * 4, s));
     JS_CUDA(cudaMemsetAsync(c.stamp, 0, MN * 4, s));
     JS_CUDA(cudaMemsetAsync(c.claim, 0, MN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.wclaim, 0, MN * 8, s));
     JS_CUDA(cudaMemsetAsync(c.lagm, 0, MN, s));
     JS_CUDA(cudaMemsetAsync(sm, 0, n_small * 4, s));
     {
@@ -733,13 +916,12 @@ int build_dags(Dags *d, cudaStream_t s) {
 
     // ---- frontier loop with stall resolution
     const int B = d->opt.cycle_search_max;
-    const int walk_max = 4 * B + 64;
+    const int walk_max = 1 << 15;
     const size_t shmem = (size_t)kResolveWarps * (2 * B + (B + 3) / 4) * 4;
-    if (shmem > 48 * 1024)
-        JS_CUDA(cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    JS_CUDA(cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
     const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (256 * 32)), 16);
     const int64_t max_steps = 4 * N + 1024;
-    int32_t status[4] = {0, 0, 1, 0};
+    int32_t status[8] = {0, 0, 1, 0, 0, 0, 0, 0};
     int64_t step = 0;
     const int check_every = 8;
     int32_t last_remaining = -1;
@@ -748,13 +930,12 @@ int build_dags(Dags *d, cudaStream_t s) {
         int cur = (int)(step & 1);
         k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
         k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B, walk_max);
-        k_commit<<<64, 256, 0, s>>>(c, cur ^ 1);
-        k_step_end<<<1, 256, 0, s>>>(c, cur);
-        note_launches(3);  // peel, resolve, commit; the check below counts step_end
+        k_commit<<<64, 256, 0, s>>>(c, cur ^ 1, cur);
+        note_launches(2);  // peel, resolve; the check below counts commit
         JS_LAUNCH_CHECK();
         ++step;
         if (step % check_every == 0) {
-            JS_CUDA(cudaMemcpyAsync(status, c.status, 16, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaMemcpyAsync(status, c.status, 32, cudaMemcpyDeviceToHost, s));
             JS_CUDA(cudaStreamSynchronize(s));
             if (status[0] != 0) {
                 if (status[0] == JSWEEP_ERR_CYCLE)
@@ -857,9 +1038,25 @@ int build_dags(Dags *d, cudaStream_t s) {
     JS_LAUNCH_CHECK();
     std::vector<int32_t> lp32(M + 1);
     JS_CUDA(cudaMemcpyAsync(lp32.data(), d->lag_ptr.p, (M + 1) * 4, cudaMemcpyDeviceToHost, s));
-    JS_CUDA(cudaEventRecord(d->ev[1], s));
     JS_CUDA(cudaStreamSynchronize(s));
     d->lag_ptr_h.assign(lp32.begin(), lp32.end());
+    d->timing.build_steps = step;
+    d->timing.build_stall_rounds = status[4];
+
+    // ---- schedule layering
+    d->layering = JSWEEP_LAYERS_LEVEL;
+    d->s_order = d->order.as<int32_t>();
+    d->s_mask = d->mask.as<uint8_t>();
+    d->s_lp = d->lp.as<int32_t>();
+    d->slayers = d->nlevels;
+    d->sp_off = d->lp_off;
+    d->Smax = d->Lmax;
+    if (d->opt.layering == JSWEEP_LAYERS_OCTANT) {
+        int rc = octant_layers(d, c.inm, c.lagm, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), s);
+        if (rc != JSWEEP_OK) return rc;
+    }
+    JS_CUDA(cudaEventRecord(d->ev[1], s));
+    JS_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]);
     d->timing.build_ms = ms;

@@ -140,92 +140,156 @@ __device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *
     return (lo < lag_ptr[m + 1] && lag_face[lo] == f) ? lo : -1;
 }
 
-template <class T, int R>
-__device__ __forceinline__ void solve_cell(const SweepArgs<T> &a, int m, int64_t pos) {
-    const int64_t idx = (int64_t)m * a.N + pos;
-    const int c = a.order[idx];
-    const unsigned msk = a.mask[idx];
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Per-cell geometry and bookkeeping shared by the sweep kernels.
+template <class T, int MAXF> struct CellGeo {
+    typename V4<T>::type g[MAXF];
+};
+
+// One (cell, direction) for RH = R / SPLIT right-hand sides, sub-range `sub`
+// (SPLIT lanes cooperate on one cell so that each lane moves 16-byte pieces
+// and a 32-byte sector is read by one warp instruction).  MAXF >= faces per
+// cell; the face loop is unrolled so that the geometry loads of all faces, and
+// then the upwind loads of all incoming faces, are in flight together.
+// WAIT: before reading an upwind cell's psi, spin (bounded) until that cell's
+// flag for this direction shows the current sweep epoch (data-driven schedule).
+template <class T, int R, int SPLIT, int MAXF, bool WAIT>
+__device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
+                                           const int *flags, int want, int *err, long long timeout) {
+    using V = typename V4<T>::type;
+    constexpr int RH = R / SPLIT;
     const T ox = a.dirs[4 * m], oy = a.dirs[4 * m + 1], oz = a.dirs[4 * m + 2];
-    T num[R];
-    load_ro<T, R>(a.srcv + (int64_t)c * R, num);
-    T den = a.sigv[c];
-    const typename V4<T>::type *g = a.geo + (int64_t)c * a.FS;
-#pragma unroll 1
-    for (int k = 0; k < a.FS; ++k) {
-        typename V4<T>::type gk = g[k];
-        T d = ox * gk.x + oy * gk.y + oz * gk.z;
+    const V *g = a.geo + (int64_t)c * a.FS;
+    V gk[MAXF];
+#pragma unroll
+    for (int k = 0; k < MAXF; ++k) {
+        if (k < a.FS) gk[k] = g[k];
+        else gk[k] = V{T(0), T(0), T(0), T(0)};
+    }
+    T num[RH];
+    load_ro<T, RH>(a.srcv + (int64_t)c * R + sub * RH, num);
+    T den = __ldg(a.sigv + c);
+    // lagged faces (rare): bit k set when face slot k takes the previous sweep's value
+    unsigned lagk = 0;
+    int lagj[MAXF];
+    if (msk & 0x80u) {
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            lagj[k] = -1;
+            if (((msk >> k) & 1u) && nbr_bits<T>(gk[k]) >= 0) {
+                int j = lag_index(a.lag_ptr, a.lag_face, m, a.sface[(int64_t)c * a.FS + k] >> 1);
+                lagj[k] = j;
+                if (j >= 0) lagk |= 1u << k;
+            }
+        }
+    }
+    if constexpr (WAIT) {
+        // wait until every active interior upwind cell of this direction is done
+        const int *fm = flags + (int64_t)m * a.N;
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            const int nb = nbr_bits<T>(gk[k]);
+            if (((msk >> k) & 1u) && !((lagk >> k) & 1u) && nb >= 0) {
+                if (ld_acquire(fm + nb) != want) {
+                    const long long t0 = clock64();
+                    int ns = 32;
+                    while (ld_acquire(fm + nb) != want) {
+                        if (ld_volatile(err) != 0) return false;
+                        if (clock64() - t0 > timeout) {
+                            atomicCAS(err, 0, 1);
+                            return false;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 1024 ? 2 * ns : 1024;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MAXF; ++k) {
+        const T d = ox * gk[k].x + oy * gk[k].y + oz * gk[k].z;
         if ((msk >> k) & 1u) {
-            T wf = fabs(d);
-            int nb = nbr_bits<T>(gk);
-            T up[R];
+            const T wf = fabs(d);
+            const int nb = nbr_bits<T>(gk[k]);
+            T up[RH];
             if (nb >= 0) {
-                int j = -1;
-                if (msk & 0x80u) j = lag_index(a.lag_ptr, a.lag_face, m, a.sface[(int64_t)c * a.FS + k] >> 1);
-                if (j >= 0) {
-                    load_ro<T, R>(a.psi_lag + (int64_t)j * R, up);
+                if ((lagk >> k) & 1u) {
+                    load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
                 } else {
-                    load_cg<T, R>(a.psi + ((int64_t)m * a.N + nb) * R, up);
+                    load_cg<T, RH>(a.psi + ((int64_t)m * a.N + nb) * R + sub * RH, up);
                 }
             } else {
-                int b = -nb - 1;
+                const int b = -nb - 1;
 #pragma unroll
-                for (int r = 0; r < R; ++r) up[r] = a.inflow ? a.inflow[(int64_t)r * a.Fb + b] : T(0);
+                for (int r = 0; r < RH; ++r)
+                    up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) num[r] = num[r] + wf * up[r];
+            for (int r = 0; r < RH; ++r) num[r] = num[r] + wf * up[r];
         } else {
             den += d > T(0) ? d : T(0);
         }
     }
-    T out[R];
+    T out[RH];
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[r] = num[r] / den;
-    store_cg<T, R>(a.psi + ((int64_t)m * a.N + c) * R, out);
+    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
+    store_cg<T, RH>(a.psi + ((int64_t)m * a.N + c) * R + sub * RH, out);
+    return true;
 }
 
-template <class T, int R>
+// Level-synchronous sweep: one launch per time slot; a warp handles one unit
+// of 32 / SPLIT cells.
+template <class T, int R, int SPLIT, int MAXF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T> a, int64_t u0, int64_t nu) {
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (t >= nu) return;
     const int4 u = a.units[u0 + t];
-    if (lane < u.z) solve_cell<T, R>(a, u.x, (int64_t)u.y + lane);
+    const int cell = lane / SPLIT, sub = lane % SPLIT;
+    if (cell < u.z) {
+        const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
+        solve_cell<T, R, SPLIT, MAXF, false>(a, u.x, __ldg(a.order + idx), __ldg(a.mask + idx), sub, nullptr, 0,
+                                             nullptr, 0);
+    }
 }
 
-template <class T, int R>
+// Data-driven sweep (Listing 1's readiness, per cell): units are taken in
+// schedule order, unit t by resident warp t mod W; each cell waits only for
+// its own upwind cells' flags, then publishes its psi and its flag with
+// release ordering.  The schedule is a topological order of every
+// direction's graph, so the smallest unfinished unit always has its producers
+// done and its warp free: the sweep cannot deadlock while all W warps are
+// resident (the grid is sized from the occupancy calculator).
+template <class T, int R, int SPLIT, int MAXF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_sweep_persistent(SweepArgs<T> a, int64_t n_units, unsigned long long *ticket, int *done, int *err,
-                       long long timeout_cycles, int extra_wait) {
+    k_sweep_dd(SweepArgs<T> a, int64_t n_units, int *flags, int epoch, int want, int *err, long long timeout) {
     const int lane = threadIdx.x & 31;
-    while (true) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(ticket, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= (unsigned long long)n_units) break;
+    const int64_t W = (int64_t)gridDim.x * kWarpsPerBlock;
+    const int cell = lane / SPLIT, sub = lane % SPLIT;
+    for (int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); t < n_units; t += W) {
+        if (__shfl_sync(0xffffffffu, lane == 0 ? ld_volatile(err) : 0, 0) != 0) return;
         const int4 u = a.units[t];
-        int bad = 0;
-        if (lane == 0) {
-            const int *cnt = done + u.x;
-            const int target = u.w + (u.w > 0 ? extra_wait : 0);
-            if (ld_acquire(cnt) < target) {
-                const long long t0 = clock64();
-                while (ld_acquire(cnt) < target) {
-                    if (ld_volatile(err) != 0) { bad = 1; break; }
-                    if (clock64() - t0 > timeout_cycles) {
-                        atomicCAS(err, 0, 1);
-                        bad = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
+        bool ok = true;
+        int c = -1;
+        if (cell < u.z) {
+            const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
+            c = __ldg(a.order + idx);
+            ok = solve_cell<T, R, SPLIT, MAXF, true>(a, u.x, c, __ldg(a.mask + idx), sub, flags, want, err, timeout);
         }
-        bad = __shfl_sync(0xffffffffu, bad, 0);
-        if (bad) break;
-        if (lane < u.z) solve_cell<T, R>(a, u.x, (int64_t)u.y + lane);
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(done + u.x, 1);
+        if constexpr (SPLIT == 1) {
+            if (c >= 0 && ok) st_release(flags + (int64_t)u.x * a.N + c, epoch);
+        } else {
+            // the lanes of a cell publish together: each makes its own stores
+            // visible, then the first lane of the cell releases the flag
+            __threadfence();
+            __syncwarp();
+            if (c >= 0 && ok && sub == 0) st_release(flags + (int64_t)u.x * a.N + c, epoch);
+        }
+        if (__any_sync(0xffffffffu, !ok)) return;
     }
 }
 
@@ -396,21 +460,22 @@ int pad_rhs(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8
 }  // namespace
 
 // ---- unit tables ------------------------------------------------------------------------
-int ensure_units(Dags *d, int mode, cudaStream_t s) {
-    const int U = d->opt.cluster_cells;
-    const int prio = mode == JSWEEP_MODE_LEVEL_SYNC ? JSWEEP_PRIO_LEVEL : d->opt.priority;
-    int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Lmax / 4);
+int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
+    const int U = std::max(1, std::min(d->opt.cluster_cells, max_cells));
+    const int prio = d->opt.priority;
+    int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Smax / 4);
     if (prio != JSWEEP_PRIO_OCTANT) stagger = 0;
     UnitTable &ut = d->ut;
     if (ut.mode == mode && ut.priority == prio && ut.cluster == U && ut.stagger == stagger) return JSWEEP_OK;
-    const int64_t M = d->M, Lmax = d->Lmax;
+    // schedule layers (levels or octant-aligned layers) play the part of levels here
+    const int64_t M = d->M, Lmax = d->Smax;
     std::vector<int32_t> off(M, 0);
     for (int64_t m = 0; m < M; ++m) {
-        if (prio == JSWEEP_PRIO_DEPTH) off[m] = (int32_t)(Lmax - d->nlevels[m]);
+        if (prio == JSWEEP_PRIO_DEPTH) off[m] = (int32_t)(Lmax - d->slayers[m]);
         else if (prio == JSWEEP_PRIO_OCTANT) off[m] = (M % 8 == 0) ? (int32_t)((m / (M / 8)) * stagger) : 0;
     }
     int64_t Tmax = 0;
-    for (int64_t m = 0; m < M; ++m) Tmax = std::max<int64_t>(Tmax, d->nlevels[m] + off[m]);
+    for (int64_t m = 0; m < M; ++m) Tmax = std::max<int64_t>(Tmax, d->slayers[m] + off[m]);
     DevBuf ucnt, wscan, cnt2, base2, off_d, lpoff_d, nlev_d;
     JS_TRY(ucnt.alloc(M * Lmax * 8, s));
     JS_TRY(wscan.alloc(M * Lmax * 8, s));
@@ -420,12 +485,12 @@ int ensure_units(Dags *d, int mode, cudaStream_t s) {
     JS_TRY(lpoff_d.alloc((M + 1) * 8, s));
     JS_TRY(nlev_d.alloc(M * 4, s));
     std::vector<int32_t> nl32(M);
-    for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)d->nlevels[m];
+    for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)d->slayers[m];
     JS_CUDA(cudaMemcpyAsync(off_d.p, off.data(), M * 4, cudaMemcpyHostToDevice, s));
-    JS_CUDA(cudaMemcpyAsync(lpoff_d.p, d->lp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(lpoff_d.p, d->sp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
     JS_CUDA(cudaMemcpyAsync(nlev_d.p, nl32.data(), M * 4, cudaMemcpyHostToDevice, s));
     JS_CUDA(cudaMemsetAsync(cnt2.p, 0, Tmax * M * 8, s));
-    k_unit_counts<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->lp.as<int32_t>(), lpoff_d.as<int64_t>(),
+    k_unit_counts<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
                                                                 nlev_d.as<int32_t>(), M, Lmax, U, ucnt.as<int64_t>());
     JS_LAUNCH_CHECK();
     JS_TRY(scan_exclusive_i64(ucnt.as<int64_t>(), wscan.as<int64_t>(), M * Lmax, s));
@@ -438,14 +503,14 @@ int ensure_units(Dags *d, int mode, cudaStream_t s) {
     JS_CUDA(cudaMemcpyAsync(&last_base, base2.as<int64_t>() + Tmax * M - 1, 8, cudaMemcpyDeviceToHost, s));
     JS_CUDA(cudaMemcpyAsync(&last_cnt, cnt2.as<int64_t>() + Tmax * M - 1, 8, cudaMemcpyDeviceToHost, s));
     std::vector<int64_t> b2h;
-    if (mode == JSWEEP_MODE_LEVEL_SYNC) {
+    if (mode == JSWEEP_MODE_LEVEL_SYNC) {  // one launch per time slot t = level + offset(direction)
         b2h.resize(Tmax * M);
         JS_CUDA(cudaMemcpyAsync(b2h.data(), base2.p, Tmax * M * 8, cudaMemcpyDeviceToHost, s));
     }
     JS_CUDA(cudaStreamSynchronize(s));
     const int64_t n_units = last_base + last_cnt;
     JS_TRY(ut.units.alloc(std::max<int64_t>(n_units, 1) * 16, s));
-    k_unit_fill<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->lp.as<int32_t>(), lpoff_d.as<int64_t>(),
+    k_unit_fill<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
                                                               nlev_d.as<int32_t>(), ucnt.as<int64_t>(),
                                                               wscan.as<int64_t>(), base2.as<int64_t>(),
                                                               off_d.as<int32_t>(), M, Lmax, U, ut.units.as<int4>());
@@ -485,8 +550,8 @@ template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
     a.M = (int)d->M;
     a.FS = d->mesh->FS;
     a.Fb = (int)d->mesh->Fb;
-    a.order = d->order.as<int32_t>();
-    a.mask = d->mask.as<uint8_t>();
+    a.order = d->s_order;
+    a.mask = d->s_mask;
     if constexpr (sizeof(T) == 4) {
         a.geo = d->mesh->geo32.as<float4>();
         a.dirs = reinterpret_cast<const T *>(d->quad->dirs32.p);
@@ -549,9 +614,63 @@ int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s) {
     return JSWEEP_OK;
 }
 
+template <class T, int R> constexpr int split_of() {
+    return (int)(sizeof(T) * R / 16) > 1 ? (int)(sizeof(T) * R / 16) : 1;
+}
+
+template <class T, int R, int SPLIT, int MAXF>
+int launch_dd(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
+    auto kern = k_sweep_dd<T, R, SPLIT, MAXF>;
+    int bps = d->opt.blocks_per_sm;
+    int occ = 0;
+    JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarpsPerBlock * 32, 0));
+    if (occ < 1) occ = 1;
+    if (bps <= 0 || bps > occ) bps = occ;  // every warp must be resident
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (khz <= 0) khz = 2000000;
+    const long long timeout = (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
+    int64_t grid = (int64_t)device_sm_count() * bps;
+    const int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > maxg) grid = std::max<int64_t>(1, maxg);
+    // flags: one int per (direction, cell), stamped with the sweep epoch
+    const size_t fbytes = (size_t)d->M * d->N * 4;
+    if (!d->flags.p || d->flags.bytes < fbytes) {
+        JS_TRY(d->flags.alloc(fbytes, s));
+        JS_CUDA(cudaMemsetAsync(d->flags.p, 0, fbytes, s));
+        d->epoch = 0;
+    }
+    if (d->epoch >= INT32_MAX - 2) {
+        JS_CUDA(cudaMemsetAsync(d->flags.p, 0, fbytes, s));
+        d->epoch = 0;
+    }
+    const int epoch = ++d->epoch;
+    // debug_block_waits: wait for an epoch no sweep has written (test of the bounded-wait path)
+    const int want = d->opt.debug_block_waits ? epoch + 1 : epoch;
+    int *err = reinterpret_cast<int *>(d->counters.p);
+    JS_CUDA(cudaMemsetAsync(err, 0, 8, s));
+    kern<<<(unsigned)grid, kWarpsPerBlock * 32, 0, s>>>(a, d->ut.n_units, d->flags.as<int>(), epoch, want, err,
+                                                         timeout);
+    JS_LAUNCH_CHECK();
+    d->timing.sweep_launches = 1;
+    return JSWEEP_OK;
+}
+
+template <class T, int R, int SPLIT, int MAXF>
+void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs) {
+    const auto &sp = d->ut.slot_ptr;
+    for (size_t l = 0; l + 1 < sp.size(); ++l) {
+        const int64_t nu = sp[l + 1] - sp[l];
+        if (nu <= 0) continue;
+        const int64_t blocks = (nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        k_sweep_level<T, R, SPLIT, MAXF><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, cs>>>(a, sp[l], nu);
+    }
+}
+
 template <class T, int R>
 int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
-    const int64_t M = d->M;
+    constexpr int SPLIT = split_of<T, R>();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
         char key[512];
         snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%p/%lld", (int)sizeof(T), R, (const void *)a.srcv,
@@ -565,13 +684,9 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
             if (!d->capture_stream) JS_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
             cudaStream_t cs = d->capture_stream;
             JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            const auto &sp = d->ut.slot_ptr;
-            for (size_t l = 0; l + 1 < sp.size(); ++l) {
-                int64_t nu = sp[l + 1] - sp[l];
-                if (nu <= 0) continue;
-                int64_t blocks = (nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
-                k_sweep_level<T, R><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, cs>>>(a, sp[l], nu);
-            }
+            if (a.FS <= 4) capture_levels<T, R, SPLIT, 4>(d, a, cs);
+            else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6>(d, a, cs);
+            else capture_levels<T, R, SPLIT, 7>(d, a, cs);
             cudaGraph_t g;
             cudaError_t e = cudaStreamEndCapture(cs, &g);
             if (e != cudaSuccess) {
@@ -594,39 +709,15 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         d->timing.sweep_launches = nodes;
         return JSWEEP_OK;
     }
-    // persistent
-    unsigned long long *ticket = reinterpret_cast<unsigned long long *>(d->counters.p);
-    int *err = reinterpret_cast<int *>(ticket + 1);
-    int *done = err + 2;
-    JS_CUDA(cudaMemsetAsync(d->counters.p, 0, (size_t)(M + 8) * 8, s));
-    int bps = d->opt.blocks_per_sm;
-    if (bps <= 0) {
-        JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sweep_persistent<T, R>, kWarpsPerBlock * 32, 0));
-        if (bps < 1) bps = 1;
-    }
-    int dev = 0, khz = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-    if (khz <= 0) khz = 2000000;
-    long long timeout = (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
-    int64_t grid = (int64_t)device_sm_count() * bps;
-    int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (grid > maxg) grid = std::max<int64_t>(1, maxg);
-    // debug_block_waits: a wait for one unit more than its direction has makes
-    // every wait run out (test of the bounded-wait error path)
-    const int extra = d->opt.debug_block_waits ? (int)std::min<int64_t>(d->ut.n_units + 1, INT32_MAX / 2) : 0;
-    k_sweep_persistent<T, R><<<(unsigned)grid, kWarpsPerBlock * 32, 0, s>>>(a, d->ut.n_units, ticket, done, err,
-                                                                           timeout, extra);
-    JS_LAUNCH_CHECK();
-    d->timing.sweep_launches = 1;
-    return JSWEEP_OK;
+    if (a.FS <= 4) return launch_dd<T, R, SPLIT, 4>(d, a, s);
+    if (a.FS <= 6) return launch_dd<T, R, SPLIT, 6>(d, a, s);
+    return launch_dd<T, R, SPLIT, 7>(d, a, s);
 }
 
 int check_sweep_error(Dags *d, cudaStream_t s, int mode) {
     if (mode != JSWEEP_MODE_PERSISTENT) return JSWEEP_OK;
     int err = 0;
-    JS_CUDA(cudaMemcpyAsync(&err, reinterpret_cast<unsigned long long *>(d->counters.p) + 1, 4,
-                            cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaMemcpyAsync(&err, d->counters.p, 4, cudaMemcpyDeviceToHost, s));
     JS_CUDA(cudaStreamSynchronize(s));
     if (err) {
         set_error("persistent sweep: a dependency wait exceeded %.3g s", d->opt.spin_timeout_s);
@@ -668,7 +759,7 @@ template <class T, int R>
 static int run_sweep_t(Dags *d, int nrhs, const void *sigma_t, const void *ang_source, const void *inflow,
                        void *phi_out, void *psi_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, s));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
                                   : reinterpret_cast<const T *>(d->mesh->vol32.p);
@@ -705,7 +796,7 @@ template <class T, int R>
 static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, const void *q, const void *inflow,
                     double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, s));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
     JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)

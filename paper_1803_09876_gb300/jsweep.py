@@ -39,6 +39,9 @@ JSWEEP_MODE_AUTO = 0
 JSWEEP_MODE_LEVEL_SYNC = 1
 JSWEEP_MODE_PERSISTENT = 2
 
+JSWEEP_LAYERS_OCTANT = 0
+JSWEEP_LAYERS_LEVEL = 1
+
 JSWEEP_PRIO_LEVEL = 0
 JSWEEP_PRIO_DEPTH = 1
 JSWEEP_PRIO_OCTANT = 2
@@ -71,7 +74,8 @@ class jsweep_options(ctypes.Structure):
         ("spin_timeout_s", ctypes.c_double),
         ("cycle_search_max", ctypes.c_int),
         ("debug_block_waits", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("layering", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -83,6 +87,8 @@ class jsweep_timing(ctypes.Structure):
         ("sweep_launches", ctypes.c_int64),
         ("build_launches", ctypes.c_int64),
         ("call_launches", ctypes.c_int64),
+        ("build_steps", ctypes.c_int64),
+        ("build_stall_rounds", ctypes.c_int64),
     ]
 
 
@@ -308,7 +314,8 @@ class Dags:
         _check(lib().jsweep_dags_timing(self._h, ctypes.byref(t)))
         return {"build_ms": t.build_ms, "sweep_ms": t.sweep_ms, "phi_ms": t.phi_ms,
                 "sweep_launches": t.sweep_launches, "build_launches": t.build_launches,
-                "call_launches": t.call_launches}
+                "call_launches": t.call_launches, "build_steps": t.build_steps,
+                "build_stall_rounds": t.build_stall_rounds}
 
 
 def jsweep_mesh_create(n_cells, n_faces, face_cells, normals, areas, volumes) -> Mesh:
