@@ -224,6 +224,36 @@ int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const voi
                           int max_iters, void *phi_out, int *iters_out, double *resid_out,
                           void *stream);
 
+/* ---- source iteration that allocates no device memory ----------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory while they run: for example a host application
+ * that owns and budgets all of the device's memory through its own runtime, or a
+ * latency-critical solve loop where the device-wide synchronisation of
+ * cudaMalloc / cudaFree is not acceptable.
+ * Same arguments, arithmetic and results as jsweep_source_iterate (level-by-level
+ * schedule), but every temporary (psi, sources, lagged values, phi iterates,
+ * residual accumulators) lives in one fixed device array of
+ * JSWEEP_NOALLOC_SCRATCH_BYTES that the library defines at file scope; every GPU
+ * that loads the library holds that array until the process exits.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine) and
+ * does not touch the handle's own sweep workspaces or lagged values.
+ *   - Problems whose temporaries exceed the array are rejected with
+ *     JSWEEP_ERR_INVALID_ARG (the message gives the bytes needed): roughly
+ *     directions x cells x padded right-hand sides x element size must stay
+ *     below 64 MiB (e.g. 4,096 cells x 96 directions x 1 rhs in FP64 fits).
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents (each
+ *     call zeroes what must start at zero), so calls that overlap on the GPU
+ *     (different streams or threads) race: serialise them.
+ *   - The handle must have been built (jsweep_build_dags); its level arrays,
+ *     lag lists, mesh and directions are read, never written. */
+#define JSWEEP_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int jsweep_source_iterate_noalloc(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+                                  const void *c_ratio, const void *q, const void *inflow, double tol,
+                                  int max_iters, void *phi_out, int *iters_out, double *resid_out,
+                                  void *stream);
+
 /* ---- timing of the last sweep call on a handle (phase breakdown, Sec. VI-C) */
 typedef struct {
     double build_ms;        /* last jsweep_build_dags: device time of the whole build */

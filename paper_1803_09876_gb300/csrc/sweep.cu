@@ -32,6 +32,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -898,4 +899,254 @@ int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const
 #undef JS_SI
 }
 
+// ---- source iteration without device allocations ----------------------------------
+// Some callers cannot allocate device memory once they are running: for example
+// a host application that hands this library a device whose memory is entirely
+// owned and budgeted by its own runtime, or a latency-critical solve loop in
+// which the device-wide synchronisation of cudaMalloc/cudaFree is not
+// acceptable.  jsweep_source_iterate_noalloc serves them: every temporary it
+// needs lives in one fixed, file-scope device array (kNoallocScratchBytes),
+// which every GPU that loads this library holds until the process exits.
+constexpr size_t kNoallocScratchBytes = JSWEEP_NOALLOC_SCRATCH_BYTES;
+
+namespace {
+
+// Sweep of one level for every direction, reading the level pointers directly
+// (no work-unit table, which would have to be allocated).
+template <class T, int R, int SPLIT, int MAXF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sweep_level_na(SweepArgs<T> a, const int32_t *lp, const int64_t *lp_off, const int64_t *nlev, int32_t l) {
+    const int64_t m = blockIdx.y;
+    if (l >= nlev[m]) return;
+    const int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
+    constexpr int CPW = 32 / SPLIT;
+    const int lane = threadIdx.x & 31, cell = lane / SPLIT, sub = lane % SPLIT;
+    const int32_t wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int32_t stride = gridDim.x * kWarpsPerBlock * CPW;
+    for (int32_t pos = p0 + wid * CPW + cell; pos < p1; pos += stride) {
+        const int64_t idx = m * a.N + pos;
+        solve_cell<T, R, SPLIT, MAXF, false>(a, (int)m, __ldg(a.order + idx), __ldg(a.mask + idx), sub, nullptr, 0,
+                                             nullptr, 0);
+    }
+}
+
+__global__ void k_pad_dirs(const double *d3, int64_t M, double *d4) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        d4[4 * m] = d3[3 * m];
+        d4[4 * m + 1] = d3[3 * m + 1];
+        d4[4 * m + 2] = d3[3 * m + 2];
+        d4[4 * m + 3] = 0.0;
+    }
+}
+
+}  // namespace
+
 }  // namespace js
+
+// The scratch array (file scope, internal linkage).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[js::kNoallocScratchBytes];
+
+namespace js {
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device: looked up once
+// per device, with that device current.
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    JS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d not supported", dev);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+            return JSWEEP_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return JSWEEP_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <class T, int R>
+int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, const void *q, const void *inflow,
+                 double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
+    constexpr int SPLIT = split_of<T, R>();
+    const int64_t N = d->N, M = d->M;
+    const int64_t Tl = std::max<int64_t>(d->T, 1);
+    // scratch layout
+    size_t off = 0;
+    const size_t o_psi = off;   off = align256(off + (size_t)M * N * R * sizeof(T));
+    const size_t o_src = off;   off = align256(off + (size_t)N * R * sizeof(T));
+    const size_t o_sig = off;   off = align256(off + (size_t)N * sizeof(T));
+    const size_t o_lag = off;   off = align256(off + (size_t)Tl * R * sizeof(T));
+    const size_t o_phi0 = off;  off = align256(off + (size_t)nrhs * N * sizeof(T));
+    const size_t o_phi1 = off;  off = align256(off + (size_t)nrhs * N * sizeof(T));
+    const size_t o_inf = off;   off = align256(off + (size_t)std::max<int64_t>(d->mesh->Fb, 1) * R * sizeof(T));
+    const size_t o_dirs = off;  off = align256(off + (size_t)M * 4 * sizeof(double));
+    const size_t o_lpoff = off; off = align256(off + (size_t)(M + 1) * 8);
+    const size_t o_nlev = off;  off = align256(off + (size_t)M * 8);
+    const size_t o_acc = off;   off = align256(off + 32 * 8 + 16 * 8);
+    if (off > kNoallocScratchBytes) {
+        set_error("jsweep_source_iterate_noalloc: this problem needs %zu bytes of scratch, more than the %zu-byte "
+                  "fixed array (directions x cells x right-hand sides is too large)",
+                  off, kNoallocScratchBytes);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    void *base = nullptr;
+    JS_TRY(noalloc_scratch(&base));
+    char *b = static_cast<char *>(base);
+    T *psi = reinterpret_cast<T *>(b + o_psi);
+    T *srcv = reinterpret_cast<T *>(b + o_src);
+    T *sigv = reinterpret_cast<T *>(b + o_sig);
+    T *lag = reinterpret_cast<T *>(b + o_lag);
+    T *phis[2] = {reinterpret_cast<T *>(b + o_phi0), reinterpret_cast<T *>(b + o_phi1)};
+    T *infl = reinterpret_cast<T *>(b + o_inf);
+    double *d4 = reinterpret_cast<double *>(b + o_dirs);
+    int64_t *lpoff = reinterpret_cast<int64_t *>(b + o_lpoff);
+    int64_t *nlev = reinterpret_cast<int64_t *>(b + o_nlev);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(b + o_acc);
+    double *resid_d = reinterpret_cast<double *>(acc + 32);
+
+    // what must start at zero: the lagged values (and the padded inflow rows)
+    JS_CUDA(cudaMemsetAsync(lag, 0, (size_t)Tl * R * sizeof(T), s));
+    if (inflow) {
+        JS_CUDA(cudaMemsetAsync(infl, 0, (size_t)std::max<int64_t>(d->mesh->Fb, 1) * R * sizeof(T), s));
+        JS_CUDA(cudaMemcpyAsync(infl, inflow, (size_t)nrhs * d->mesh->Fb * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    JS_CUDA(cudaMemcpyAsync(lpoff, d->lp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(nlev, d->nlevels.data(), M * 8, cudaMemcpyHostToDevice, s));
+    SweepArgs<T> a;
+    a.N = N;
+    a.M = (int)M;
+    a.FS = d->mesh->FS;
+    a.Fb = (int)d->mesh->Fb;
+    a.order = d->order.as<int32_t>();
+    a.mask = d->mask.as<uint8_t>();
+    if constexpr (sizeof(T) == 4) {
+        a.geo = d->mesh->geo32.as<float4>();
+        a.dirs = reinterpret_cast<const T *>(d->quad->dirs32.p);
+    } else {
+        a.geo = d->mesh->geo64.as<double4>();
+        k_pad_dirs<<<grid_for(M, 256), 256, 0, s>>>(d->quad->dirs64.as<double>(), M, d4);
+        JS_LAUNCH_CHECK();
+        a.dirs = reinterpret_cast<const T *>(d4);
+    }
+    a.srcv = srcv;
+    a.sigv = sigv;
+    a.inflow = inflow ? infl : nullptr;
+    a.psi = psi;
+    a.psi_lag = lag;
+    a.lag_ptr = d->lag_ptr.as<int32_t>();
+    a.lag_face = d->lag_face.as<int32_t>();
+    a.sface = d->mesh->sface.as<int32_t>();
+    a.units = nullptr;
+    const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
+                                  : reinterpret_cast<const T *>(d->mesh->vol32.p);
+    const T *w = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->quad->w64.p)
+                                : reinterpret_cast<const T *>(d->quad->w32.p);
+    const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (kWarpsPerBlock * (32 / SPLIT) * 16)), 32);
+    T *phi_old = nullptr, *phi_new = phis[0];
+    double resid_h[9] = {0};
+    bool conv = false;
+    int it = 0;
+    for (it = 1; it <= max_iters; ++it) {
+        phi_new = phis[(it - 1) & 1];
+        k_emission<T, R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>((const T *)sigma_t, (const T *)c_ratio,
+                                                                    (const T *)q, phi_old, vol, N, nrhs, srcv, sigv);
+        JS_LAUNCH_CHECK();
+        for (int64_t l = 0; l < d->Lmax; ++l) {
+            if (a.FS <= 4)
+                k_sweep_level_na<T, R, SPLIT, 4><<<dim3(gx, (unsigned)M), kWarpsPerBlock * 32, 0, s>>>(
+                    a, d->lp.as<int32_t>(), lpoff, nlev, (int32_t)l);
+            else if (a.FS <= 6)
+                k_sweep_level_na<T, R, SPLIT, 6><<<dim3(gx, (unsigned)M), kWarpsPerBlock * 32, 0, s>>>(
+                    a, d->lp.as<int32_t>(), lpoff, nlev, (int32_t)l);
+            else
+                k_sweep_level_na<T, R, SPLIT, 7><<<dim3(gx, (unsigned)M), kWarpsPerBlock * 32, 0, s>>>(
+                    a, d->lp.as<int32_t>(), lpoff, nlev, (int32_t)l);
+            JS_LAUNCH_CHECK();
+        }
+        if (d->T > 0) {
+            k_lag_update<T, R><<<grid_for(d->T, 256), 256, 0, s>>>(psi, d->lag_m.as<int32_t>(), d->lag_up.as<int32_t>(),
+                                                                  d->T, N, lag);
+            JS_LAUNCH_CHECK();
+        }
+        k_phi<T, R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(psi, w, N, (int)M, nrhs, phi_new);
+        JS_LAUNCH_CHECK();
+        JS_CUDA(cudaMemsetAsync(acc, 0, 2 * 8 * 8, s));
+        k_resid<T><<<dim3(grid_for(N, 256, 152 * 4), nrhs), 256, 0, s>>>(phi_new, phi_old, N, acc);
+        JS_LAUNCH_CHECK();
+        k_resid_final<<<1, 32, 0, s>>>(acc, nrhs, resid_d);
+        JS_LAUNCH_CHECK();
+        JS_CUDA(cudaMemcpyAsync(resid_h, resid_d, (nrhs + 1) * 8, cudaMemcpyDeviceToHost, s));
+        JS_CUDA(cudaStreamSynchronize(s));
+        phi_old = phi_new;
+        if (resid_h[nrhs] < tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (it > max_iters) it = max_iters;
+    JS_CUDA(cudaMemcpyAsync(phi_out, phi_new, (size_t)nrhs * N * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    if (iters_out) *iters_out = it;
+    if (resid_out) *resid_out = resid_h[nrhs];
+    if (!conv) {
+        set_error("source iteration did not reach tol %g in %d iterations (residual %g)", tol, max_iters,
+                  resid_h[nrhs]);
+        return JSWEEP_ERR_NOT_CONVERGED;
+    }
+    return JSWEEP_OK;
+}
+
+}  // namespace
+}  // namespace js
+
+extern "C" int jsweep_source_iterate_noalloc(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+                                             const void *c_ratio, const void *q, const void *inflow, double tol,
+                                             int max_iters, void *phi_out, int *iters_out, double *resid_out,
+                                             void *stream) {
+    using namespace js;
+    clear_error();
+    if (!dags || !sigma_t || !c_ratio || !q || !phi_out) {
+        set_error("jsweep_source_iterate_noalloc: NULL argument");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    if (nrhs < 1 || nrhs > 8 || (precision != JSWEEP_F64 && precision != JSWEEP_F32)) {
+        set_error("jsweep_source_iterate_noalloc: nrhs=%d precision=%d", nrhs, precision);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    if (!(tol >= 0.0) || max_iters < 1) {
+        set_error("jsweep_source_iterate_noalloc: tol=%g max_iters=%d", tol, max_iters);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    Dags *d = impl(dags);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Rp = nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8;
+#define JS_NA(T, R) si_noalloc_t<T, R>(d, nrhs, sigma_t, c_ratio, q, inflow, tol, max_iters, phi_out, iters_out, resid_out, s)
+    if (precision == JSWEEP_F64) {
+        switch (Rp) {
+            case 1: return JS_NA(double, 1);
+            case 2: return JS_NA(double, 2);
+            case 4: return JS_NA(double, 4);
+            default: return JS_NA(double, 8);
+        }
+    }
+    switch (Rp) {
+        case 1: return JS_NA(float, 1);
+        case 2: return JS_NA(float, 2);
+        case 4: return JS_NA(float, 4);
+        default: return JS_NA(float, 8);
+    }
+#undef JS_NA
+}

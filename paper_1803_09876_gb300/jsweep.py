@@ -54,6 +54,7 @@ EXPORTED = [
     "jsweep_build_dags", "jsweep_dags_destroy", "jsweep_dags_info", "jsweep_dags_nlevels",
     "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
     "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
+    "jsweep_source_iterate_noalloc",
 ]
 
 
@@ -150,6 +151,7 @@ def load(path: str = LIB_PATH):
             "jsweep_sweep": (I, [P, I, I, P, P, P, P, P, P]),
             "jsweep_source_iterate": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
             "jsweep_dags_timing": (I, [P, P]),
+            "jsweep_source_iterate_noalloc": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -407,4 +409,35 @@ def jsweep_source_iterate(dags: Dags, sigma_t, c_ratio, q, inflow=None, tol=1e-8
     if rc == JSWEEP_ERR_NOT_CONVERGED and allow_not_converged:
         return phi_out, it.value, res.value, False
     _check(rc, "jsweep_source_iterate")
+    return phi_out, it.value, res.value, True
+
+
+JSWEEP_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def jsweep_source_iterate_noalloc(dags: Dags, sigma_t, c_ratio, q, phi_out, inflow=None, tol=1e-8,
+                                  max_iters=1000, stream=None, allow_not_converged=False):
+    """Source iteration that allocates no device memory (jsweep_source_iterate_noalloc).
+
+    For callers that cannot allocate device memory while they run (a host
+    application that owns the device's memory budget, or a loop that cannot
+    afford cudaMalloc's device-wide synchronisation): all temporaries live in
+    the library's fixed JSWEEP_NOALLOC_SCRATCH_BYTES device array.  The caller
+    passes every input and the output ``phi_out`` [R, N]; nothing here
+    allocates on the device.  Calls share that array, so calls that overlap on
+    the GPU must be serialised.  Returns (phi_out, iterations, residual, converged).
+    """
+    N, Fb = dags.n_cells, dags.mesh.n_bfaces
+    R = q.shape[0] if q.dim() == 2 else 1
+    dt = q.dtype
+    prec = _prec(dt)
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    rc = lib().jsweep_source_iterate_noalloc(
+        dags._h, R, prec, _dptr(sigma_t, dt, N, "sigma_t"), _dptr(c_ratio, dt, N, "c_ratio"),
+        _dptr(q, dt, R * N, "q"), _dptr(inflow, dt, R * Fb, "inflow"), float(tol), int(max_iters),
+        _dptr(phi_out, dt, R * N, "phi_out"), ctypes.byref(it), ctypes.byref(res), _stream(stream))
+    if rc == JSWEEP_ERR_NOT_CONVERGED and allow_not_converged:
+        return phi_out, it.value, res.value, False
+    _check(rc, "jsweep_source_iterate_noalloc")
     return phi_out, it.value, res.value, True
