@@ -97,7 +97,11 @@ typedef struct {
                               the waits run out and the call returns JSWEEP_ERR_DEVICE_TIMEOUT */
     int layering;          /* schedule layers (set at jsweep_build_dags): JSWEEP_LAYERS_OCTANT (default)
                               or JSWEEP_LAYERS_LEVEL; results do not depend on it */
-    int reserved[6];
+    int unit_order;        /* order of the work units inside a layer: 0 = direction by direction,
+                              1 = interleaved across the directions of an octant (default), so that
+                              units covering the same cells for different directions run side by side
+                              and share the cells' geometry and sources in cache */
+    int reserved[5];
 } jsweep_options;
 
 /* Fill *opt with defaults. */
@@ -264,6 +268,9 @@ typedef struct {
     int64_t call_launches;  /* kernels launched by the last jsweep_sweep / jsweep_source_iterate */
     int64_t build_steps;    /* frontier steps of the last build (about the largest level count) */
     int64_t build_stall_rounds; /* cycle-resolution rounds of the last build, summed over directions */
+    double build_phase_ms[6];   /* last build, device time per phase: [0] octant diagonals, [1] set-up and
+                                   face classification, [2] frontier steps with cycle resolution,
+                                   [3] level-major order, [4] lag lists, [5] schedule layers */
 } jsweep_timing;
 int jsweep_dags_timing(jsweep_dags_t dags, jsweep_timing *t);
 

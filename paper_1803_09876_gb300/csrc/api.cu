@@ -167,6 +167,7 @@ int jsweep_options_default(jsweep_options *opt) {
     opt->octant_stagger = 0;
     opt->spin_timeout_s = 2.0;
     opt->cycle_search_max = 256;
+    opt->unit_order = 1;
     return JSWEEP_OK;
 }
 
@@ -253,9 +254,11 @@ int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cel
         if (nf[c] > FS) FS = nf[c];
     }
     // slots per cell, faces in increasing id
+    // geometry records padded to 4 or 8 slots: a hexahedron's record is one 128-byte line (FP32)
+    const int GS = FS <= 4 ? 4 : 8;
     std::vector<int32_t> sface(N * FS, -1), nbr(N * FS, INT32_MIN);
-    std::vector<float> geo32(N * FS * 4, 0.0f);
-    std::vector<double> geo64(N * FS * 4, 0.0);
+    std::vector<float> geo32(N * GS * 4, 0.0f);
+    std::vector<double> geo64(N * GS * 4, 0.0);
     std::vector<int> fill(N, 0);
     int64_t b = 0;
     for (int64_t f = 0; f < F; ++f) {
@@ -267,27 +270,29 @@ int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cel
             if (c < 0) continue;
             int k = fill[c]++;
             int64_t slot = c * FS + k;
+            int64_t gslot = c * GS + k;
             sface[slot] = (int32_t)((f << 1) | side);
             int32_t nb = side == 0 ? (c1 >= 0 ? (int32_t)c1 : -(bid + 1)) : (int32_t)c0;
             nbr[slot] = nb;
             double sg = side == 0 ? 1.0 : -1.0;
             for (int k3 = 0; k3 < 3; ++k3) {
                 double av = sg * areas[f] * normals[3 * f + k3];
-                geo64[4 * slot + k3] = av;
-                geo32[4 * slot + k3] = (float)av;
+                geo64[4 * gslot + k3] = av;
+                geo32[4 * gslot + k3] = (float)av;
             }
             int32_t nb32 = nb;
-            std::memcpy(&geo32[4 * slot + 3], &nb32, 4);
+            std::memcpy(&geo32[4 * gslot + 3], &nb32, 4);
             long long nb64 = nb;
-            std::memcpy(&geo64[4 * slot + 3], &nb64, 8);
+            std::memcpy(&geo64[4 * gslot + 3], &nb64, 8);
         }
     }
-    for (int64_t s = 0; s < N * FS; ++s) {
-        if (sface[s] < 0) {  // empty slot: zero area, marker neighbour
+    for (int64_t c = 0; c < N; ++c) {
+        for (int k = fill[c]; k < GS; ++k) {  // empty slots: zero area, marker neighbour
+            int64_t gslot = c * GS + k;
             int32_t nb32 = INT32_MIN;
-            std::memcpy(&geo32[4 * s + 3], &nb32, 4);
+            std::memcpy(&geo32[4 * gslot + 3], &nb32, 4);
             long long nb64 = INT32_MIN;
-            std::memcpy(&geo64[4 * s + 3], &nb64, 8);
+            std::memcpy(&geo64[4 * gslot + 3], &nb64, 8);
         }
     }
     std::vector<float> vol32(N);
@@ -298,6 +303,7 @@ int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cel
     m->F = F;
     m->Fb = Fb;
     m->FS = FS;
+    m->GS = GS;
     cudaStream_t s = nullptr;
     int rc = JSWEEP_OK;
     auto up = [&](DevBuf &buf, const void *src, size_t bytes) {
@@ -312,6 +318,12 @@ int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cel
     };
     up(m->sface, sface.data(), sface.size() * 4);
     up(m->nbr, nbr.data(), nbr.size() * 4);
+    {
+        std::vector<int32_t> nbr8(N * 8, INT32_MIN);
+        for (int64_t c = 0; c < N; ++c)
+            for (int k = 0; k < FS; ++k) nbr8[c * 8 + k] = nbr[c * FS + k];
+        up(m->nbr8, nbr8.data(), nbr8.size() * 4);
+    }
     up(m->normal, normals, F * 3 * sizeof(double));
     up(m->geo32, geo32.data(), geo32.size() * 4);
     up(m->geo64, geo64.data(), geo64.size() * 8);
@@ -454,6 +466,11 @@ static int check_options(const jsweep_options *opt, jsweep_options *o) {
         return JSWEEP_ERR_INVALID_ARG;
     }
     o->layering = opt->layering;
+    if (opt->unit_order < 0 || opt->unit_order > 1) {
+        set_error("jsweep_options.unit_order=%d out of range", opt->unit_order);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    o->unit_order = opt->unit_order;
     return JSWEEP_OK;
 }
 

@@ -79,11 +79,13 @@ struct Mesh {
     std::atomic<int> refs{1};
     int64_t N = 0, F = 0, Fb = 0;
     int FS = 0;  // face slots per cell = max faces per cell
+    int GS = 0;  // slots per cell in the geometry records (FS padded to 4 or 8)
     DevBuf sface;    // int32 [N][FS]: (face id << 1) | (cell is cell1), -1 = empty slot
     DevBuf nbr;      // int32 [N][FS]: neighbour id, -(b+1) for boundary face b, INT32_MIN empty
+    DevBuf nbr8;     // int32 [N][8]: the same padded to 8 slots (two 16-byte loads per cell)
     DevBuf normal;   // double [F][3]
-    DevBuf geo32;    // float4 [N][FS]: outward vector area (a n, oriented out of the cell), w = nbr bits
-    DevBuf geo64;    // double4 [N][FS]: outward vector area, w = nbr as double bits
+    DevBuf geo32;    // float4 [N][GS]: outward vector area (a n, oriented out of the cell), w = nbr bits
+    DevBuf geo64;    // double4 [N][GS]: outward vector area, w = nbr as double bits
     DevBuf vol64;    // double [N]
     DevBuf vol32;    // float [N]
 };
@@ -99,7 +101,7 @@ struct Quad {
 };
 
 struct UnitTable {
-    int mode = -1, priority = -1, cluster = -1, stagger = -1;
+    int mode = -1, priority = -1, cluster = -1, stagger = -1, order = -1;
     DevBuf units;                  // int4 [n_units]: (m, pos0, ncells, wait target)
     int64_t n_units = 0;
     std::vector<int64_t> slot_ptr; // level-sync: units of level l are [slot_ptr[l], slot_ptr[l+1])
@@ -132,9 +134,8 @@ struct Dags {
     DevBuf psi_lag;
     int lag_R = 0, lag_prec = -1;
     // sweep workspaces
-    DevBuf psi;      // [M][N][R]
-    DevBuf srcv;     // [N][R]: S V
-    DevBuf sigv;     // [N]: sigma_t V
+    DevBuf psi;      // [N][M][R] (cell-major: a cell's directions are contiguous)
+    DevBuf srcv;     // [N][RS] source records: S V for each rhs, then sigma_t V (see src_stride)
     DevBuf inflow;   // [R][Fb] copy (stable pointer for graphs)
     DevBuf phi_a, phi_b;  // [R][N] (SI ping-pong)
     DevBuf red;      // residual accumulators / flags

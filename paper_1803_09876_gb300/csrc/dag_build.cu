@@ -33,6 +33,7 @@
 //      LSD radix sort; level_ptr from the sorted keys; the incoming mask is
 //      gathered into level order (bit 7 flags a cell with a lagged face).
 #include <climits>
+#include <memory>
 
 #include "common.cuh"
 
@@ -59,6 +60,7 @@ struct BuildCtx {
     int64_t N, M;
     int FS;
     const int32_t *sface, *nbr;
+    const int4 *nbr8;  // [N][2]: neighbour ids padded to 8 slots
     const double *normal, *dirs;
     int32_t *cnt, *lvl, *stamp, *claim;
     uint8_t *inm, *outm, *lagm;
@@ -76,6 +78,14 @@ struct BuildCtx {
     int32_t *status;  // [0] error code, [1] error info, [2] remaining (clamped), [3] step counter,
                       // [4] stall rounds, [5] cycles found by walks, [6] components lagged
     unsigned long long *wclaim;  // [M][N]: (epoch << 32) | (walker + 1) of the walk that owns the cell
+    // acyclicity certificate: a direction in which the level of its octant's
+    // diagonal (lam) increases along every edge has no cycle, so it needs no
+    // cycle candidates or resolution.  cyc[m] = 1 when not certified.
+    int32_t *seeds;      // [M][kSeedCapG]: cells at which walks closed a pointer cycle this step
+    int32_t *nseeds;     // [M]
+    const int32_t *lam;  // [8][N] or null (no certificate: every direction is treated as cyclic)
+    const int32_t *oct;  // [M]
+    int32_t *cyc;        // [M]
 };
 
 __device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, int64_t cap,
@@ -86,6 +96,12 @@ __device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, i
     } else {
         atomicCAS(&status[0], 0, JSWEEP_ERR_OOM);
     }
+}
+
+__device__ __forceinline__ void load_nbr8(const BuildCtx &c, int32_t v, int32_t (&nb)[8]) {
+    const int4 a = __ldg(c.nbr8 + 2 * (int64_t)v), b = __ldg(c.nbr8 + 2 * (int64_t)v + 1);
+    nb[0] = a.x; nb[1] = a.y; nb[2] = a.z; nb[3] = a.w;
+    nb[4] = b.x; nb[5] = b.y; nb[6] = b.z; nb[7] = b.w;
 }
 
 __global__ void k_classify(BuildCtx c) {
@@ -107,7 +123,15 @@ __global__ void k_classify(BuildCtx c) {
             int32_t nb = c.nbr[(int64_t)v * c.FS + k];
             if (s < 0.0) {
                 in |= 1u << k;
-                if (nb >= 0) ++count; else bin = true;
+                if (nb >= 0) {
+                    ++count;
+                    if (c.lam) {
+                        const int64_t lo = (int64_t)c.oct[m] * c.N;
+                        if (c.lam[lo + v] <= c.lam[lo + nb]) c.cyc[m] = 1;  // back edge: not certified
+                    }
+                } else {
+                    bin = true;
+                }
             } else if (s > 0.0 && nb >= 0) {
                 out |= 1u << k;
             }
@@ -138,28 +162,34 @@ __global__ void k_peel(BuildCtx c, int cur) {
     int32_t *ncl = c.ncand + ci * c.M + m;
     const int32_t ep = c.epoch[m];
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.npend = 0;  // read by the last commit
+    const bool cyclic = c.cyc[m] != 0;
     int processed = 0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int32_t v = fr[i];
-        unsigned inb = c.inm[base + v], lg = c.lagm[base + v];
+        const int32_t v = fr[i];
+        const unsigned act = (unsigned)c.inm[base + v] & ~(unsigned)c.lagm[base + v];
+        const unsigned ob = c.outm[base + v];
+        int32_t nb[8];
+        load_nbr8(c, v, nb);
+        // all upwind levels in flight together
+        int lv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[base + nb[k]] + 1 : 0;
         int lev = 0;
-        for (int k = 0; k < c.FS; ++k) {
-            if (((inb & ~lg) >> k) & 1u) {
-                int32_t u = c.nbr[(int64_t)v * c.FS + k];
-                if (u >= 0) lev = max(lev, c.lvl[base + u] + 1);
-            }
-        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) lev = max(lev, lv[k]);
         c.lvl[base + v] = lev;
-        unsigned ob = c.outm[base + v];
-        for (int k = 0; k < c.FS; ++k) {
-            if ((ob >> k) & 1u) {
-                int32_t w = c.nbr[(int64_t)v * c.FS + k];
-                int32_t old = atomicSub(&c.cnt[base + w], 1);
-                if (old == 1) {
-                    push(fn, nfn, w, c.N, c.status);
-                } else if (atomicExch(&c.stamp[base + w], ep) != ep) {
-                    push(cl, ncl, w, c.N, c.status);
-                }
+        // all downwind decrements in flight together
+        int32_t old[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) old[k] = ((ob >> k) & 1u) ? atomicSub(&c.cnt[base + nb[k]], 1) : 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (!((ob >> k) & 1u)) continue;
+            const int32_t w = nb[k];
+            if (old[k] == 1) {
+                push(fn, nfn, w, c.N, c.status);
+            } else if (cyclic && atomicExch(&c.stamp[base + w], ep) != ep) {
+                push(cl, ncl, w, c.N, c.status);
             }
         }
         ++processed;
@@ -171,13 +201,15 @@ __global__ void k_peel(BuildCtx c, int cur) {
 
 // First unfinished active upwind cell of x (slots in increasing face id).
 __device__ __forceinline__ int32_t first_open_pred(const BuildCtx &c, int64_t base, int32_t x) {
-    unsigned act = (unsigned)c.inm[base + x] & ~(unsigned)c.lagm[base + x];
-    for (int k = 0; k < c.FS; ++k) {
-        if ((act >> k) & 1u) {
-            int32_t u = c.nbr[(int64_t)x * c.FS + k];
-            if (u >= 0 && c.lvl[base + u] < 0) return u;
-        }
-    }
+    const unsigned act = (unsigned)c.inm[base + x] & ~(unsigned)c.lagm[base + x];
+    int32_t nb[8];
+    load_nbr8(c, x, nb);
+    int lv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[base + nb[k]] : 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (((act >> k) & 1u) && nb[k] >= 0 && lv[k] < 0) return nb[k];
     return -1;
 }
 
@@ -192,7 +224,7 @@ __device__ __forceinline__ int warp_find(const int32_t *X, int size, int32_t v, 
 }
 
 constexpr int kResolveWarps = 16;
-constexpr int kSeedCap = 2048;  // cycles kept per stalled direction and step (more wait for the next stall)
+constexpr int kSeedCap = 4096;  // cycles kept per direction and step (more wait for the next round)
 
 // Walk x -> first_open_pred(x) from candidate `i` with claimed cells: a cell
 // owned (this epoch) by a lower walker id stops the walk, a higher id is taken
@@ -201,8 +233,15 @@ constexpr int kSeedCap = 2048;  // cycles kept per stalled direction and step (m
 __device__ int32_t claim_walk(const BuildCtx &c, int64_t base, int32_t v, uint32_t me, int32_t ep,
                               int walk_max) {
     const unsigned long long tag = ((unsigned long long)(uint32_t)ep << 32) | me;
+    // a cell whose count is zero is ready (its upwind cells are all done), so
+    // it is on no cycle: such a walk ends without claiming anything
+    {
+        const int32_t p = first_open_pred(c, base, v);
+        if (p < 0 || c.cnt[base + p] <= 0) return -1;
+    }
     int32_t x = v;
     for (int step = 0; step < walk_max && x >= 0; ++step) {
+        if (step > 0 && c.cnt[base + x] <= 0) return -1;
         unsigned long long *slot = c.wclaim + base + x;
         unsigned long long old = *((volatile unsigned long long *)slot);
         while (true) {
@@ -220,32 +259,56 @@ __device__ int32_t claim_walk(const BuildCtx &c, int64_t base, int32_t v, uint32
     return -1;
 }
 
-// Cycle resolution, every step, for every unfinished direction with new
-// candidates (blockIdx.x = direction).  A component is resolved as soon as a
-// walk can close it, not only when the whole direction has stalled, so that
-// the cells behind it are not held back until the rest of the front drains.
-// The closure test only ever accepts a set closed under unfinished upwind
-// cells, which contains the whole component whatever the frontier holds.
-// Phase A: every thread walks candidates (claim_walk) and records the cells at
-// which it closed a pointer cycle.  Phase B: one warp per recorded cycle
-// gathers the unfinished cells that reach it backwards (cap B); when that set
-// closes, the cycle's strongly connected component is computed inside it and
-// its smallest active face is lagged (one lag per component: the component is
-// claimed through its smallest cell).
-// Dynamic shared memory: per warp X[B] (int32), Sidx[B] (int32), inS[B] (uint8).
-__global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
-    const int64_t m = blockIdx.x;
-    if (c.nproc[m] >= c.N) return;  // direction finished
-    const bool stalled = c.nfront[nxt * c.M + m] == 0;
-    if (!stalled && c.ncand[c.cidx[m] * c.M + m] == 0) return;  // nothing new to look at
-    extern __shared__ int32_t sh[];
-    __shared__ int32_t seeds[kSeedCap];
-    __shared__ int32_t nseeds, new_lags;
-    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
-    if (threadIdx.x == 0) {
-        nseeds = 0;
-        new_lags = 0;
+// Cycle resolution runs every step for every unfinished direction that is not
+// certified acyclic and has new candidates (or has stalled).  A component is
+// resolved as soon as a walk can close it, not only when the whole direction
+// has stalled, so that the cells behind it are not held back until the rest of
+// the front drains.  The closure test only ever accepts a set closed under
+// unfinished upwind cells, which contains the whole component whatever the
+// frontier holds.
+__device__ __forceinline__ bool resolve_active(const BuildCtx &c, int64_t m, int nxt, bool *stalled) {
+    if (c.nproc[m] >= c.N) return false;  // direction finished
+    *stalled = c.nfront[nxt * c.M + m] == 0;
+    return *stalled || (c.cyc[m] != 0 && c.ncand[c.cidx[m] * c.M + m] != 0);
+}
+
+// Walks (grid (blocks, direction)): every thread walks candidates with
+// claim_walk and records the cells at which it closed a pointer cycle.
+__global__ void k_walk(BuildCtx c, int nxt, int walk_max) {
+    const int64_t m = blockIdx.y;
+    bool stalled;
+    if (!resolve_active(c, m, nxt, &stalled)) return;
+    const int64_t base = m * c.N;
+    const int ci = c.cidx[m];
+    const int32_t nc = min(c.ncand[ci * c.M + m], (int32_t)c.N);
+    const int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
+    const int32_t ep = c.epoch[m];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        const int32_t v = cl[i];
+        if (c.lvl[base + v] >= 0 || c.cnt[base + v] <= 0) continue;
+        const int32_t x = claim_walk(c, base, v, (uint32_t)i + 1u, ep, walk_max);
+        if (x >= 0) {
+            const int32_t k = atomicAdd(&c.nseeds[m], 1);
+            if (k < kSeedCap) c.seeds[m * kSeedCap + k] = x;
+        }
     }
+}
+
+// Closures (blockIdx.x = direction): one warp per recorded cycle gathers the
+// unfinished cells that reach it backwards (cap B); when that set closes, the
+// cycle's strongly connected component is computed inside it and its smallest
+// active face is lagged (one lag per component: the component is claimed
+// through its smallest cell).  Then the direction's candidate lists are
+// rotated.  Dynamic shared memory: per warp X[B] (int32), Sidx[B] (int32),
+// inS[B] (uint8).
+__global__ void k_resolve(BuildCtx c, int nxt, int B) {
+    const int64_t m = blockIdx.x;
+    bool stalled;
+    if (!resolve_active(c, m, nxt, &stalled)) return;
+    extern __shared__ int32_t sh[];
+    __shared__ int32_t new_lags;
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    if (threadIdx.x == 0) new_lags = 0;
     __syncthreads();
     const int64_t base = m * c.N;
     const int ci = c.cidx[m];
@@ -254,19 +317,9 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
     int32_t *cn = c.cand + (int64_t)(ci ^ 1) * c.M * c.N + base;
     int32_t *ncn = c.ncand + (ci ^ 1) * c.M + m;
     const int32_t ep = c.epoch[m];
-
-    // ---- phase A: claimed pointer walks
-    for (int32_t i = threadIdx.x; i < nc; i += blockDim.x) {
-        int32_t v = cl[i];
-        if (c.lvl[base + v] >= 0 || c.cnt[base + v] <= 0) continue;
-        int32_t x = claim_walk(c, base, v, (uint32_t)i + 1u, ep, walk_max);
-        if (x >= 0) {
-            int32_t k = atomicAdd(&nseeds, 1);
-            if (k < kSeedCap) seeds[k] = x;
-        }
-    }
-    __syncthreads();
+    const int32_t nseeds = c.nseeds[m];
     const int ns_total = min(nseeds, kSeedCap);
+    const int32_t *seeds = c.seeds + m * kSeedCap;
     if (threadIdx.x == 0) atomicAdd(&c.status[5], ns_total);
 
     int32_t *X = sh + warp * (2 * B + (B + 3) / 4);
@@ -409,6 +462,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int walk_max) {
         c.ncand[ci * c.M + m] = 0;
         c.cidx[m] = ci ^ 1;
         c.epoch[m] = ep + 1;
+        c.nseeds[m] = 0;
     }
 }
 
@@ -531,7 +585,7 @@ __global__ void k_lag_ptr(const int32_t *lm, int32_t T, int64_t M, int32_t *lag_
 // kappa(c) = max(floor(rho_o * lambda_o(c)), 1 + max kappa(active upwind cell)).
 // Upwind cells have smaller levels, so their kappa is final when c's level runs.
 __global__ void k_kappa_level(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
-                              const uint8_t *inm, const uint8_t *lagm, const int32_t *nbr, int FS, int64_t N,
+                              const uint8_t *inm, const uint8_t *lagm, const int4 *nbr8, int64_t N,
                               const int32_t *oct, const float *rho, const int32_t *lam, int32_t l, int32_t *kap) {
     const int64_t m = blockIdx.y;
     if (l >= nlev[m]) return;
@@ -543,12 +597,13 @@ __global__ void k_kappa_level(const int32_t *order, const int32_t *lp, const int
         const int32_t c = order[base + pos];
         int32_t k = (int32_t)(r * (float)lam[(int64_t)o * N + c]);
         const unsigned act = (unsigned)inm[base + c] & ~(unsigned)lagm[base + c];
-        for (int q = 0; q < FS; ++q) {
-            if ((act >> q) & 1u) {
-                const int32_t u = nbr[(int64_t)c * FS + q];
-                if (u >= 0) k = max(k, kap[base + u] + 1);
-            }
-        }
+        const int4 a = __ldg(nbr8 + 2 * (int64_t)c), b = __ldg(nbr8 + 2 * (int64_t)c + 1);
+        const int32_t nb[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        int32_t kk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) kk[q] = (((act >> q) & 1u) && nb[q] >= 0) ? kap[base + nb[q]] + 1 : k;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) k = max(k, kk[q]);
         kap[base + c] = k;
     }
 }
@@ -724,17 +779,20 @@ int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len,
     return JSWEEP_OK;
 }
 
-// Octant-aligned schedule layers (see jsweep_options.layering).  The levels
-// of the 8 diagonal directions come from a nested build over the same mesh.
-static int octant_layers(Dags *d, const uint8_t *inm, const uint8_t *lagm, const int64_t *lpoff_dev,
-                         const int32_t *nlev_dev, cudaStream_t s) {
-    const int64_t N = d->N, M = d->M;
-    // octant of every direction and the diagonal of each octant
-    std::vector<int32_t> oct(M);
-    for (int64_t m = 0; m < M; ++m) {
+// Octant of every direction: bits (1, 2, 4) set for negative (x, y, z).
+static std::vector<int32_t> octant_of(const Dags *d) {
+    std::vector<int32_t> oct(d->M);
+    for (int64_t m = 0; m < d->M; ++m) {
         const double *o = d->quad->dirs.data() + 3 * m;
         oct[m] = (o[0] < 0 ? 1 : 0) | (o[1] < 0 ? 2 : 0) | (o[2] < 0 ? 4 : 0);
     }
+    return oct;
+}
+
+// Dependency graphs of the 8 octant diagonals (+-1, +-1, +-1)/sqrt(3) over the
+// same mesh (a nested build with longest-path levels).  Returns nullptr (and no
+// error) if that build fails: the diagonals only serve the schedule.
+static Dags *build_diagonals(Dags *d, cudaStream_t s) {
     Quad *dq = new Quad();
     dq->M = 8;
     std::vector<double> dd(24), dw(8, 1.0);
@@ -746,28 +804,33 @@ static int octant_layers(Dags *d, const uint8_t *inm, const uint8_t *lagm, const
     }
     dq->dirs = dd;
     dq->w = dw;
-    int rc = dq->dirs64.alloc(24 * 8, s);
-    if (rc == JSWEEP_OK && cudaMemcpy(dq->dirs64.p, dd.data(), 24 * 8, cudaMemcpyHostToDevice) != cudaSuccess)
-        rc = JSWEEP_ERR_CUDA;
-    if (rc != JSWEEP_OK) {
+    if (dq->dirs64.alloc(24 * 8, s) != JSWEEP_OK ||
+        cudaMemcpy(dq->dirs64.p, dd.data(), 24 * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
         delete dq;
-        return rc;
+        clear_error();
+        return nullptr;
     }
     Dags *dg = new Dags();
     dg->mesh = d->mesh;
     d->mesh->refs.fetch_add(1);
     dg->quad = dq;  // owned by dg
-    dg->N = N;
+    dg->N = d->N;
     dg->M = 8;
     dg->opt = d->opt;
     dg->opt.layering = JSWEEP_LAYERS_LEVEL;
-    rc = build_dags(dg, s);
-    if (rc != JSWEEP_OK) {
-        // the layering is only a schedule: keep the longest-path levels
+    if (build_dags(dg, s) != JSWEEP_OK) {
         delete dg;
         clear_error();
-        return JSWEEP_OK;
+        return nullptr;
     }
+    return dg;
+}
+
+// Octant-aligned schedule layers (see jsweep_options.layering) from the levels
+// of the octant diagonals.
+static int octant_layers(Dags *d, const Dags *dg, const std::vector<int32_t> &oct, const uint8_t *inm,
+                         const uint8_t *lagm, const int64_t *lpoff_dev, const int32_t *nlev_dev, cudaStream_t s) {
+    const int64_t N = d->N, M = d->M;
     std::vector<float> rho(8, 1.0f);
     for (int o = 0; o < 8; ++o) {
         int64_t lmax = 0;
@@ -784,13 +847,12 @@ static int octant_layers(Dags *d, const uint8_t *inm, const uint8_t *lagm, const
     const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (256 * 64)), 8);
     for (int64_t l = 0; l < d->Lmax; ++l) {
         k_kappa_level<<<dim3(gx, (unsigned)M), 256, 0, s>>>(d->order.as<int32_t>(), d->lp.as<int32_t>(), lpoff_dev,
-                                                           nlev_dev, inm, lagm, d->mesh->nbr.as<int32_t>(),
-                                                           d->mesh->FS, N, oct_d.as<int32_t>(), rho_d.as<float>(),
+                                                           nlev_dev, inm, lagm, d->mesh->nbr8.as<int4>(), N,
+                                                           oct_d.as<int32_t>(), rho_d.as<float>(),
                                                            dg->level.as<int32_t>(), (int32_t)l, kap.as<int32_t>());
         note_launches(1);
     }
     JS_CUDA(cudaGetLastError());
-    delete dg;
     // layer counts, sort by (layer, cell id), layer pointers, mask in layer order
     JS_TRY(kmax.alloc(M * 4, s));
     JS_CUDA(cudaMemsetAsync(kmax.p, 0xff, M * 4, s));
@@ -847,6 +909,16 @@ int build_dags(Dags *d, cudaStream_t s) {
     if (!d->ev[0])
         for (auto &e : d->ev) JS_CUDA(cudaEventCreate(&e));
     JS_CUDA(cudaEventRecord(d->ev[0], s));
+    // phase boundaries (device time of each build phase)
+    cudaEvent_t pe[7];
+    for (auto &e : pe) JS_CUDA(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 7; ++i) cudaEventDestroy(e[i]);
+        }
+    } ev_guard{pe};
+    for (int i = 0; i < 6; ++i) d->timing.build_phase_ms[i] = 0.0;
 
     // ---- scratch
     DevBuf cnt, stamp, claim, wclaim, inm, outm, lagm, front, cand, small, pend, lagall;
@@ -874,6 +946,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.FS = mesh->FS;
     c.sface = mesh->sface.as<int32_t>();
     c.nbr = mesh->nbr.as<int32_t>();
+    c.nbr8 = mesh->nbr8.as<int4>();
     c.normal = mesh->normal.as<double>();
     c.dirs = quad->dirs64.as<double>();
     c.cnt = cnt.as<int32_t>();
@@ -911,8 +984,32 @@ int build_dags(Dags *d, cudaStream_t s) {
         JS_CUDA(cudaMemcpyAsync(c.epoch, ones.data(), M * 4, cudaMemcpyHostToDevice, s));
         JS_CUDA(cudaStreamSynchronize(s));
     }
+    // diagonals of the octants first: their levels certify acyclic directions and
+    // give the octant-aligned schedule layers
+    std::vector<int32_t> oct = octant_of(d);
+    DevBuf oct_d, cyc_d, seed_d, nseed_d;
+    JS_TRY(oct_d.alloc(M * 4, s));
+    JS_TRY(cyc_d.alloc(M * 4, s));
+    JS_TRY(seed_d.alloc((size_t)M * kSeedCap * 4, s));
+    JS_TRY(nseed_d.alloc(M * 4, s));
+    JS_CUDA(cudaMemsetAsync(nseed_d.p, 0, M * 4, s));
+    c.seeds = seed_d.as<int32_t>();
+    c.nseeds = nseed_d.as<int32_t>();
+    std::vector<int32_t> ones(M, 1);
+    JS_CUDA(cudaMemcpyAsync(oct_d.p, oct.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(cyc_d.p, ones.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    std::unique_ptr<Dags> dg;
+    JS_CUDA(cudaEventRecord(pe[0], s));
+    if (d->opt.layering == JSWEEP_LAYERS_OCTANT) dg.reset(build_diagonals(d, s));
+    JS_CUDA(cudaEventRecord(pe[1], s));
+    c.lam = dg ? dg->level.as<int32_t>() : nullptr;
+    c.oct = oct_d.as<int32_t>();
+    c.cyc = cyc_d.as<int32_t>();
+    if (dg) JS_CUDA(cudaMemsetAsync(c.cyc, 0, M * 4, s));
     k_classify<<<grid_for(MN, 256, 152 * 64), 256, 0, s>>>(c);
     JS_LAUNCH_CHECK();
+    JS_CUDA(cudaEventRecord(pe[2], s));
 
     // ---- frontier loop with stall resolution
     const int B = d->opt.cycle_search_max;
@@ -929,9 +1026,10 @@ int build_dags(Dags *d, cudaStream_t s) {
     while (true) {
         int cur = (int)(step & 1);
         k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
-        k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B, walk_max);
+        k_walk<<<dim3(8, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
+        k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B);
         k_commit<<<64, 256, 0, s>>>(c, cur ^ 1, cur);
-        note_launches(2);  // peel, resolve; the check below counts commit
+        note_launches(3);  // peel, walk, resolve; the check below counts commit
         JS_LAUNCH_CHECK();
         ++step;
         if (step % check_every == 0) {
@@ -957,6 +1055,7 @@ int build_dags(Dags *d, cudaStream_t s) {
         }
     }
 
+    JS_CUDA(cudaEventRecord(pe[3], s));
     // ---- levels per direction
     DevBuf lmax;
     JS_TRY(lmax.alloc(M * 4, s));
@@ -1006,6 +1105,7 @@ int build_dags(Dags *d, cudaStream_t s) {
                                                                     d->mask.as<uint8_t>());
     JS_LAUNCH_CHECK();
 
+    JS_CUDA(cudaEventRecord(pe[4], s));
     // ---- lag list sorted by (direction, face id)
     const int32_t T = std::min<int32_t>(nlag_total, (int32_t)lag_cap);
     d->T = T;
@@ -1043,6 +1143,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     d->timing.build_steps = step;
     d->timing.build_stall_rounds = status[4];
 
+    JS_CUDA(cudaEventRecord(pe[5], s));
     // ---- schedule layering
     d->layering = JSWEEP_LAYERS_LEVEL;
     d->s_order = d->order.as<int32_t>();
@@ -1051,15 +1152,21 @@ int build_dags(Dags *d, cudaStream_t s) {
     d->slayers = d->nlevels;
     d->sp_off = d->lp_off;
     d->Smax = d->Lmax;
-    if (d->opt.layering == JSWEEP_LAYERS_OCTANT) {
-        int rc = octant_layers(d, c.inm, c.lagm, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), s);
+    if (dg) {
+        int rc = octant_layers(d, dg.get(), oct, c.inm, c.lagm, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), s);
         if (rc != JSWEEP_OK) return rc;
     }
+    JS_CUDA(cudaEventRecord(pe[6], s));
     JS_CUDA(cudaEventRecord(d->ev[1], s));
     JS_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]);
     d->timing.build_ms = ms;
+    for (int i = 0; i < 6; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, pe[i], pe[i + 1]);
+        d->timing.build_phase_ms[i] = t;
+    }
     d->psi_lag.release();
     d->lag_R = 0;
     d->lag_prec = -1;

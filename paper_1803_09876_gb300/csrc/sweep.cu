@@ -48,15 +48,14 @@ template <> struct V4<double> { using type = double4; };
 
 template <class T> struct SweepArgs {
     int64_t N;
-    int M, FS, Fb;
+    int M, FS, GS, Fb;
     const int32_t *order;
     const uint8_t *mask;
     const typename V4<T>::type *geo;
     const T *dirs;  // [M][4] (x, y, z, 0)
-    const T *srcv;  // [N][R]
-    const T *sigv;  // [N]
+    const T *srcv;  // [N][RS]: S V of each rhs at [0, R), sigma_t V at [R]
     const T *inflow;  // [R][Fb] or null
-    T *psi;           // [M][N][R]
+    T *psi;           // [N][M][R]
     const T *psi_lag; // [Tl][R]
     const int32_t *lag_ptr, *lag_face, *sface;
     const int4 *units;
@@ -141,6 +140,10 @@ __device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *
     return (lo < lag_ptr[m + 1] && lag_face[lo] == f) ? lo : -1;
 }
 
+// Source record stride: the R values S V, then sigma_t V, padded so that a
+// record is 8, 16, 32 or 64 bytes (FP32) and one DRAM transaction brings both.
+template <int R> constexpr int src_stride() { return R >= 4 ? 2 * R : (R == 2 ? 4 : 2); }
+
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -163,16 +166,17 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
     using V = typename V4<T>::type;
     constexpr int RH = R / SPLIT;
     const T ox = a.dirs[4 * m], oy = a.dirs[4 * m + 1], oz = a.dirs[4 * m + 2];
-    const V *g = a.geo + (int64_t)c * a.FS;
+    const V *g = a.geo + (int64_t)c * a.GS;
     V gk[MAXF];
 #pragma unroll
     for (int k = 0; k < MAXF; ++k) {
         if (k < a.FS) gk[k] = g[k];
         else gk[k] = V{T(0), T(0), T(0), T(0)};
     }
+    constexpr int RS = src_stride<R>();
     T num[RH];
-    load_ro<T, RH>(a.srcv + (int64_t)c * R + sub * RH, num);
-    T den = __ldg(a.sigv + c);
+    load_ro<T, RH>(a.srcv + (int64_t)c * RS + sub * RH, num);
+    T den = __ldg(a.srcv + (int64_t)c * RS + R);
     // lagged faces (rare): bit k set when face slot k takes the previous sweep's value
     unsigned lagk = 0;
     int lagj[MAXF];
@@ -221,7 +225,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
                 if ((lagk >> k) & 1u) {
                     load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
                 } else {
-                    load_cg<T, RH>(a.psi + ((int64_t)m * a.N + nb) * R + sub * RH, up);
+                    load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
                 }
             } else {
                 const int b = -nb - 1;
@@ -238,7 +242,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
     T out[RH];
 #pragma unroll
     for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
-    store_cg<T, RH>(a.psi + ((int64_t)m * a.N + c) * R + sub * RH, out);
+    store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
     return true;
 }
 
@@ -306,30 +310,54 @@ __global__ void k_unit_counts(const int32_t *lp, const int64_t *lp_off, const in
     }
 }
 
-__global__ void k_unit_slots(const int64_t *ucnt, const int32_t *off, int64_t M, int64_t Lmax, int64_t Tmax,
-                             int64_t *cnt2) {
+// Per-slot unit counts, laid out per slot in grouped direction order (qpos[m]).
+__global__ void k_unit_slots(const int64_t *ucnt, const int32_t *off, const int32_t *qpos, int64_t M, int64_t Lmax,
+                             int64_t Tmax, int64_t *cnt2) {
     const int64_t total = M * Lmax;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t m = i / Lmax, l = i - m * Lmax;
         int64_t t = l + off[m];
-        if (t < Tmax) cnt2[t * M + m] = ucnt[i];
+        if (t < Tmax) cnt2[t * M + qpos[m]] = ucnt[i];
     }
 }
 
+// Fills the unit table.  Inside a slot t the directions are laid out in grouped
+// order (octant by octant: gmem, group g = [gstart[g], gstart[g+1]), qpos[m] =
+// position of m).  Either direction by direction (interleave = 0), or with the
+// units of a group interleaved: chunk 0 of each of its directions, chunk 1 of
+// each, ... (interleave = 1), so that chunks covering nearby cells for
+// different directions sit next to each other.
 __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, const int64_t *ucnt,
-                            const int64_t *wscan, const int64_t *base2, const int32_t *off, int64_t M,
-                            int64_t Lmax, int U, int4 *units) {
+                            const int64_t *wscan, const int64_t *base2, const int64_t *cnt2, const int32_t *off,
+                            int64_t M, int64_t Lmax, int U, const int32_t *gmem, const int32_t *gstart,
+                            const int32_t *gof, const int32_t *qpos, int interleave, int4 *units) {
     const int64_t total = M * Lmax;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t m = i / Lmax, l = i - m * Lmax;
         if (l >= nlev[m]) continue;
         int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
         int64_t nu = ucnt[i];
-        int64_t b = base2[(l + off[m]) * M + m];
+        const int64_t t = l + off[m];
         int32_t wait = (int32_t)(wscan[i] - wscan[m * Lmax]);
+        if (!interleave) {
+            const int64_t b = base2[t * M + qpos[m]];
+            for (int64_t j = 0; j < nu; ++j) {
+                int32_t s = p0 + (int32_t)(j * U);
+                units[b + j] = make_int4((int)m, s, min(U, p1 - s), wait);
+            }
+            continue;
+        }
+        const int g = gof[m];
+        const int64_t gb = base2[t * M + gstart[g]];
         for (int64_t j = 0; j < nu; ++j) {
+            int64_t pos = gb;
+            for (int q = gstart[g]; q < gstart[g + 1]; ++q) {
+                const int64_t uq = cnt2[t * M + q];
+                pos += uq < j ? uq : j;                 // chunks 0..j-1 of every direction of the group
+                if (gmem[q] < m && uq > j) pos += 1;    // chunk j of the group's directions before m
+            }
             int32_t s = p0 + (int32_t)(j * U);
-            units[b + j] = make_int4((int)m, s, min(U, p1 - s), wait);
+            units[pos] = make_int4((int)m, s, min(U, p1 - s), wait);
         }
     }
 }
@@ -337,48 +365,69 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
 // ---- emission, phi, residual, lag update ----------------------------------------------
 template <class T, int R>
 __global__ void k_emission(const T *sig, const T *cr, const T *q, const T *phi, const T *vol, int64_t N,
-                           int nrhs, T *srcv, T *sigv) {
+                           int nrhs, T *srcv) {
+    constexpr int RS = src_stride<R>();
     const T four_pi = T(4.0 * 3.141592653589793);
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         T V = vol[c], s = sig[c];
-        sigv[c] = s * V;
         T cs = cr ? cr[c] * s : T(0);
-        T out[R];
+        T out[RS];
+#pragma unroll
+        for (int r = 0; r < RS; ++r) out[r] = T(0);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            T val = T(0);
             if (r < nrhs) {
                 T p = phi ? phi[(int64_t)r * N + c] : T(0);
-                val = ((cs * p + q[(int64_t)r * N + c]) / four_pi) * V;
+                out[r] = ((cs * p + q[(int64_t)r * N + c]) / four_pi) * V;
             }
-            out[r] = val;
         }
+        out[R] = s * V;
 #pragma unroll
-        for (int r = 0; r < R; ++r) srcv[c * R + r] = out[r];
+        for (int r = 0; r < RS; ++r) srcv[c * RS + r] = out[r];
     }
 }
 
-// Angular source given directly: srcv = S V.
+// Angular source given directly: records of S V and sigma_t V.
 template <class T, int R>
-__global__ void k_source_prep(const T *sig, const T *src, const T *vol, int64_t N, int nrhs, T *srcv, T *sigv) {
+__global__ void k_source_prep(const T *sig, const T *src, const T *vol, int64_t N, int nrhs, T *srcv) {
+    constexpr int RS = src_stride<R>();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         T V = vol[c];
-        sigv[c] = sig[c] * V;
+        T out[RS];
 #pragma unroll
-        for (int r = 0; r < R; ++r) srcv[c * R + r] = r < nrhs ? src[(int64_t)r * N + c] * V : T(0);
+        for (int r = 0; r < RS; ++r) out[r] = T(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[r] = r < nrhs ? src[(int64_t)r * N + c] * V : T(0);
+        out[R] = sig[c] * V;
+#pragma unroll
+        for (int r = 0; r < RS; ++r) srcv[c * RS + r] = out[r];
     }
 }
 
-// phi[r][c] = sum_m w_m psi[m][c][r], in direction order; FP32 with Kahan compensation.
+// phi[r][c] = sum_m w_m psi[c][m][r]: one warp per cell reads the cell's
+// contiguous [M][R] block (coalesced); lane l sums directions l, l+32, ... in
+// increasing order (FP32: Kahan-compensated), then the 32 partial sums are
+// combined by a fixed butterfly with error-free two-sums.  The order of every
+// operation is fixed, so phi does not depend on the sweep's schedule.
+template <class T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+    s = a + b;
+    T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 template <class T, int R>
 __global__ void k_phi(const T *psi, const T *w, int64_t N, int M, int nrhs, T *phi) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < N; c += warps) {
         T s[R], comp[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) s[r] = comp[r] = T(0);
-        for (int m = 0; m < M; ++m) {
+        const T *blk = psi + (int64_t)c * M * R;
+        for (int m = lane; m < M; m += 32) {
             T x[R];
-            load_cg<T, R>(psi + ((int64_t)m * N + c) * R, x);
+            load_cg<T, R>(blk + (int64_t)m * R, x);
             const T wm = w[m];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -393,17 +442,30 @@ __global__ void k_phi(const T *psi, const T *w, int64_t N, int M, int nrhs, T *p
             }
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (r < nrhs) phi[(int64_t)r * N + c] = s[r];
+        for (int r = 0; r < R; ++r) {
+            T v = s[r], e = -comp[r];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, v, off);
+                const T oe = __shfl_xor_sync(0xffffffffu, e, off);
+                // combine the lower and the upper lane in the same order on both sides
+                const bool lower = (lane & off) == 0;
+                T ss, ee;
+                two_sum(lower ? v : ov, lower ? ov : v, ss, ee);
+                v = ss;
+                e = (lower ? e : oe) + (lower ? oe : e) + ee;
+            }
+            if (lane == 0 && r < nrhs) phi[(int64_t)r * N + c] = v + e;
+        }
     }
 }
 
 template <class T, int R>
-__global__ void k_lag_update(const T *psi, const int32_t *lag_m, const int32_t *lag_up, int64_t Tl, int64_t N,
+__global__ void k_lag_update(const T *psi, const int32_t *lag_m, const int32_t *lag_up, int64_t Tl, int64_t M,
                              T *psi_lag) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Tl; j += (int64_t)gridDim.x * blockDim.x) {
         T v[R];
-        load_cg<T, R>(psi + ((int64_t)lag_m[j] * N + lag_up[j]) * R, v);
+        load_cg<T, R>(psi + ((int64_t)lag_up[j] * M + lag_m[j]) * R, v);
 #pragma unroll
         for (int r = 0; r < R; ++r) psi_lag[j * R + r] = v[r];
     }
@@ -448,11 +510,12 @@ template <class T, int R>
 __global__ void k_psi_out(const T *psi, int64_t N, int M, int nrhs, T *out) {
     const int64_t total = (int64_t)M * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / M, m = i - c * M;  // i = c * M + m (psi order)
         T v[R];
         load_cg<T, R>(psi + i * R, v);
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (r < nrhs) out[(int64_t)r * total + i] = v[r];
+            if (r < nrhs) out[((int64_t)r * M + m) * N + c] = v[r];
     }
 }
 
@@ -466,8 +529,10 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
     const int prio = d->opt.priority;
     int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Smax / 4);
     if (prio != JSWEEP_PRIO_OCTANT) stagger = 0;
+    const int order = d->opt.unit_order;
     UnitTable &ut = d->ut;
-    if (ut.mode == mode && ut.priority == prio && ut.cluster == U && ut.stagger == stagger) return JSWEEP_OK;
+    if (ut.mode == mode && ut.priority == prio && ut.cluster == U && ut.stagger == stagger && ut.order == order)
+        return JSWEEP_OK;
     // schedule layers (levels or octant-aligned layers) play the part of levels here
     const int64_t M = d->M, Lmax = d->Smax;
     std::vector<int32_t> off(M, 0);
@@ -477,7 +542,31 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
     }
     int64_t Tmax = 0;
     for (int64_t m = 0; m < M; ++m) Tmax = std::max<int64_t>(Tmax, d->slayers[m] + off[m]);
-    DevBuf ucnt, wscan, cnt2, base2, off_d, lpoff_d, nlev_d;
+    // directions grouped by octant (sign pattern), in increasing index inside a group
+    std::vector<int32_t> oct(M), gmem, gstart(9, 0), gof(M), qpos(M);
+    for (int64_t m = 0; m < M; ++m) {
+        const double *o = d->quad->dirs.data() + 3 * m;
+        oct[m] = (o[0] < 0 ? 1 : 0) | (o[1] < 0 ? 2 : 0) | (o[2] < 0 ? 4 : 0);
+    }
+    for (int g = 0; g < 8; ++g) {
+        gstart[g] = (int32_t)gmem.size();
+        for (int64_t m = 0; m < M; ++m)
+            if (oct[m] == g) {
+                qpos[m] = (int32_t)gmem.size();
+                gof[m] = g;
+                gmem.push_back((int32_t)m);
+            }
+    }
+    gstart[8] = (int32_t)gmem.size();
+    DevBuf ucnt, wscan, cnt2, base2, off_d, lpoff_d, nlev_d, gmem_d, gstart_d, gof_d, qpos_d;
+    JS_TRY(gmem_d.alloc(M * 4, s));
+    JS_TRY(gstart_d.alloc(9 * 4, s));
+    JS_TRY(gof_d.alloc(M * 4, s));
+    JS_TRY(qpos_d.alloc(M * 4, s));
+    JS_CUDA(cudaMemcpyAsync(gmem_d.p, gmem.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(gstart_d.p, gstart.data(), 9 * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(gof_d.p, gof.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(qpos_d.p, qpos.data(), M * 4, cudaMemcpyHostToDevice, s));
     JS_TRY(ucnt.alloc(M * Lmax * 8, s));
     JS_TRY(wscan.alloc(M * Lmax * 8, s));
     JS_TRY(cnt2.alloc(Tmax * M * 8, s));
@@ -495,8 +584,9 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
                                                                 nlev_d.as<int32_t>(), M, Lmax, U, ucnt.as<int64_t>());
     JS_LAUNCH_CHECK();
     JS_TRY(scan_exclusive_i64(ucnt.as<int64_t>(), wscan.as<int64_t>(), M * Lmax, s));
-    k_unit_slots<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(ucnt.as<int64_t>(), off_d.as<int32_t>(), M, Lmax,
-                                                               Tmax, cnt2.as<int64_t>());
+    k_unit_slots<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(ucnt.as<int64_t>(), off_d.as<int32_t>(),
+                                                               qpos_d.as<int32_t>(), M, Lmax, Tmax,
+                                                               cnt2.as<int64_t>());
     JS_LAUNCH_CHECK();
     JS_TRY(scan_exclusive_i64(cnt2.as<int64_t>(), base2.as<int64_t>(), Tmax * M, s));
     // total units = base2[last] + cnt2[last]
@@ -514,7 +604,10 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
     k_unit_fill<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
                                                               nlev_d.as<int32_t>(), ucnt.as<int64_t>(),
                                                               wscan.as<int64_t>(), base2.as<int64_t>(),
-                                                              off_d.as<int32_t>(), M, Lmax, U, ut.units.as<int4>());
+                                                              cnt2.as<int64_t>(), off_d.as<int32_t>(), M, Lmax, U,
+                                                              gmem_d.as<int32_t>(), gstart_d.as<int32_t>(),
+                                                              gof_d.as<int32_t>(), qpos_d.as<int32_t>(), order,
+                                                              ut.units.as<int4>());
     JS_LAUNCH_CHECK();
     ut.slot_ptr.clear();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
@@ -528,6 +621,7 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
     ut.priority = prio;
     ut.cluster = U;
     ut.stagger = stagger;
+    ut.order = order;
     // the graph refers to the unit table
     if (d->graph) {
         cudaGraphExecDestroy(d->graph);
@@ -550,6 +644,7 @@ template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
     a.N = d->N;
     a.M = (int)d->M;
     a.FS = d->mesh->FS;
+    a.GS = d->mesh->GS;
     a.Fb = (int)d->mesh->Fb;
     a.order = d->s_order;
     a.mask = d->s_mask;
@@ -561,7 +656,6 @@ template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
         a.dirs = nullptr;  // set from the padded copy below
     }
     a.srcv = d->srcv.as<T>();
-    a.sigv = d->sigv.as<T>();
     a.inflow = has_inflow ? d->inflow.as<T>() : nullptr;
     a.psi = d->psi.as<T>();
     a.psi_lag = d->psi_lag.as<T>();
@@ -577,10 +671,10 @@ template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
 int ensure_workspace(Dags *d, int prec, int Rp, int nrhs, cudaStream_t s) {
     const size_t es = prec == JSWEEP_F64 ? 8 : 4;
     const int64_t N = d->N, M = d->M;
-    size_t before = (size_t)d->psi.p + (size_t)d->srcv.p + (size_t)d->sigv.p + (size_t)d->inflow.p;
+    size_t before = (size_t)d->psi.p + (size_t)d->srcv.p + (size_t)d->inflow.p;
     JS_TRY(d->psi.ensure((size_t)M * N * Rp * es, s));
-    JS_TRY(d->srcv.ensure((size_t)N * Rp * es, s));
-    JS_TRY(d->sigv.ensure((size_t)N * es, s));
+    const int RS = Rp >= 4 ? 2 * Rp : (Rp == 2 ? 4 : 2);  // src_stride
+    JS_TRY(d->srcv.ensure((size_t)N * RS * es, s));
     JS_TRY(d->inflow.ensure((size_t)std::max<int64_t>(d->mesh->Fb, 1) * Rp * es, s));
     JS_TRY(d->phi_a.ensure((size_t)N * nrhs * es, s));
     JS_TRY(d->phi_b.ensure((size_t)N * nrhs * es, s));
@@ -592,7 +686,7 @@ int ensure_workspace(Dags *d, int prec, int Rp, int nrhs, cudaStream_t s) {
         d->lag_R = Rp;
         d->lag_prec = prec;
     }
-    size_t after = (size_t)d->psi.p + (size_t)d->srcv.p + (size_t)d->sigv.p + (size_t)d->inflow.p;
+    size_t after = (size_t)d->psi.p + (size_t)d->srcv.p + (size_t)d->inflow.p;
     if (before != after && d->graph) {
         cudaGraphExecDestroy(d->graph);
         d->graph = nullptr;
@@ -674,8 +768,8 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
     constexpr int SPLIT = split_of<T, R>();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
         char key[512];
-        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%p/%lld", (int)sizeof(T), R, (const void *)a.srcv,
-                 (const void *)a.sigv, (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld", (int)sizeof(T), R, (const void *)a.srcv,
+                 (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
                  (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units);
         if (!d->graph || d->graph_key != key) {
             if (d->graph) {
@@ -737,7 +831,7 @@ int one_sweep(Dags *d, int mode, bool has_inflow, const T *wts, T *phi_dst, int 
     JS_CUDA(cudaEventRecord(d->ev[1], s));
     if (d->T > 0) {
         k_lag_update<T, R><<<grid_for(d->T, 256), 256, 0, s>>>(d->psi.as<T>(), d->lag_m.as<int32_t>(),
-                                                              d->lag_up.as<int32_t>(), d->T, d->N, d->psi_lag.as<T>());
+                                                              d->lag_up.as<int32_t>(), d->T, d->M, d->psi_lag.as<T>());
         JS_LAUNCH_CHECK();
     }
     JS_CUDA(cudaEventRecord(d->ev[2], s));
@@ -769,7 +863,7 @@ static int run_sweep_t(Dags *d, int nrhs, const void *sigma_t, const void *ang_s
     const double *d64 = nullptr;
     if (sizeof(T) == 8) JS_TRY(dirs64x4(d, s, &d64));
     k_source_prep<T, R><<<grid_for(d->N, 256, 152 * 16), 256, 0, s>>>(
-        (const T *)sigma_t, (const T *)ang_source, vol, d->N, nrhs, d->srcv.as<T>(), d->sigv.as<T>());
+        (const T *)sigma_t, (const T *)ang_source, vol, d->N, nrhs, d->srcv.as<T>());
     JS_LAUNCH_CHECK();
     const bool has_inflow = inflow != nullptr;
     if (has_inflow) {
@@ -822,8 +916,7 @@ static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio,
     for (it = 1; it <= max_iters; ++it) {
         phi_new = bufs[(it - 1) & 1];
         k_emission<T, R><<<grid_for(d->N, 256, 152 * 16), 256, 0, s>>>(
-            (const T *)sigma_t, (const T *)c_ratio, (const T *)q, phi_old, vol, d->N, nrhs, d->srcv.as<T>(),
-            d->sigv.as<T>());
+            (const T *)sigma_t, (const T *)c_ratio, (const T *)q, phi_old, vol, d->N, nrhs, d->srcv.as<T>());
         JS_LAUNCH_CHECK();
         JS_TRY((one_sweep<T, R>(d, mode, has_inflow, w, phi_new, nrhs, s, (const T *)d64)));
         JS_CUDA(cudaMemsetAsync(acc, 0, 2 * 8 * 8, s));
@@ -986,8 +1079,7 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
     // scratch layout
     size_t off = 0;
     const size_t o_psi = off;   off = align256(off + (size_t)M * N * R * sizeof(T));
-    const size_t o_src = off;   off = align256(off + (size_t)N * R * sizeof(T));
-    const size_t o_sig = off;   off = align256(off + (size_t)N * sizeof(T));
+    const size_t o_src = off;   off = align256(off + (size_t)N * src_stride<R>() * sizeof(T));
     const size_t o_lag = off;   off = align256(off + (size_t)Tl * R * sizeof(T));
     const size_t o_phi0 = off;  off = align256(off + (size_t)nrhs * N * sizeof(T));
     const size_t o_phi1 = off;  off = align256(off + (size_t)nrhs * N * sizeof(T));
@@ -1007,7 +1099,6 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
     char *b = static_cast<char *>(base);
     T *psi = reinterpret_cast<T *>(b + o_psi);
     T *srcv = reinterpret_cast<T *>(b + o_src);
-    T *sigv = reinterpret_cast<T *>(b + o_sig);
     T *lag = reinterpret_cast<T *>(b + o_lag);
     T *phis[2] = {reinterpret_cast<T *>(b + o_phi0), reinterpret_cast<T *>(b + o_phi1)};
     T *infl = reinterpret_cast<T *>(b + o_inf);
@@ -1029,6 +1120,7 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
     a.N = N;
     a.M = (int)M;
     a.FS = d->mesh->FS;
+    a.GS = d->mesh->GS;
     a.Fb = (int)d->mesh->Fb;
     a.order = d->order.as<int32_t>();
     a.mask = d->mask.as<uint8_t>();
@@ -1042,7 +1134,6 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
         a.dirs = reinterpret_cast<const T *>(d4);
     }
     a.srcv = srcv;
-    a.sigv = sigv;
     a.inflow = inflow ? infl : nullptr;
     a.psi = psi;
     a.psi_lag = lag;
@@ -1062,7 +1153,7 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
     for (it = 1; it <= max_iters; ++it) {
         phi_new = phis[(it - 1) & 1];
         k_emission<T, R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>((const T *)sigma_t, (const T *)c_ratio,
-                                                                    (const T *)q, phi_old, vol, N, nrhs, srcv, sigv);
+                                                                    (const T *)q, phi_old, vol, N, nrhs, srcv);
         JS_LAUNCH_CHECK();
         for (int64_t l = 0; l < d->Lmax; ++l) {
             if (a.FS <= 4)
@@ -1078,7 +1169,7 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
         }
         if (d->T > 0) {
             k_lag_update<T, R><<<grid_for(d->T, 256), 256, 0, s>>>(psi, d->lag_m.as<int32_t>(), d->lag_up.as<int32_t>(),
-                                                                  d->T, N, lag);
+                                                                  d->T, M, lag);
             JS_LAUNCH_CHECK();
         }
         k_phi<T, R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(psi, w, N, (int)M, nrhs, phi_new);

@@ -76,7 +76,8 @@ class jsweep_options(ctypes.Structure):
         ("cycle_search_max", ctypes.c_int),
         ("debug_block_waits", ctypes.c_int),
         ("layering", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("unit_order", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -90,6 +91,7 @@ class jsweep_timing(ctypes.Structure):
         ("call_launches", ctypes.c_int64),
         ("build_steps", ctypes.c_int64),
         ("build_stall_rounds", ctypes.c_int64),
+        ("build_phase_ms", ctypes.c_double * 6),
     ]
 
 
@@ -317,7 +319,7 @@ class Dags:
         return {"build_ms": t.build_ms, "sweep_ms": t.sweep_ms, "phi_ms": t.phi_ms,
                 "sweep_launches": t.sweep_launches, "build_launches": t.build_launches,
                 "call_launches": t.call_launches, "build_steps": t.build_steps,
-                "build_stall_rounds": t.build_stall_rounds}
+                "build_stall_rounds": t.build_stall_rounds, "build_phase_ms": list(t.build_phase_ms)}
 
 
 def jsweep_mesh_create(n_cells, n_faces, face_cells, normals, areas, volumes) -> Mesh:
