@@ -35,6 +35,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define JSWEEP_API __attribute__((visibility("default")))
+#else
+#define JSWEEP_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -97,21 +103,23 @@ typedef struct {
                               the waits run out and the call returns JSWEEP_ERR_DEVICE_TIMEOUT */
     int layering;          /* schedule layers (set at jsweep_build_dags): JSWEEP_LAYERS_OCTANT (default)
                               or JSWEEP_LAYERS_LEVEL; results do not depend on it */
+    int angles_per_warp;   /* data-driven schedule: units one warp runs side by side (1, 2 or 4; 0 =
+                              1); each holds up to 32 / angles_per_warp cells of one direction */
     int unit_order;        /* order of the work units inside a layer: 0 = direction by direction,
                               1 = interleaved across the directions of an octant (default), so that
                               units covering the same cells for different directions run side by side
                               and share the cells' geometry and sources in cache */
-    int reserved[5];
+    int reserved[4];
 } jsweep_options;
 
 /* Fill *opt with defaults. */
-int jsweep_options_default(jsweep_options *opt);
+JSWEEP_API int jsweep_options_default(jsweep_options *opt);
 
 /* Message of the calling thread's last failure ("" if none). */
-const char *jsweep_last_error(void);
+JSWEEP_API const char *jsweep_last_error(void);
 
 /* Library version as 10000*major + 100*minor + patch. */
-int jsweep_version(void);
+JSWEEP_API int jsweep_version(void);
 
 /* Route the library's own device allocations through the caller's allocator
  * (for example PyTorch's caching allocator).  alloc returns a device pointer
@@ -121,7 +129,7 @@ int jsweep_version(void);
  * the switch is released with the allocator that produced it. */
 typedef void *(*jsweep_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*jsweep_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
-int jsweep_set_allocator(jsweep_alloc_fn alloc, jsweep_free_fn free_fn, void *ctx);
+JSWEEP_API int jsweep_set_allocator(jsweep_alloc_fn alloc, jsweep_free_fn free_fn, void *ctx);
 
 /* ---- mesh ----------------------------------------------------------------
  * A mesh of n_cells polyhedral cells and n_faces faces (Sec. II-B: the patch
@@ -138,11 +146,11 @@ int jsweep_set_allocator(jsweep_alloc_fn alloc, jsweep_free_fn free_fn, void *ct
  * and closed cells: |sum_f +-a_f n_f| <= 1e-8 * sum_f a_f.
  * Boundary faces are numbered 0..n_bfaces-1 in increasing face id; inflow
  * arrays use that numbering. */
-int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cells,
+JSWEEP_API int jsweep_mesh_create(int64_t n_cells, int64_t n_faces, const int64_t *face_cells,
                        const double *normals, const double *areas, const double *volumes,
                        jsweep_mesh_t *out);
-int jsweep_mesh_destroy(jsweep_mesh_t mesh);
-int jsweep_mesh_info(jsweep_mesh_t mesh, int64_t *n_cells, int64_t *n_faces, int64_t *n_bfaces,
+JSWEEP_API int jsweep_mesh_destroy(jsweep_mesh_t mesh);
+JSWEEP_API int jsweep_mesh_info(jsweep_mesh_t mesh, int64_t *n_cells, int64_t *n_faces, int64_t *n_bfaces,
                      int *max_faces_per_cell);
 
 /* ---- quadrature ------------------------------------------------------------
@@ -158,10 +166,10 @@ int jsweep_mesh_info(jsweep_mesh_t mesh, int64_t *n_cells, int64_t *n_faces, int
  * jsweep_quadrature_create copies any direction set (host arrays): directions
  * must be finite and non-zero (they need not be unit vectors: a 1D slab test
  * uses (mu, 0, 0)); weights finite. */
-int jsweep_quadrature_product(int n_polar, int n_azim, double *dirs, double *weights);
-int jsweep_quadrature_create(int64_t n_dirs, const double *dirs, const double *weights,
+JSWEEP_API int jsweep_quadrature_product(int n_polar, int n_azim, double *dirs, double *weights);
+JSWEEP_API int jsweep_quadrature_create(int64_t n_dirs, const double *dirs, const double *weights,
                              jsweep_quad_t *out);
-int jsweep_quadrature_destroy(jsweep_quad_t quad);
+JSWEEP_API int jsweep_quadrature_destroy(jsweep_quad_t quad);
 
 /* ---- dependency graphs (Sec. V-A, Listing 1 init; cycle rule) -------------
  * Builds, on the device, for every direction m:
@@ -177,23 +185,25 @@ int jsweep_quadrature_destroy(jsweep_quad_t quad);
  * The result is resident on the device and stays valid while mesh and quad
  * live (the handle keeps its own references).  Errors: JSWEEP_ERR_CYCLE if a
  * strongly connected component exceeds opt->cycle_search_max cells. */
-int jsweep_build_dags(jsweep_mesh_t mesh, jsweep_quad_t quad, const jsweep_options *opt,
+JSWEEP_API int jsweep_build_dags(jsweep_mesh_t mesh, jsweep_quad_t quad, const jsweep_options *opt,
                       void *stream, jsweep_dags_t *out);
-int jsweep_dags_destroy(jsweep_dags_t dags);
+/* Releases the caller's reference; batch problems that use the handle keep it
+ * alive until they are removed. */
+JSWEEP_API int jsweep_dags_destroy(jsweep_dags_t dags);
 /* n_dirs, the largest level count over directions, total lagged (face, dir) pairs. */
-int jsweep_dags_info(jsweep_dags_t dags, int64_t *n_dirs, int64_t *max_levels, int64_t *n_lag_total);
-int jsweep_dags_nlevels(jsweep_dags_t dags, int64_t m, int64_t *nlevels);
+JSWEEP_API int jsweep_dags_info(jsweep_dags_t dags, int64_t *n_dirs, int64_t *max_levels, int64_t *n_lag_total);
+JSWEEP_API int jsweep_dags_nlevels(jsweep_dags_t dags, int64_t m, int64_t *nlevels);
 /* level_of_cell [n_cells] (host). */
-int jsweep_dags_levels(jsweep_dags_t dags, int64_t m, int32_t *level_of_cell);
+JSWEEP_API int jsweep_dags_levels(jsweep_dags_t dags, int64_t m, int32_t *level_of_cell);
 /* order [n_cells], level_ptr [nlevels+1] (host). */
-int jsweep_dags_order(jsweep_dags_t dags, int64_t m, int32_t *order, int32_t *level_ptr);
+JSWEEP_API int jsweep_dags_order(jsweep_dags_t dags, int64_t m, int32_t *order, int32_t *level_ptr);
 /* Lagged faces of direction m sorted by face id, rows (face, upwind cell,
  * downwind cell) into rows [*n][3] (host; may be NULL to query *n only). */
-int jsweep_dags_lagged(jsweep_dags_t dags, int64_t m, int64_t *rows, int64_t *n);
+JSWEEP_API int jsweep_dags_lagged(jsweep_dags_t dags, int64_t m, int64_t *rows, int64_t *n);
 /* Zero the lagged upwind values (the state a source iteration starts from). */
-int jsweep_dags_reset_lag(jsweep_dags_t dags);
+JSWEEP_API int jsweep_dags_reset_lag(jsweep_dags_t dags);
 /* Replace the sweep options (mode, priority, grain, ...) of a built handle. */
-int jsweep_dags_set_options(jsweep_dags_t dags, const jsweep_options *opt);
+JSWEEP_API int jsweep_dags_set_options(jsweep_dags_t dags, const jsweep_options *opt);
 
 /* ---- one transport sweep (Listing 1 compute/solve; Sec. V-B) -------------
  * Sweeps all directions for nrhs right-hand sides with the step (upwind
@@ -210,7 +220,7 @@ int jsweep_dags_set_options(jsweep_dags_t dags, const jsweep_options *opt);
  *   psi_out [nrhs][n_dirs][n_cells] (device) or NULL.
  * Uses the handle's lagged values and then replaces them by this sweep's.
  * 1 <= nrhs <= 8.  Device-side waits are bounded (JSWEEP_ERR_DEVICE_TIMEOUT). */
-int jsweep_sweep(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+JSWEEP_API int jsweep_sweep(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
                  const void *ang_source, const void *inflow, void *phi_out, void *psi_out,
                  void *stream);
 
@@ -223,10 +233,85 @@ int jsweep_sweep(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_
  *   jsweep_sweep, phi_out [nrhs][n_cells] (device).
  *   iters_out, resid_out (host, may be NULL): sweeps done, final residual.
  * Returns JSWEEP_ERR_NOT_CONVERGED (phi_out filled) after max_iters sweeps. */
-int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
                           const void *c_ratio, const void *q, const void *inflow, double tol,
                           int max_iters, void *phi_out, int *iters_out, double *resid_out,
                           void *stream);
+
+/* ---- batches: many independent problems in one persistent launch ----------
+ * Sec. V-B runs the (patch, angle) programs of all angles at once; a batch
+ * extends that to many independent problems (meshes, direction sets,
+ * right-hand sides, of uneven size): every source iteration sweeps all of the
+ * batch's active problems in one data-driven launch.  Its work units (up to
+ * 32 cells of one schedule layer of one direction of one problem) are merged
+ * by schedule slot, so each problem's units stay in a topological order of
+ * its graphs and the launch cannot deadlock.  The other steps of an iteration
+ * (emission source, lagged-value copy, phi with the FP64 residual, the
+ * convergence test) are batched kernels too, and the iteration is replayed
+ * from a CUDA graph.  Every problem keeps its own state and stops on its own
+ * test (residual below its tol, defined as for jsweep_source_iterate, or
+ * max_iters); its phi is bit-identical to what jsweep_source_iterate returns
+ * for it alone with the same precision and nrhs.
+ *
+ * Problems are identified by the id jsweep_batch_add returns (stable until
+ * the problem is removed).  Problems may be added and removed between calls,
+ * so a server can admit new requests while others are still iterating
+ * (continuous batching).  A handle used by a batch problem stays alive until
+ * the problem is removed, even if jsweep_dags_destroy is called meanwhile.
+ * Calls on one batch must not overlap in time.
+ *
+ *   jsweep_batch_create: precision and nrhs shared by the batch's problems;
+ *     opt (may be NULL) sets cluster_cells, angles_per_warp, unit_order,
+ *     priority, spin_timeout_s and debug_block_waits of the batched launch.
+ *   jsweep_batch_problem_bytes: device bytes that jsweep_batch_add will
+ *     allocate for a problem on this handle (its workspaces: psi, epoch flags,
+ *     source records, lagged values, two phi buffers, inflow copy).
+ *   jsweep_batch_add: a built handle and the problem's device arrays, laid out
+ *     as for jsweep_source_iterate (sigma_t, c_ratio [N], q [nrhs][N], inflow
+ *     [nrhs][n_bfaces] or NULL, phi_out [nrhs][N]); they must stay valid until
+ *     the problem is removed.  The problem starts from phi = 0 at the next
+ *     step.  tol >= 0, 1 <= max_iters < 2^30.  Allocates the workspaces now
+ *     (JSWEEP_ERR_OOM if that fails; nothing is added then).
+ *   jsweep_batch_step: up to n_sweeps source iterations of every active
+ *     problem, then waits for them; a problem that finished during the call
+ *     has phi_out written before the call returns.  *n_active (may be NULL)
+ *     receives the number of problems still iterating.
+ *   jsweep_batch_query: state (JSWEEP_PROBLEM_*), sweeps done and last
+ *     residual of a problem (pointers may be NULL).
+ *   jsweep_batch_remove: drops a problem and frees its workspaces.
+ *   jsweep_batch_source_iterate: restarts every problem from phi = 0 and
+ *     steps until none is active; iters_out / resid_out (host, may be NULL)
+ *     receive one entry per problem in increasing id.  Returns
+ *     JSWEEP_ERR_NOT_CONVERGED if a problem stopped at max_iters.
+ *   jsweep_batch_autotune: for each candidate (cluster_cells, angles_per_warp,
+ *     unit_order) times one batched iteration and keeps the fastest; *best_ms
+ *     (may be NULL) receives its time.  It restarts every problem from
+ *     phi = 0, as jsweep_batch_source_iterate does.
+ *   jsweep_batch_stats: device time of the last batched sweep launch and of
+ *     the whole last iteration, in ms, and the number of kernels the batch
+ *     has launched since it was created (pointers may be NULL).
+ */
+#define JSWEEP_BATCH_MAX_PROBLEMS 65536
+#define JSWEEP_PROBLEM_ACTIVE 0    /* still iterating */
+#define JSWEEP_PROBLEM_CONVERGED 1 /* residual below tol; phi_out written */
+#define JSWEEP_PROBLEM_MAX_ITERS 2 /* stopped at max_iters; phi_out written */
+JSWEEP_API int jsweep_batch_create(int precision, int nrhs, const jsweep_options *opt, jsweep_batch_t *out);
+JSWEEP_API int jsweep_batch_problem_bytes(jsweep_batch_t batch, jsweep_dags_t dags, int has_inflow,
+                                          int64_t *bytes);
+JSWEEP_API int jsweep_batch_add(jsweep_batch_t batch, jsweep_dags_t dags, const void *sigma_t,
+                                const void *c_ratio, const void *q, const void *inflow, void *phi_out,
+                                double tol, int max_iters, int64_t *id, void *stream);
+JSWEEP_API int jsweep_batch_step(jsweep_batch_t batch, int n_sweeps, int64_t *n_active, void *stream);
+JSWEEP_API int jsweep_batch_query(jsweep_batch_t batch, int64_t id, int *state, int *iters, double *resid);
+JSWEEP_API int jsweep_batch_remove(jsweep_batch_t batch, int64_t id);
+JSWEEP_API int jsweep_batch_clear(jsweep_batch_t batch);
+JSWEEP_API int jsweep_batch_size(jsweep_batch_t batch, int64_t *n_problems);
+JSWEEP_API int jsweep_batch_source_iterate(jsweep_batch_t batch, int *iters_out, double *resid_out,
+                                           void *stream);
+JSWEEP_API int jsweep_batch_autotune(jsweep_batch_t batch, void *stream, double *best_ms);
+JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double *iteration_ms,
+                                  int64_t *launches);
+JSWEEP_API int jsweep_batch_destroy(jsweep_batch_t batch);
 
 /* ---- source iteration that allocates no device memory ----------------------
  * The paper has no counterpart to this entry point; it exists for callers that
@@ -253,7 +338,7 @@ int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const voi
  *   - The handle must have been built (jsweep_build_dags); its level arrays,
  *     lag lists, mesh and directions are read, never written. */
 #define JSWEEP_NOALLOC_SCRATCH_BYTES (64ull << 20)
-int jsweep_source_iterate_noalloc(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
+JSWEEP_API int jsweep_source_iterate_noalloc(jsweep_dags_t dags, int nrhs, int precision, const void *sigma_t,
                                   const void *c_ratio, const void *q, const void *inflow, double tol,
                                   int max_iters, void *phi_out, int *iters_out, double *resid_out,
                                   void *stream);
@@ -272,7 +357,7 @@ typedef struct {
                                    face classification, [2] frontier steps with cycle resolution,
                                    [3] level-major order, [4] lag lists, [5] schedule layers */
 } jsweep_timing;
-int jsweep_dags_timing(jsweep_dags_t dags, jsweep_timing *t);
+JSWEEP_API int jsweep_dags_timing(jsweep_dags_t dags, jsweep_timing *t);
 
 #ifdef __cplusplus
 }

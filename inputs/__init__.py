@@ -12,4 +12,7 @@ from .workloads import (  # noqa: F401
     make_workload,
     lognormal_blocks_sigma,
     batch_problem_specs,
+    make_batch_problem,
+    tets_edge_for_cells,
+    QUAD_BY_NDIRS,
 )

@@ -91,6 +91,12 @@ void mesh_release(Mesh *m) {
 void quad_release(Quad *q) {
     if (q && q->refs.fetch_sub(1) == 1) delete q;
 }
+void dags_release(Dags *d) {
+    if (d && d->refs.fetch_sub(1) == 1) {
+        cudaDeviceSynchronize();
+        delete d;
+    }
+}
 
 Dags::~Dags() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -168,6 +174,7 @@ int jsweep_options_default(jsweep_options *opt) {
     opt->spin_timeout_s = 2.0;
     opt->cycle_search_max = 256;
     opt->unit_order = 1;
+    opt->angles_per_warp = 1;
     return JSWEEP_OK;
 }
 
@@ -439,7 +446,11 @@ int jsweep_quadrature_destroy(jsweep_quad_t quad) {
 }
 
 // ---- dependency graphs --------------------------------------------------------------
-static int check_options(const jsweep_options *opt, jsweep_options *o) {
+}  // extern "C"
+
+namespace js {
+// Validated copy of the caller's options (defaults where unset).
+int check_options(const jsweep_options *opt, jsweep_options *o) {
     jsweep_options_default(o);
     if (!opt) return JSWEEP_OK;
     if (opt->struct_size != (int)sizeof(jsweep_options)) {
@@ -471,8 +482,17 @@ static int check_options(const jsweep_options *opt, jsweep_options *o) {
         return JSWEEP_ERR_INVALID_ARG;
     }
     o->unit_order = opt->unit_order;
+    if (opt->angles_per_warp != 0 && opt->angles_per_warp != 1 && opt->angles_per_warp != 2 &&
+        opt->angles_per_warp != 4) {
+        set_error("jsweep_options.angles_per_warp=%d (1, 2 or 4)", opt->angles_per_warp);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    o->angles_per_warp = opt->angles_per_warp > 0 ? opt->angles_per_warp : 1;
     return JSWEEP_OK;
 }
+}  // namespace js
+
+extern "C" {
 
 int jsweep_build_dags(jsweep_mesh_t mesh, jsweep_quad_t quad, const jsweep_options *opt,
                       void *stream, jsweep_dags_t *out) {
@@ -511,10 +531,7 @@ int jsweep_build_dags(jsweep_mesh_t mesh, jsweep_quad_t quad, const jsweep_optio
 }
 
 int jsweep_dags_destroy(jsweep_dags_t dags) {
-    if (dags) {
-        cudaDeviceSynchronize();
-        delete impl(dags);
-    }
+    dags_release(impl(dags));  // a batch that still uses the handle keeps it alive
     return JSWEEP_OK;
 }
 

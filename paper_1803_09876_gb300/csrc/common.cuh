@@ -108,6 +108,7 @@ struct UnitTable {
 };
 
 struct Dags {
+    std::atomic<int> refs{1};  // the handle and every batch problem that uses it
     Mesh *mesh = nullptr;
     Quad *quad = nullptr;
     jsweep_options opt{};
@@ -155,12 +156,14 @@ struct Dags {
 
 void mesh_release(Mesh *m);
 void quad_release(Quad *q);
+void dags_release(Dags *d);
 
 // dag build (dag_build.cu)
 int build_dags(Dags *d, cudaStream_t s);
 
 // unit schedules and sweeps (sweep.cu)
 int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s);
+int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s);  // FP64 directions as [M][4]
 int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source,
               const void *inflow, void *phi_out, void *psi_out, cudaStream_t s);
 int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio,
@@ -181,6 +184,7 @@ inline int grid_for(int64_t n, int block, int64_t cap = 1 << 20) {
 }
 
 int device_sm_count();
+int check_options(const jsweep_options *opt, jsweep_options *o);
 
 }  // namespace js
 

@@ -1,250 +1,40 @@
-// Sweeps and source iteration on the device.
+// Sweeps and source iteration of one problem on the device.
 //
-// Work unit: up to `cluster_cells` (<= 32) consecutive cells of one level of
-// one direction in the level-major order (vertex clustering, Sec. V-C); one
-// warp processes a unit, one lane per cell.  Cells of one level never depend
-// on each other, so a unit needs no internal ordering.
+// Work unit: up to `cluster_cells` (<= 32 / SPLIT) consecutive cells of one
+// schedule layer of one direction (vertex clustering, Sec. V-C); one warp
+// processes a unit, SPLIT lanes per cell.  Cells of one layer never depend on
+// each other, so a unit needs no internal ordering.
 //
 // Two schedules (Sec. V-B patch-angle parallelism: all directions progress
 // together):
-//   level-synchronous: one launch per level index covering that level of all
-//     directions; the launches are captured once into a CUDA graph and
-//     replayed.
-//   persistent: one launch of resident warps that take units from a global
-//     ticket counter in a precomputed priority order (a topological order of
-//     the units); a unit waits until its direction has completed every unit
-//     of the levels before its own (per-direction done counter; acquire/
-//     release ordering), with a bounded spin that reports
-//     JSWEEP_ERR_DEVICE_TIMEOUT instead of hanging.  Tickets are dispensed in
-//     order and a warp finishes its unit before taking the next, so the
-//     oldest unfinished unit never waits on anything: no deadlock, whatever
-//     the number of resident warps.
+//   level-synchronous: one launch per schedule slot covering that slot's
+//     layers of all directions; the launches are captured once into a CUDA
+//     graph and replayed.
+//   data-driven (persistent): one launch of resident warps; unit t of the
+//     slot-ordered table goes to warp t mod W, and each cell waits (bounded
+//     spin, acquire) for its own upwind cells' epoch flags, then releases its
+//     own.  The table is a topological order of every direction's graph, so
+//     the smallest unfinished unit always has its producers done: no
+//     deadlock while every warp is resident.
 //
-// Per-cell solve (step scheme):  psi = (S V + sum_in |Omega.A_f| psi_up) /
-// (sigma_t V + sum_out Omega.A_f), with A_f the outward vector area; the
-// incoming faces are the ones the FP64 classification marked (never a
-// recomputed low-precision sign), so a grazing face cannot read an upwind
-// value that is not written yet.
+// Per-cell solve (step scheme, Sec. II-C): see solve_cell in sweep_cell.cuh.
 //
-// Layouts: psi [M][N][R] (the R right-hand sides of one cell-direction are
-// contiguous: one 32-byte sector for R = 8 in FP32), sources [N][R]
-// premultiplied by the cell volume, lagged values [T][R].
+// Layouts: psi [N][M][R] (cell-major: a cell's directions are contiguous, the
+// R right-hand sides of one cell-direction form one 16/32-byte piece), source
+// records [N][RS] (S V of each rhs, then sigma_t V), lagged values [T][R].
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
 #include "common.cuh"
+#include "sweep_cell.cuh"
 
 namespace js {
 
+using namespace dev;
+
 namespace {
-
-constexpr int kWarpsPerBlock = 8;
-
-template <class T> struct V4;
-template <> struct V4<float> { using type = float4; };
-template <> struct V4<double> { using type = double4; };
-
-template <class T> struct SweepArgs {
-    int64_t N;
-    int M, FS, GS, Fb;
-    const int32_t *order;
-    const uint8_t *mask;
-    const typename V4<T>::type *geo;
-    const T *dirs;  // [M][4] (x, y, z, 0)
-    const T *srcv;  // [N][RS]: S V of each rhs at [0, R), sigma_t V at [R]
-    const T *inflow;  // [R][Fb] or null
-    T *psi;           // [N][M][R]
-    const T *psi_lag; // [Tl][R]
-    const int32_t *lag_ptr, *lag_face, *sface;
-    const int4 *units;
-};
-
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
-
-template <class T> __device__ __forceinline__ int nbr_bits(const typename V4<T>::type &g);
-template <> __device__ __forceinline__ int nbr_bits<float>(const float4 &g) { return __float_as_int(g.w); }
-template <> __device__ __forceinline__ int nbr_bits<double>(const double4 &g) {
-    return (int)__double_as_longlong(g.w);
-}
-
-// R contiguous values through L2 (bypassing L1: values written by other SMs
-// during a persistent sweep must not be served from a stale L1 line).
-template <class T, int R> __device__ __forceinline__ void load_cg(const T *p, T (&v)[R]) {
-    if constexpr (sizeof(T) * R % 16 == 0) {
-        constexpr int n16 = sizeof(T) * R / 16;
-#pragma unroll
-        for (int i = 0; i < n16; ++i) {
-            float4 x = __ldcg(reinterpret_cast<const float4 *>(p) + i);
-            memcpy(reinterpret_cast<char *>(v) + 16 * i, &x, 16);
-        }
-    } else if constexpr (sizeof(T) * R == 8) {
-        float2 x = __ldcg(reinterpret_cast<const float2 *>(p));
-        memcpy(v, &x, 8);
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = __ldcg(p + r);
-    }
-}
-
-template <class T, int R> __device__ __forceinline__ void load_ro(const T *p, T (&v)[R]) {
-    if constexpr (sizeof(T) * R % 16 == 0) {
-        constexpr int n16 = sizeof(T) * R / 16;
-#pragma unroll
-        for (int i = 0; i < n16; ++i) {
-            float4 x = __ldg(reinterpret_cast<const float4 *>(p) + i);
-            memcpy(reinterpret_cast<char *>(v) + 16 * i, &x, 16);
-        }
-    } else if constexpr (sizeof(T) * R == 8) {
-        float2 x = __ldg(reinterpret_cast<const float2 *>(p));
-        memcpy(v, &x, 8);
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = __ldg(p + r);
-    }
-}
-
-template <class T, int R> __device__ __forceinline__ void store_cg(T *p, const T (&v)[R]) {
-    if constexpr (sizeof(T) * R % 16 == 0) {
-        constexpr int n16 = sizeof(T) * R / 16;
-#pragma unroll
-        for (int i = 0; i < n16; ++i) {
-            float4 x;
-            memcpy(&x, reinterpret_cast<const char *>(v) + 16 * i, 16);
-            __stcg(reinterpret_cast<float4 *>(p) + i, x);
-        }
-    } else if constexpr (sizeof(T) * R == 8) {
-        float2 x;
-        memcpy(&x, v, 8);
-        __stcg(reinterpret_cast<float2 *>(p), x);
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) __stcg(p + r, v[r]);
-    }
-}
-
-// Index of the lagged face f of direction m in the lag list, or -1.
-__device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *lag_face, int m, int32_t f) {
-    int lo = lag_ptr[m], hi = lag_ptr[m + 1];
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (lag_face[mid] < f) lo = mid + 1; else hi = mid;
-    }
-    return (lo < lag_ptr[m + 1] && lag_face[lo] == f) ? lo : -1;
-}
-
-// Source record stride: the R values S V, then sigma_t V, padded so that a
-// record is 8, 16, 32 or 64 bytes (FP32) and one DRAM transaction brings both.
-template <int R> constexpr int src_stride() { return R >= 4 ? 2 * R : (R == 2 ? 4 : 2); }
-
-__device__ __forceinline__ void st_release(int *p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Per-cell geometry and bookkeeping shared by the sweep kernels.
-template <class T, int MAXF> struct CellGeo {
-    typename V4<T>::type g[MAXF];
-};
-
-// One (cell, direction) for RH = R / SPLIT right-hand sides, sub-range `sub`
-// (SPLIT lanes cooperate on one cell so that each lane moves 16-byte pieces
-// and a 32-byte sector is read by one warp instruction).  MAXF >= faces per
-// cell; the face loop is unrolled so that the geometry loads of all faces, and
-// then the upwind loads of all incoming faces, are in flight together.
-// WAIT: before reading an upwind cell's psi, spin (bounded) until that cell's
-// flag for this direction shows the current sweep epoch (data-driven schedule).
-template <class T, int R, int SPLIT, int MAXF, bool WAIT>
-__device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
-                                           const int *flags, int want, int *err, long long timeout) {
-    using V = typename V4<T>::type;
-    constexpr int RH = R / SPLIT;
-    const T ox = a.dirs[4 * m], oy = a.dirs[4 * m + 1], oz = a.dirs[4 * m + 2];
-    const V *g = a.geo + (int64_t)c * a.GS;
-    V gk[MAXF];
-#pragma unroll
-    for (int k = 0; k < MAXF; ++k) {
-        if (k < a.FS) gk[k] = g[k];
-        else gk[k] = V{T(0), T(0), T(0), T(0)};
-    }
-    constexpr int RS = src_stride<R>();
-    T num[RH];
-    load_ro<T, RH>(a.srcv + (int64_t)c * RS + sub * RH, num);
-    T den = __ldg(a.srcv + (int64_t)c * RS + R);
-    // lagged faces (rare): bit k set when face slot k takes the previous sweep's value
-    unsigned lagk = 0;
-    int lagj[MAXF];
-    if (msk & 0x80u) {
-#pragma unroll
-        for (int k = 0; k < MAXF; ++k) {
-            lagj[k] = -1;
-            if (((msk >> k) & 1u) && nbr_bits<T>(gk[k]) >= 0) {
-                int j = lag_index(a.lag_ptr, a.lag_face, m, a.sface[(int64_t)c * a.FS + k] >> 1);
-                lagj[k] = j;
-                if (j >= 0) lagk |= 1u << k;
-            }
-        }
-    }
-    if constexpr (WAIT) {
-        // wait until every active interior upwind cell of this direction is done
-        const int *fm = flags + (int64_t)m * a.N;
-#pragma unroll
-        for (int k = 0; k < MAXF; ++k) {
-            const int nb = nbr_bits<T>(gk[k]);
-            if (((msk >> k) & 1u) && !((lagk >> k) & 1u) && nb >= 0) {
-                if (ld_acquire(fm + nb) != want) {
-                    const long long t0 = clock64();
-                    int ns = 32;
-                    while (ld_acquire(fm + nb) != want) {
-                        if (ld_volatile(err) != 0) return false;
-                        if (clock64() - t0 > timeout) {
-                            atomicCAS(err, 0, 1);
-                            return false;
-                        }
-                        __nanosleep(ns);
-                        ns = ns < 1024 ? 2 * ns : 1024;
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < MAXF; ++k) {
-        const T d = ox * gk[k].x + oy * gk[k].y + oz * gk[k].z;
-        if ((msk >> k) & 1u) {
-            const T wf = fabs(d);
-            const int nb = nbr_bits<T>(gk[k]);
-            T up[RH];
-            if (nb >= 0) {
-                if ((lagk >> k) & 1u) {
-                    load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
-                } else {
-                    load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
-                }
-            } else {
-                const int b = -nb - 1;
-#pragma unroll
-                for (int r = 0; r < RH; ++r)
-                    up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
-            }
-#pragma unroll
-            for (int r = 0; r < RH; ++r) num[r] = num[r] + wf * up[r];
-        } else {
-            den += d > T(0) ? d : T(0);
-        }
-    }
-    T out[RH];
-#pragma unroll
-    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
-    store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
-    return true;
-}
 
 // Level-synchronous sweep: one launch per time slot; a warp handles one unit
 // of 32 / SPLIT cells.
@@ -404,59 +194,16 @@ __global__ void k_source_prep(const T *sig, const T *src, const T *vol, int64_t 
     }
 }
 
-// phi[r][c] = sum_m w_m psi[c][m][r]: one warp per cell reads the cell's
-// contiguous [M][R] block (coalesced); lane l sums directions l, l+32, ... in
-// increasing order (FP32: Kahan-compensated), then the 32 partial sums are
-// combined by a fixed butterfly with error-free two-sums.  The order of every
-// operation is fixed, so phi does not depend on the sweep's schedule.
-template <class T>
-__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
-    s = a + b;
-    T bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
 template <class T, int R>
 __global__ void k_phi(const T *psi, const T *w, int64_t N, int M, int nrhs, T *phi) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < N; c += warps) {
-        T s[R], comp[R];
+        T v[R];
+        phi_warp<T, R>(psi + (int64_t)c * M * R, w, M, lane, v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[r] = comp[r] = T(0);
-        const T *blk = psi + (int64_t)c * M * R;
-        for (int m = lane; m < M; m += 32) {
-            T x[R];
-            load_cg<T, R>(blk + (int64_t)m * R, x);
-            const T wm = w[m];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if constexpr (sizeof(T) == 4) {
-                    T y = wm * x[r] - comp[r];
-                    T t = s[r] + y;
-                    comp[r] = (t - s[r]) - y;
-                    s[r] = t;
-                } else {
-                    s[r] = s[r] + wm * x[r];
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            T v = s[r], e = -comp[r];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ov = __shfl_xor_sync(0xffffffffu, v, off);
-                const T oe = __shfl_xor_sync(0xffffffffu, e, off);
-                // combine the lower and the upper lane in the same order on both sides
-                const bool lower = (lane & off) == 0;
-                T ss, ee;
-                two_sum(lower ? v : ov, lower ? ov : v, ss, ee);
-                v = ss;
-                e = (lower ? e : oe) + (lower ? oe : e) + ee;
-            }
-            if (lane == 0 && r < nrhs) phi[(int64_t)r * N + c] = v + e;
-        }
+        for (int r = 0; r < R; ++r)
+            if (lane == 0 && r < nrhs) phi[(int64_t)r * N + c] = v[r];
     }
 }
 
@@ -593,11 +340,9 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
     int64_t last_base = 0, last_cnt = 0;
     JS_CUDA(cudaMemcpyAsync(&last_base, base2.as<int64_t>() + Tmax * M - 1, 8, cudaMemcpyDeviceToHost, s));
     JS_CUDA(cudaMemcpyAsync(&last_cnt, cnt2.as<int64_t>() + Tmax * M - 1, 8, cudaMemcpyDeviceToHost, s));
-    std::vector<int64_t> b2h;
-    if (mode == JSWEEP_MODE_LEVEL_SYNC) {  // one launch per time slot t = level + offset(direction)
-        b2h.resize(Tmax * M);
-        JS_CUDA(cudaMemcpyAsync(b2h.data(), base2.p, Tmax * M * 8, cudaMemcpyDeviceToHost, s));
-    }
+    // slot boundaries (level-synchronous launches; merging of batched problems)
+    std::vector<int64_t> b2h(Tmax * M);
+    JS_CUDA(cudaMemcpyAsync(b2h.data(), base2.p, Tmax * M * 8, cudaMemcpyDeviceToHost, s));
     JS_CUDA(cudaStreamSynchronize(s));
     const int64_t n_units = last_base + last_cnt;
     JS_TRY(ut.units.alloc(std::max<int64_t>(n_units, 1) * 16, s));
@@ -609,12 +354,9 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
                                                               gof_d.as<int32_t>(), qpos_d.as<int32_t>(), order,
                                                               ut.units.as<int4>());
     JS_LAUNCH_CHECK();
-    ut.slot_ptr.clear();
-    if (mode == JSWEEP_MODE_LEVEL_SYNC) {
-        ut.slot_ptr.resize(Tmax + 1);
-        for (int64_t t = 0; t < Tmax; ++t) ut.slot_ptr[t] = b2h[t * M];
-        ut.slot_ptr[Tmax] = n_units;
-    }
+    ut.slot_ptr.resize(Tmax + 1);
+    for (int64_t t = 0; t < Tmax; ++t) ut.slot_ptr[t] = b2h[t * M];
+    ut.slot_ptr[Tmax] = n_units;
     JS_CUDA(cudaStreamSynchronize(s));
     ut.n_units = n_units;
     ut.mode = mode;
@@ -628,6 +370,20 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
         d->graph = nullptr;
         d->graph_key.clear();
     }
+    return JSWEEP_OK;
+}
+
+// dirs as [M][4] in the working precision
+int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s) {
+    if (buf.p) return JSWEEP_OK;
+    std::vector<double> v(4 * d->M);
+    for (int64_t m = 0; m < d->M; ++m) {
+        for (int k = 0; k < 3; ++k) v[4 * m + k] = d->quad->dirs[3 * m + k];
+        v[4 * m + 3] = 0.0;
+    }
+    JS_TRY(buf.alloc(v.size() * 8, s));
+    JS_CUDA(cudaMemcpyAsync(buf.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaStreamSynchronize(s));
     return JSWEEP_OK;
 }
 
@@ -692,20 +448,6 @@ int ensure_workspace(Dags *d, int prec, int Rp, int nrhs, cudaStream_t s) {
         d->graph = nullptr;
         d->graph_key.clear();
     }
-    return JSWEEP_OK;
-}
-
-// dirs as [M][4] in the working precision
-int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s) {
-    if (buf.p) return JSWEEP_OK;
-    std::vector<double> v(4 * d->M);
-    for (int64_t m = 0; m < d->M; ++m) {
-        for (int k = 0; k < 3; ++k) v[4 * m + k] = d->quad->dirs[3 * m + k];
-        v[4 * m + 3] = 0.0;
-    }
-    JS_TRY(buf.alloc(v.size() * 8, s));
-    JS_CUDA(cudaMemcpyAsync(buf.p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s));
-    JS_CUDA(cudaStreamSynchronize(s));
     return JSWEEP_OK;
 }
 

@@ -1,0 +1,278 @@
+// Device code shared by the single-problem sweeps (sweep.cu) and the batched
+// sweeps (batch.cu): the argument block of one problem, cached/uncached vector
+// loads, the per-cell upwind solve and the warp reduction of phi.
+#pragma once
+
+#include <climits>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace js {
+namespace dev {
+
+constexpr int kWarpsPerBlock = 8;
+
+template <class T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+template <class T> struct SweepArgs {
+    int64_t N;
+    int M, FS, GS, Fb;
+    const int32_t *order;
+    const uint8_t *mask;
+    const typename V4<T>::type *geo;
+    const T *dirs;  // [M][4] (x, y, z, 0)
+    const T *srcv;  // [N][RS]: S V of each rhs at [0, R), sigma_t V at [R]
+    const T *inflow;  // [R][Fb] or null
+    T *psi;           // [N][M][R]
+    const T *psi_lag; // [Tl][R]
+    const int32_t *lag_ptr, *lag_face, *sface;
+    const int4 *units;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+template <class T> __device__ __forceinline__ int nbr_bits(const typename V4<T>::type &g);
+template <> __device__ __forceinline__ int nbr_bits<float>(const float4 &g) { return __float_as_int(g.w); }
+template <> __device__ __forceinline__ int nbr_bits<double>(const double4 &g) {
+    return (int)__double_as_longlong(g.w);
+}
+
+// R contiguous values through L2 (bypassing L1: values written by other SMs
+// during a persistent sweep must not be served from a stale L1 line).
+template <class T, int R> __device__ __forceinline__ void load_cg(const T *p, T (&v)[R]) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+            memcpy(reinterpret_cast<char *>(v) + 16 * i, &x, 16);
+        }
+    } else if constexpr (sizeof(T) * R == 8) {
+        float2 x = __ldcg(reinterpret_cast<const float2 *>(p));
+        memcpy(v, &x, 8);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldcg(p + r);
+    }
+}
+
+template <class T, int R> __device__ __forceinline__ void load_ro(const T *p, T (&v)[R]) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            memcpy(reinterpret_cast<char *>(v) + 16 * i, &x, 16);
+        }
+    } else if constexpr (sizeof(T) * R == 8) {
+        float2 x = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(v, &x, 8);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = __ldg(p + r);
+    }
+}
+
+template <class T, int R> __device__ __forceinline__ void store_cg(T *p, const T (&v)[R]) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x;
+            memcpy(&x, reinterpret_cast<const char *>(v) + 16 * i, 16);
+            __stcg(reinterpret_cast<float4 *>(p) + i, x);
+        }
+    } else if constexpr (sizeof(T) * R == 8) {
+        float2 x;
+        memcpy(&x, v, 8);
+        __stcg(reinterpret_cast<float2 *>(p), x);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcg(p + r, v[r]);
+    }
+}
+
+// Index of the lagged face f of direction m in the lag list, or -1.
+__device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *lag_face, int m, int32_t f) {
+    int lo = lag_ptr[m], hi = lag_ptr[m + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (lag_face[mid] < f) lo = mid + 1; else hi = mid;
+    }
+    return (lo < lag_ptr[m + 1] && lag_face[lo] == f) ? lo : -1;
+}
+
+// Source record stride: the R values S V, then sigma_t V, padded so that a
+// record is 8, 16, 32 or 64 bytes (FP32) and one DRAM transaction brings both.
+template <int R> constexpr int src_stride() { return R >= 4 ? 2 * R : (R == 2 ? 4 : 2); }
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Per-cell geometry and bookkeeping shared by the sweep kernels.
+template <class T, int MAXF> struct CellGeo {
+    typename V4<T>::type g[MAXF];
+};
+
+// One (cell, direction) for RH = R / SPLIT right-hand sides, sub-range `sub`
+// (SPLIT lanes cooperate on one cell so that each lane moves 16-byte pieces
+// and a 32-byte sector is read by one warp instruction).  MAXF >= faces per
+// cell; the face loop is unrolled so that the geometry loads of all faces, and
+// then the upwind loads of all incoming faces, are in flight together.
+// WAIT: before reading an upwind cell's psi, spin (bounded) until that cell's
+// flag for this direction shows the current sweep epoch (data-driven schedule).
+template <class T, int R, int SPLIT, int MAXF, bool WAIT>
+__device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
+                                           const int *flags, int want, int *err, long long timeout) {
+    using V = typename V4<T>::type;
+    constexpr int RH = R / SPLIT;
+    const T ox = a.dirs[4 * m], oy = a.dirs[4 * m + 1], oz = a.dirs[4 * m + 2];
+    const V *g = a.geo + (int64_t)c * a.GS;
+    V gk[MAXF];
+#pragma unroll
+    for (int k = 0; k < MAXF; ++k) {
+        if (k < a.FS) gk[k] = g[k];
+        else gk[k] = V{T(0), T(0), T(0), T(0)};
+    }
+    constexpr int RS = src_stride<R>();
+    T num[RH];
+    load_ro<T, RH>(a.srcv + (int64_t)c * RS + sub * RH, num);
+    T den = __ldg(a.srcv + (int64_t)c * RS + R);
+    // lagged faces (rare): bit k set when face slot k takes the previous sweep's value
+    unsigned lagk = 0;
+    int lagj[MAXF];
+    if (msk & 0x80u) {
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            lagj[k] = -1;
+            if (((msk >> k) & 1u) && nbr_bits<T>(gk[k]) >= 0) {
+                int j = lag_index(a.lag_ptr, a.lag_face, m, a.sface[(int64_t)c * a.FS + k] >> 1);
+                lagj[k] = j;
+                if (j >= 0) lagk |= 1u << k;
+            }
+        }
+    }
+    if constexpr (WAIT) {
+        // wait until every active interior upwind cell of this direction is done
+        const int *fm = flags + (int64_t)m * a.N;
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            const int nb = nbr_bits<T>(gk[k]);
+            if (((msk >> k) & 1u) && !((lagk >> k) & 1u) && nb >= 0) {
+                if (ld_acquire(fm + nb) != want) {
+                    const long long t0 = clock64();
+                    int ns = 32;
+                    while (ld_acquire(fm + nb) != want) {
+                        if (ld_volatile(err) != 0) return false;
+                        if (clock64() - t0 > timeout) {
+                            atomicCAS(err, 0, 1);
+                            return false;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 1024 ? 2 * ns : 1024;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MAXF; ++k) {
+        const T d = ox * gk[k].x + oy * gk[k].y + oz * gk[k].z;
+        if ((msk >> k) & 1u) {
+            const T wf = fabs(d);
+            const int nb = nbr_bits<T>(gk[k]);
+            T up[RH];
+            if (nb >= 0) {
+                if ((lagk >> k) & 1u) {
+                    load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
+                } else {
+                    load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
+                }
+            } else {
+                const int b = -nb - 1;
+#pragma unroll
+                for (int r = 0; r < RH; ++r)
+                    up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
+            }
+#pragma unroll
+            for (int r = 0; r < RH; ++r) num[r] = num[r] + wf * up[r];
+        } else {
+            den += d > T(0) ? d : T(0);
+        }
+    }
+    T out[RH];
+#pragma unroll
+    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
+    store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
+    return true;
+}
+
+// phi[r][c] = sum_m w_m psi[c][m][r]: one warp per cell reads the cell's
+// contiguous [M][R] block (coalesced); lane l sums directions l, l+32, ... in
+// increasing order (FP32: Kahan-compensated), then the 32 partial sums are
+// combined by a fixed butterfly with error-free two-sums.  The order of every
+// operation is fixed, so phi does not depend on the sweep's schedule.
+template <class T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+    s = a + b;
+    T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// phi of one cell: lane l sums directions l, l+32, ... of the cell's
+// contiguous [M][R] block in increasing order (FP32: Kahan-compensated), then
+// the 32 partial sums are combined by a fixed butterfly of error-free
+// two-sums.  The order of every operation is fixed, so phi does not depend on
+// the sweep's schedule or on which kernel calls this; every lane returns the
+// full sum.
+template <class T, int R>
+__device__ __forceinline__ void phi_warp(const T *blk, const T *w, int M, int lane, T (&out)[R]) {
+    T s[R], comp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[r] = comp[r] = T(0);
+    for (int m = lane; m < M; m += 32) {
+        T x[R];
+        load_cg<T, R>(blk + (int64_t)m * R, x);
+        const T wm = w[m];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if constexpr (sizeof(T) == 4) {
+                T y = wm * x[r] - comp[r];
+                T t = s[r] + y;
+                comp[r] = (t - s[r]) - y;
+                s[r] = t;
+            } else {
+                s[r] = s[r] + wm * x[r];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        T v = s[r], e = -comp[r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, v, off);
+            const T oe = __shfl_xor_sync(0xffffffffu, e, off);
+            // combine the lower and the upper lane in the same order on both sides
+            const bool lower = (lane & off) == 0;
+            T ss, ee;
+            two_sum(lower ? v : ov, lower ? ov : v, ss, ee);
+            v = ss;
+            e = (lower ? e : oe) + (lower ? oe : e) + ee;
+        }
+        out[r] = v + e;
+    }
+}
+
+}  // namespace dev
+}  // namespace js

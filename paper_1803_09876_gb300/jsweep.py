@@ -55,6 +55,9 @@ EXPORTED = [
     "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
     "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
     "jsweep_source_iterate_noalloc",
+    "jsweep_batch_create", "jsweep_batch_problem_bytes", "jsweep_batch_add", "jsweep_batch_step",
+    "jsweep_batch_query", "jsweep_batch_remove", "jsweep_batch_clear", "jsweep_batch_size",
+    "jsweep_batch_source_iterate", "jsweep_batch_autotune", "jsweep_batch_stats", "jsweep_batch_destroy",
 ]
 
 
@@ -76,8 +79,9 @@ class jsweep_options(ctypes.Structure):
         ("cycle_search_max", ctypes.c_int),
         ("debug_block_waits", ctypes.c_int),
         ("layering", ctypes.c_int),
+        ("angles_per_warp", ctypes.c_int),
         ("unit_order", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -154,6 +158,18 @@ def load(path: str = LIB_PATH):
             "jsweep_source_iterate": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
             "jsweep_dags_timing": (I, [P, P]),
             "jsweep_source_iterate_noalloc": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
+            "jsweep_batch_create": (I, [I, I, P, P]),
+            "jsweep_batch_problem_bytes": (I, [P, P, I, P]),
+            "jsweep_batch_add": (I, [P, P, P, P, P, P, P, ctypes.c_double, I, P, P]),
+            "jsweep_batch_step": (I, [P, I, P, P]),
+            "jsweep_batch_query": (I, [P, I64, P, P, P]),
+            "jsweep_batch_remove": (I, [P, I64]),
+            "jsweep_batch_clear": (I, [P]),
+            "jsweep_batch_size": (I, [P, P]),
+            "jsweep_batch_source_iterate": (I, [P, P, P, P]),
+            "jsweep_batch_autotune": (I, [P, P, P]),
+            "jsweep_batch_stats": (I, [P, P, P, P]),
+            "jsweep_batch_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -412,6 +428,111 @@ def jsweep_source_iterate(dags: Dags, sigma_t, c_ratio, q, inflow=None, tol=1e-8
         return phi_out, it.value, res.value, False
     _check(rc, "jsweep_source_iterate")
     return phi_out, it.value, res.value, True
+
+
+JSWEEP_PROBLEM_ACTIVE = 0
+JSWEEP_PROBLEM_CONVERGED = 1
+JSWEEP_PROBLEM_MAX_ITERS = 2
+
+
+class Batch:
+    """Many independent source-iteration problems advanced by one data-driven
+    launch per iteration (jsweep_batch_*).
+
+    ``add`` takes a built :class:`Dags` and the problem's device tensors (kept
+    referenced here until the problem is removed) and returns the problem id.
+    ``step`` advances every active problem by up to ``n_sweeps`` iterations;
+    a finished problem has its ``phi_out`` written when ``step`` returns.
+    """
+
+    def __init__(self, dtype, nrhs: int = 1, options: jsweep_options | None = None):
+        self.dtype = dtype
+        self.nrhs = int(nrhs)
+        self._prec = _prec(dtype)
+        h = ctypes.c_void_p()
+        _check(lib().jsweep_batch_create(self._prec, self.nrhs, ctypes.byref(options) if options is not None else None,
+                                         ctypes.byref(h)), "jsweep_batch_create")
+        self._h = h
+        self._keep = {}  # id -> (dags, tensors) referenced while the problem is in the batch
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _live():
+            _lib.jsweep_batch_destroy(self._h)
+            self._h = None
+
+    def problem_bytes(self, dags: Dags, has_inflow: bool = False) -> int:
+        out = ctypes.c_int64()
+        _check(lib().jsweep_batch_problem_bytes(self._h, dags._h, int(bool(has_inflow)), ctypes.byref(out)),
+               "jsweep_batch_problem_bytes")
+        return out.value
+
+    def add(self, dags: Dags, sigma_t, c_ratio, q, inflow=None, phi_out=None, tol=1e-8, max_iters=1000,
+            stream=None) -> int:
+        import torch
+        N, Fb, R, dt = dags.n_cells, dags.mesh.n_bfaces, self.nrhs, self.dtype
+        if phi_out is None:
+            phi_out = torch.empty((R, N), dtype=dt, device=q.device)
+        pid = ctypes.c_int64()
+        _check(lib().jsweep_batch_add(self._h, dags._h, _dptr(sigma_t, dt, N, "sigma_t"),
+                                      _dptr(c_ratio, dt, N, "c_ratio"), _dptr(q, dt, R * N, "q"),
+                                      _dptr(inflow, dt, R * Fb, "inflow"), _dptr(phi_out, dt, R * N, "phi_out"),
+                                      float(tol), int(max_iters), ctypes.byref(pid), _stream(stream)),
+               "jsweep_batch_add")
+        self._keep[pid.value] = (dags, sigma_t, c_ratio, q, inflow, phi_out)
+        return pid.value
+
+    def phi(self, pid: int):
+        return self._keep[pid][5]
+
+    def step(self, n_sweeps: int = 1, stream=None) -> int:
+        n = ctypes.c_int64()
+        _check(lib().jsweep_batch_step(self._h, int(n_sweeps), ctypes.byref(n), _stream(stream)),
+               "jsweep_batch_step")
+        return n.value
+
+    def query(self, pid: int):
+        """(state, iterations, residual) of a problem."""
+        st, it, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().jsweep_batch_query(self._h, int(pid), ctypes.byref(st), ctypes.byref(it), ctypes.byref(res)),
+               "jsweep_batch_query")
+        return st.value, it.value, res.value
+
+    def remove(self, pid: int):
+        _check(lib().jsweep_batch_remove(self._h, int(pid)), "jsweep_batch_remove")
+        self._keep.pop(pid, None)
+
+    def clear(self):
+        _check(lib().jsweep_batch_clear(self._h), "jsweep_batch_clear")
+        self._keep.clear()
+
+    def __len__(self):
+        n = ctypes.c_int64()
+        _check(lib().jsweep_batch_size(self._h, ctypes.byref(n)), "jsweep_batch_size")
+        return n.value
+
+    def source_iterate(self, stream=None, allow_not_converged=False):
+        """Restart every problem from phi = 0 and iterate all to the end.
+        Returns (iterations, residuals) as arrays in increasing id."""
+        n = len(self)
+        it = np.zeros(max(n, 1), dtype=np.int32)
+        res = np.zeros(max(n, 1), dtype=np.float64)
+        rc = lib().jsweep_batch_source_iterate(self._h, _ptr(it), _ptr(res), _stream(stream))
+        if not (rc == JSWEEP_ERR_NOT_CONVERGED and allow_not_converged):
+            _check(rc, "jsweep_batch_source_iterate")
+        return it[:n], res[:n]
+
+    def autotune(self, stream=None) -> float:
+        ms = ctypes.c_double()
+        _check(lib().jsweep_batch_autotune(self._h, _stream(stream), ctypes.byref(ms)), "jsweep_batch_autotune")
+        return ms.value
+
+    def stats(self):
+        """(sweep launch ms, whole iteration ms) of the last batched iteration
+        and the kernels launched by this batch so far."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(lib().jsweep_batch_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+               "jsweep_batch_stats")
+        return a.value, b.value, n.value
 
 
 JSWEEP_NOALLOC_SCRATCH_BYTES = 64 << 20

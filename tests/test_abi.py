@@ -24,7 +24,7 @@ def lib():
 
 def header_symbols():
     text = open(os.path.join(ROOT, "include", "jsweep.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(jsweep_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:JSWEEP_API\s+)?(?:int|const char \*)\s*(jsweep_\w+)\s*\(", text, re.M)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -33,6 +33,13 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(J.EXPORTED) == syms
     for s in syms:
         assert hasattr(lib, s), s
+
+
+def test_exports_nothing_else(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", libbuild.LIB], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert exported == set(header_symbols())
 
 
 def test_version_and_options(lib):
@@ -64,3 +71,28 @@ def test_error_message_is_thread_local_and_cleared(lib):
         J.jsweep_quadrature_product(0, 0)
     J.jsweep_quadrature_product(1, 1)
     assert lib.jsweep_last_error() == b""
+
+
+def test_batch_host_side_errors(lib):
+    # host-only paths of the batch entry points (no device work is queued)
+    P = ctypes.c_void_p
+    h = P()
+    assert lib.jsweep_batch_create(7, 1, None, ctypes.byref(h)) == J.JSWEEP_ERR_INVALID_ARG
+    assert lib.jsweep_batch_create(J.JSWEEP_F32, 9, None, ctypes.byref(h)) == J.JSWEEP_ERR_INVALID_ARG
+    assert lib.jsweep_batch_create(J.JSWEEP_F32, 2, None, ctypes.byref(h)) == J.JSWEEP_OK
+    n = ctypes.c_int64(-1)
+    assert lib.jsweep_batch_size(h, ctypes.byref(n)) == J.JSWEEP_OK and n.value == 0
+    assert lib.jsweep_batch_query(h, 0, None, None, None) == J.JSWEEP_ERR_INVALID_ARG
+    assert b"no problem with id 0" in lib.jsweep_last_error()
+    assert lib.jsweep_batch_remove(h, 3) == J.JSWEEP_ERR_INVALID_ARG
+    assert lib.jsweep_batch_add(h, None, None, None, None, None, None, 1e-6, 10, None, None) == \
+        J.JSWEEP_ERR_INVALID_ARG
+    assert lib.jsweep_batch_step(h, 0, None, None) == J.JSWEEP_ERR_INVALID_ARG
+    # an empty batch has nothing to iterate
+    assert lib.jsweep_batch_step(h, 1, ctypes.byref(n), None) == J.JSWEEP_OK and n.value == 0
+    assert lib.jsweep_batch_source_iterate(h, None, None, None) == J.JSWEEP_OK
+    a, b, nl = ctypes.c_double(-1), ctypes.c_double(-1), ctypes.c_int64(-1)
+    assert lib.jsweep_batch_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(nl)) == J.JSWEEP_OK
+    assert a.value == 0.0 and nl.value == 0
+    assert lib.jsweep_batch_destroy(h) == J.JSWEEP_OK
+    assert lib.jsweep_batch_destroy(None) == J.JSWEEP_OK
