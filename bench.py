@@ -52,6 +52,15 @@ def parse():
     p.add_argument("--cluster", type=int, default=32)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve"],
+                   help="hex128: the single large problem (default line); batch: 256 independent tet problems "
+                        "in one persistent launch per iteration; serve: Poisson request stream through the "
+                        "continuous-batching server")
+    p.add_argument("--problems", type=int, default=256, help="batch: number of problems")
+    p.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    p.add_argument("--rate", type=float, default=8.0, help="serve: Poisson arrival rate (requests/s)")
+    p.add_argument("--meshes", type=int, default=24, help="serve: meshes in the catalog")
+    p.add_argument("--budget-gb", type=float, default=60.0, help="serve: device-memory budget")
     return p.parse_args()
 
 
@@ -348,10 +357,385 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+# ---- batched and served workloads ----------------------------------------------------
+BATCH_WORKLOAD = "batch256_kuhn_tets_edge8-40_loguniform_dirs24-96-288_fp32_si_tol1e-6"
+SERVE_WORKLOAD = "serve_poisson_tets1e3-1e6_dirs48-128-288_fp32_si_tol1e-6_budget60GB"
+
+
+def _pool_map(fn, items, procs=None):
+    """Host-side input generation in worker processes (spawned, before any GPU use)."""
+    import multiprocessing as mp
+    procs = procs or min(16, os.cpu_count() or 1)
+    if procs <= 1 or len(items) < 4:
+        return [fn(x) for x in items]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(fn, items, chunksize=1)
+
+
+def _batch_inputs(n_problems):
+    from inputs import batch_problem_specs, make_batch_problem
+    specs = batch_problem_specs(n_problems, seed=4)
+    return specs, _pool_map(make_batch_problem, specs)
+
+
+def _tet_bytes_per_cell_dir(R, M, p=4, G=64):
+    """Algorithmic bytes per (cell, direction) of one sweep of a tet mesh:
+    psi written once and read once downwind (R p each), order index 4 B,
+    incoming mask 1 B, and per cell (4 faces x 16 B geometry, sources in and
+    phi out, 2 R p) once per sweep, i.e. per direction (G + 2 R p) / M."""
+    return 2 * R * p + 5 + (G + 2 * R * p) / M
+
+
+def run_reference_batch(args):
+    """Oracle arm of the batched / served workloads: FP64 CPU oracle (DAG build
+    + one sweep of every direction) on the first problems of the same inputs,
+    as many as fit about 20 s."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    specs, probs = _batch_inputs(args.problems)
+    nt = oracle.max_threads()
+
+    def one_pass(budget_s=20.0):
+        units, t_tot, k = 0.0, 0.0, 0
+        for p in probs:
+            dirs, w = oracle.product_quadrature(*p["spec"]["quad"])
+            t0 = time.perf_counter()
+            o = oracle.build_dags(p, dirs)
+            o.sweep(p["sigma_t"], p["q"] / (4 * math.pi), w, nthreads=nt)
+            t_tot += time.perf_counter() - t0
+            units += float(p["n_cells"]) * len(dirs)
+            k += 1
+            if t_tot > budget_s / max(1, args.steps):
+                break
+        return units, t_tot, k
+
+    for _ in range(args.warmup):
+        one_pass(2.0)
+    tot_u, tot_s, ks = 0.0, 0.0, []
+    for _ in range(args.steps):
+        u, s_, k = one_pass()
+        tot_u += u
+        tot_s += s_
+        ks.append(k)
+    value = tot_u / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-angle updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD if args.workload == "batch" else SERVE_WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "cell-angle updates/s", "cores": nt, "kind": "oracle",
+                             "sample": f"per step: oracle DAG build + one sweep of all directions of the first "
+                                       f"{min(ks)}-{max(ks)} batch problems, {nt} OpenMP threads"},
+            "e2e": {"value": value, "unit": "cell-angle updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """256 independent tet problems: batched persistent launch vs one at a time."""
+    import numpy as np
+
+    specs, probs = _batch_inputs(args.problems)  # before any GPU use (spawned workers)
+    import torch
+
+    from paper_1803_09876_gb300 import build as libbuild
+    from paper_1803_09876_gb300 import jsweep as J
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    libbuild.build()
+    J.load()
+    J.use_torch_allocator()
+    dev = torch.device("cuda", local)
+    tol, max_iters = 1e-6, 1000
+    t0 = time.perf_counter()
+    handles, tens = [], []
+    for p in probs:
+        dirs, w = J.jsweep_quadrature_product(*p["spec"]["quad"])
+        g = J.jsweep_build_dags(J.mesh_from_dict(p), J.jsweep_quadrature_create(dirs, w))
+        handles.append(g)
+        tens.append(tuple(torch.as_tensor(x, dtype=torch.float32, device=dev).contiguous()
+                          for x in (p["sigma_t"], p["c_ratio"], p["q"])))
+    torch.cuda.synchronize()
+    setup_build_s = time.perf_counter() - t0
+    NM = np.array([g.n_cells * g.n_dirs for g in handles], dtype=np.float64)
+    phis = [torch.empty((1, g.n_cells), dtype=torch.float32, device=dev) for g in handles]
+    b = J.Batch(torch.float32, 1)
+    ids = [b.add(g, *t, phi_out=ph, tol=tol, max_iters=max_iters) for g, t, ph in zip(handles, tens, phis)]
+    tune_ms = b.autotune()
+    o = b.options()
+    chosen = {"sweep_mode": "persistent" if o.sweep_mode == J.JSWEEP_MODE_PERSISTENT else "level_synchronous",
+              "cluster_cells": o.cluster_cells, "angles_per_warp": o.angles_per_warp, "unit_order": o.unit_order,
+              "one_iteration_ms": tune_ms}
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        its, _ = b.source_iterate()
+    torch.cuda.synchronize()
+    _, _, l0 = b.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    units = 0.0
+    for _ in range(args.steps):
+        its, res = b.source_iterate()
+        units += float(np.dot(its, NM))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    _, _, l1 = b.stats()
+    ms = ev0.elapsed_time(ev1)
+    units_all, ms_all = aggregate(units, ms, ws, dev)
+    value = units_all / (ms_all / 1e3)
+    batched_iters = its.copy()
+
+    # dominant kernel: the batched sweep launch with every problem active
+    sweep_ms = []
+    b_full = J.Batch(torch.float32, 1, o)
+    for g, t, ph in zip(handles, tens, phis):
+        b_full.add(g, *t, phi_out=ph, tol=0.0, max_iters=max_iters)
+    for _ in range(4):
+        b_full.step(1)
+        sweep_ms.append(b_full.stats()[0])
+    sw = statistics.median(sweep_ms[1:])
+    alg = float(sum(_tet_bytes_per_cell_dir(1, g.n_dirs) * g.n_cells * g.n_dirs for g in handles))
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = alg / (sw / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None,
+            "kernel": ("k_sweep_dd_batch, one persistent launch" if o.sweep_mode == J.JSWEEP_MODE_PERSISTENT
+                       else "k_sweep_level_batch, one CUDA-graph node per merged slot")
+                      + " over all problems and directions (one full iteration)",
+            "sweep_ms": sw, "alg_bytes": alg,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
+    del b_full
+
+    # one problem at a time through the plain single-problem path
+    def solo_pass():
+        u = 0.0
+        its_solo = []
+        for g, t, ph in zip(handles, tens, phis):
+            _, it, _, _ = J.jsweep_source_iterate(g, *t, tol=tol, max_iters=max_iters, phi_out=ph)
+            its_solo.append(it)
+            u += float(it) * g.n_cells * g.n_dirs
+        return u, its_solo
+
+    solo_pass()  # warm: per-handle unit tables and graphs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    u_solo, its_solo = solo_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solo_ms = e0.elapsed_time(e1)
+    solo_value = u_solo / (solo_ms / 1e3)
+
+    # end to end through the batch API with host buffers
+    h_in = [tuple(torch.as_tensor(x, dtype=torch.float32).contiguous().pin_memory()
+                  for x in (p["sigma_t"], p["c_ratio"], p["q"])) for p in probs]
+    h_out = [torch.empty((1, g.n_cells), dtype=torch.float32).pin_memory() for g in handles]
+    b.source_iterate()  # the solo pass switched the handles' unit tables: rebuild them untimed
+    torch.cuda.synchronize()
+    e0.record(stream)
+    u_e2e = 0.0
+    for _ in range(args.steps):
+        for ht, dt in zip(h_in, tens):
+            for h, d in zip(ht, dt):
+                d.copy_(h, non_blocking=True)
+        its_e, _ = b.source_iterate()
+        for ho, ph in zip(h_out, phis):
+            ho.copy_(ph, non_blocking=True)
+        u_e2e += float(np.dot(its_e, NM))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1)
+    eu, em = aggregate(u_e2e, e_ms, ws, dev)
+    e2e = {"value": eu / (em / 1e3), "unit": "cell-angle updates/s",
+           "h2d_bytes_per_step": int(sum(sum(x.numel() * 4 for x in ht) for ht in h_in)),
+           "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in h_out))}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        nt = oracle.max_threads()
+        u, t_tot, k = 0.0, 0.0, 0
+        for p in probs:
+            dirs, w = oracle.product_quadrature(*p["spec"]["quad"])
+            t1 = time.perf_counter()
+            od = oracle.build_dags(p, dirs)
+            od.sweep(p["sigma_t"], p["q"] / (4 * math.pi), w, nthreads=nt)
+            t_tot += time.perf_counter() - t1
+            u += float(p["n_cells"]) * len(dirs)
+            k += 1
+            if t_tot > 15.0:
+                break
+        cpu = {"value": u / t_tot, "unit": "cell-angle updates/s", "cores": nt, "kind": "oracle",
+               "sample": f"oracle DAG build + one sweep of all directions of the first {k} of {len(probs)} "
+                         f"problems ({t_tot:.1f} s, {nt} OpenMP threads)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-angle updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "problems": len(probs), "cells_total": int(sum(
+                g.n_cells for g in handles)), "cell_dirs_per_iteration": float(NM.sum()),
+                "step": "source iteration of every problem from phi = 0 to tol 1e-6 (FP64 residual)",
+                "l2": "inputs larger than L2 (psi 14 GB), no flush", "parallelism": f"replicas x{ws}",
+                "autotuned": chosen},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(l1 - l0),
+            "clocks": clk,
+            "one_at_a_time": {"value": solo_value, "unit": "cell-angle updates/s", "ms": solo_ms,
+                              "path": "jsweep_source_iterate per problem (level-synchronous CUDA graph)"},
+            "speedup_vs_one_at_a_time": value / solo_value,
+            "iterations_equal_solo": bool(list(batched_iters) == list(its_solo)),
+            "setup_s": {"mesh_and_dag_build": setup_build_s},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _serve_catalog(n_meshes, seed=5000):
+    """Catalog of tet meshes: cell counts log-uniform in [1e3, 1e6], direction
+    sets drawn from {48, 128, 288} (seeded)."""
+    import numpy as np
+
+    from inputs import QUAD_BY_NDIRS, tets_edge_for_cells
+    rng = np.random.default_rng(seed)
+    cells = np.exp(rng.uniform(np.log(1e3), np.log(1e6), n_meshes))
+    nd = rng.choice(np.array([48, 128, 288]), n_meshes)
+    return [dict(key=f"m{i}", n=tets_edge_for_cells(c), ndirs=int(d), quad=QUAD_BY_NDIRS[int(d)],
+                 seed=seed + 1 + i) for i, (c, d) in enumerate(zip(cells, nd))]
+
+
+def _serve_mesh(spec):
+    from inputs import kuhn_tets
+    return kuhn_tets(spec["n"], 0.2, spec["seed"])
+
+
+def _serve_inputs(mesh_cells, seed):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.5, 2.0, mesh_cells), np.full(mesh_cells, 0.5), rng.uniform(0.0, 1.0, (1, mesh_cells))
+
+
+def run_serve(args):
+    """Poisson request stream: continuous batching vs one request at a time."""
+    import numpy as np
+
+    cat = _serve_catalog(args.meshes)
+    meshes = _pool_map(_serve_mesh, cat)  # before any GPU use
+    import torch
+
+    from paper_1803_09876_gb300 import build as libbuild
+    from paper_1803_09876_gb300 import jsweep as J
+    from paper_1803_09876_gb300.serve import GpuBackend, Server, poisson_stream, run_one_at_a_time, summarize
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    libbuild.build()
+    J.load()
+    J.use_torch_allocator()
+    by_key = {}
+    for spec, mesh in zip(cat, meshes):
+        dirs, w = J.jsweep_quadrature_product(*spec["quad"])
+        by_key[spec["key"]] = (mesh, dirs, w)
+    keys = [c["key"] for c in cat]
+
+    def make_inputs(key, seed):
+        return _serve_inputs(by_key[key][0]["n_cells"], seed)
+
+    def stream():
+        return poisson_stream(args.requests, args.rate, keys, make_inputs, seed=5000 + 100 * rank)
+
+    tol, max_iters = 1e-6, 1000
+    budget = args.budget_gb * 1e9
+    be = GpuBackend(lambda k: by_key[k], dtype=torch.float32, tol=tol, max_iters=max_iters)
+    srv = Server(be, budget, sweeps_per_step=1)
+    t0 = time.perf_counter()
+    resident = srv.warm(keys)  # meshes and graphs resident before the stream starts
+    torch.cuda.synchronize()
+    warm_s = time.perf_counter() - t0
+    from paper_1803_09876_gb300.serve import Request
+
+    def warm_requests():
+        # one request per catalog mesh: unit tables, graphs and allocator pools warm for every mesh
+        out = []
+        for i, k in enumerate(keys):
+            sg, c, q = make_inputs(k, 4999 * 1000 + i)
+            out.append(Request(rid=i, arrival=0.0, mesh_key=k, sigma_t=sg, c_ratio=c, q=q))
+        return out
+
+    warm = Server(be, budget, sweeps_per_step=1)
+    warm.meshes = resident
+    for _ in range(max(1, args.warmup)):
+        warm.run(warm_requests())
+
+    work = lambda r: float(r.iters) * by_key[r.mesh_key][0]["n_cells"] * len(by_key[r.mesh_key][1])  # noqa: E731
+    _, _, l0 = be.batch.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    served = srv.run(stream())
+    clk = clocks.stop()
+    _, _, l1 = be.batch.stats()
+    s_served = summarize(served, work)
+
+    solo_be = GpuBackend(lambda k: by_key[k], dtype=torch.float32, tol=tol, max_iters=max_iters)
+    for _ in range(max(1, args.warmup)):
+        run_one_at_a_time(solo_be, warm_requests(), meshes=resident)
+    alone = run_one_at_a_time(solo_be, stream(), meshes=resident)
+    s_alone = summarize(alone, work)
+    same = all(a.iters == b_.iters and np.array_equal(a.phi, b_.phi) for a, b_ in zip(
+        sorted(served, key=lambda r: r.rid), sorted(alone, key=lambda r: r.rid)))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": s_served["cell_angle_updates_per_s"], "unit": "cell-angle updates/s",
+            "n_gpus": ws, "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * s_served["makespan_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "requests": args.requests, "rate_per_s": args.rate,
+                       "catalog_meshes": len(cat), "budget_gb": args.budget_gb,
+                       "catalog_cells": [int(by_key[k][0]["n_cells"]) for k in keys],
+                       "catalog_dirs": [len(by_key[k][1]) for k in keys],
+                       "timing": "wall clock per request: arrival to result in host memory",
+                       "parallelism": f"replicas x{ws}"},
+            "latency_s": {"p50": s_served["p50_s"], "p99": s_served["p99_s"], "mean": s_served["mean_s"],
+                          "max": s_served["max_s"]},
+            "served": s_served,
+            "one_at_a_time": s_alone,
+            "p99_ratio_one_at_a_time_over_served": s_alone["p99_s"] / s_served["p99_s"],
+            "results_equal_one_at_a_time": bool(same),
+            "gpu_launches": int(l1 - l0),
+            "clocks": clk,
+            "peak_budget_used_gb": srv.peak_used / 1e9,
+            "setup_s": {"catalog_build": warm_s},
+            "e2e": {"value": s_served["cell_angle_updates_per_s"], "unit": "cell-angle updates/s",
+                    "h2d_bytes_per_step": int(sum((r.sigma_t.size + r.c_ratio.size + r.q.size) * 4 for r in served)),
+                    "d2h_bytes_per_step": int(sum(r.phi.size * 4 for r in served))},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "hex128":
+            run_reference(args)
+        else:
+            run_reference_batch(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

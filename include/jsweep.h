@@ -81,6 +81,17 @@ extern "C" {
 #define JSWEEP_PRIO_LEVEL 0     /* by level index, all directions together */
 #define JSWEEP_PRIO_DEPTH 1     /* by remaining depth: long directions start first */
 #define JSWEEP_PRIO_OCTANT 2    /* level index staggered by octant */
+/* Patch tasks (Sec. V-B patch-angle programs): the cells are cut into
+ * contiguous id ranges ("patches"; the generated meshes number cells so that
+ * a range is a spatial slab), and each (direction, patch) pair becomes one
+ * task that a single resident warp runs from its first layer to its last, so
+ * upwind values it wrote a moment ago are still in cache.  There are as many
+ * patches as resident warps allow (directions x patches <= resident warps), so
+ * every task is running at once and the sweep cannot deadlock whatever the
+ * patch graph looks like.  Persistent schedule only (others treat it as
+ * LEVEL); JSWEEP_ERR_UNIMPLEMENTED if the directions outnumber the resident
+ * warps. */
+#define JSWEEP_PRIO_PATCH 3
 
 typedef struct jsweep_mesh_s *jsweep_mesh_t;
 typedef struct jsweep_quad_s *jsweep_quad_t;
@@ -126,7 +137,10 @@ JSWEEP_API int jsweep_version(void);
  * or NULL; free releases one.  Both are called on the host thread making the
  * library call; stream is the stream the memory will first be used on.
  * Passing NULL for both restores cudaMalloc/cudaFree.  Memory obtained before
- * the switch is released with the allocator that produced it. */
+ * the switch is released with the allocator that produced it, so a free
+ * function (and its ctx) must stay callable until every buffer it may release
+ * is gone: until the handles and batch problems created while it was
+ * installed are destroyed. */
 typedef void *(*jsweep_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*jsweep_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 JSWEEP_API int jsweep_set_allocator(jsweep_alloc_fn alloc, jsweep_free_fn free_fn, void *ctx);
@@ -287,6 +301,8 @@ JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision
  *     unit_order) times one batched iteration and keeps the fastest; *best_ms
  *     (may be NULL) receives its time.  It restarts every problem from
  *     phi = 0, as jsweep_batch_source_iterate does.
+ *   jsweep_batch_options: the batch's current options (after
+ *     jsweep_batch_autotune: the chosen ones).
  *   jsweep_batch_stats: device time of the last batched sweep launch and of
  *     the whole last iteration, in ms, and the number of kernels the batch
  *     has launched since it was created (pointers may be NULL).
@@ -311,6 +327,7 @@ JSWEEP_API int jsweep_batch_source_iterate(jsweep_batch_t batch, int *iters_out,
 JSWEEP_API int jsweep_batch_autotune(jsweep_batch_t batch, void *stream, double *best_ms);
 JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double *iteration_ms,
                                   int64_t *launches);
+JSWEEP_API int jsweep_batch_options(jsweep_batch_t batch, jsweep_options *out);
 JSWEEP_API int jsweep_batch_destroy(jsweep_batch_t batch);
 
 /* ---- source iteration that allocates no device memory ----------------------

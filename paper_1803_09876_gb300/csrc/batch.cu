@@ -52,7 +52,7 @@ static_assert(sizeof(ProbState) == 32, "ProbState layout");
 // Immutable per-problem arguments of the batched kernels.
 template <class T> struct ProbArgs {
     SweepArgs<T> a;
-    int *flags;  // [M][N]
+    int *flags;  // [N][M] epoch stamps, cell-major like psi
     const T *sig, *cr, *q, *vol, *w;
     T *phi[2];
     const int32_t *lag_m, *lag_up;
@@ -104,14 +104,35 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             }
         }
         if constexpr (SPLIT == 1) {
-            if (c >= 0 && ok) st_release(P[p].flags + (int64_t)u.x * P[p].a.N + c, epoch);
+            if (c >= 0 && ok) st_release(P[p].flags + (int64_t)c * P[p].a.M + u.x, epoch);
         } else {
             // the lanes of a cell publish together (A == 1 when SPLIT > 1)
             __threadfence();
             __syncwarp();
-            if (c >= 0 && ok && sub == 0) st_release(P[p].flags + (int64_t)u.x * P[p].a.N + c, epoch);
+            if (c >= 0 && ok && sub == 0) st_release(P[p].flags + (int64_t)c * P[p].a.M + u.x, epoch);
         }
         if (__any_sync(0xffffffffu, !ok)) return;
+    }
+}
+
+// Level-synchronous batched sweep: one launch per merged schedule slot; the
+// units of a slot are independent, so no waits and no flags.
+template <class T, int R, int SPLIT, int MAXF, int A>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sweep_level_batch(const ProbArgs<T> *__restrict__ P, const ProbState *__restrict__ S, const int4 *units,
+                        const int32_t *uprob, int64_t u0, int64_t nu) {
+    const int lane = threadIdx.x & 31;
+    constexpr int LPU = 32 / A;
+    const int a_ix = lane / LPU, ll = lane % LPU, cell = ll / SPLIT, sub = ll % SPLIT;
+    const int64_t t = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * A + a_ix;
+    if (t >= nu) return;
+    const int4 u = units[u0 + t];
+    const int p = uprob[u0 + t];
+    if (cell < u.z && S[p].active) {
+        const ProbArgs<T> &pp = P[p];
+        const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
+        solve_cell<T, R, SPLIT, MAXF, false>(pp.a, u.x, __ldg(pp.a.order + idx), __ldg(pp.a.mask + idx), sub,
+                                             nullptr, 0, nullptr, 0);
     }
 }
 
@@ -297,13 +318,16 @@ struct Batch {
     bool dirty = true;
     DevBuf units, uprob, pargs, pstate, acc, cpre, lpre, err;
     int64_t n_units = 0, ncells = 0, nlags = 0;
-    int maxf = 4, apw = 1;
+    int maxf = 4, apw = 1, mode = JSWEEP_MODE_LEVEL_SYNC;
+    std::vector<int64_t> mslot;  // merged table: slot t is [mslot[t], mslot[t + 1])
+    std::vector<int64_t> tab_units;  // units of each problem in the table (by position in act)
     // the captured iteration
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double sweep_ms = 0.0, iter_ms = 0.0;
     int64_t launches = 0;  // kernels this batch launched (graph nodes counted per replay)
+    int64_t sweep_nodes = 0;  // sweep launches in one iteration
     ~Batch() {
         cudaDeviceSynchronize();
         if (graph) cudaGraphExecDestroy(graph);
@@ -397,7 +421,8 @@ int handle_units(const Batch *b, Dags *d, int max_cells, cudaStream_t s) {
     const jsweep_options saved = d->opt;
     d->opt.cluster_cells = b->opt.cluster_cells;
     d->opt.unit_order = b->opt.unit_order;
-    d->opt.priority = b->opt.priority;
+    // patch tasks are a single-problem schedule: batches merge slot-ordered tables
+    d->opt.priority = b->opt.priority == JSWEEP_PRIO_PATCH ? JSWEEP_PRIO_LEVEL : b->opt.priority;
     d->opt.octant_stagger = b->opt.octant_stagger;
     const int rc = ensure_units(d, JSWEEP_MODE_PERSISTENT, max_cells, s);
     d->opt = saved;
@@ -451,7 +476,9 @@ template <class T, int R> int build_tables(Batch *b, cudaStream_t s) {
     // base[t][k]: slot-major, problem-minor; each slot padded to a multiple of A
     std::vector<int64_t> base((size_t)nslots * K);
     int64_t pos = 0;
+    b->mslot.assign(nslots + 1, 0);
     for (int64_t t = 0; t < nslots; ++t) {
+        b->mslot[t] = pos;
         for (int k = 0; k < K; ++k) {
             const auto &sp = b->probs[b->act[k]]->d->ut.slot_ptr;
             base[t * K + k] = pos;
@@ -460,6 +487,10 @@ template <class T, int R> int build_tables(Batch *b, cudaStream_t s) {
         pos = (pos + A - 1) / A * A;
     }
     b->n_units = pos;
+    b->mslot[nslots] = pos;
+    b->tab_units.assign(K, 0);
+    for (int k = 0; k < K; ++k) b->tab_units[k] = uoff[k + 1] - uoff[k];
+    b->mode = b->opt.sweep_mode == JSWEEP_MODE_PERSISTENT ? JSWEEP_MODE_PERSISTENT : JSWEEP_MODE_LEVEL_SYNC;
     b->ncells = cpre[K];
     b->nlags = lpre[K];
     b->maxf = FS <= 4 ? 4 : FS <= 6 ? 6 : 7;
@@ -516,6 +547,18 @@ template <class T, int R, int SPLIT, int MAXF> void *dd_kernel_a(int A) {
     return dd_kernel<T, R, SPLIT, MAXF, 1>();
 }
 
+template <class T, int R, int SPLIT, int MAXF, int A> void *level_kernel() {
+    return reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A>);
+}
+
+template <class T, int R, int SPLIT, int MAXF> void *level_kernel_a(int A) {
+    if constexpr (SPLIT == 1) {
+        if (A == 2) return level_kernel<T, R, SPLIT, MAXF, 2>();
+        if (A == 4) return level_kernel<T, R, SPLIT, MAXF, 4>();
+    }
+    return level_kernel<T, R, SPLIT, MAXF, 1>();
+}
+
 // Queue one batched iteration on stream cs (captured into the graph).
 template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     constexpr int SPLIT = split_for<T, R>();
@@ -524,6 +567,25 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     ProbState *S = b->pstate.as<ProbState>();
     k_emission_batch<T, R><<<grid_for(b->ncells, 256, 152 * 16), 256, 0, cs>>>(P, S, b->cpre.as<int64_t>(), K,
                                                                                b->ncells);
+    if (b->mode == JSWEEP_MODE_LEVEL_SYNC) {
+        void *lk = b->maxf == 4 ? level_kernel_a<T, R, SPLIT, 4>(b->apw)
+                 : b->maxf == 6 ? level_kernel_a<T, R, SPLIT, 6>(b->apw)
+                                : level_kernel_a<T, R, SPLIT, 7>(b->apw);
+        const int4 *units = b->units.as<int4>();
+        const int32_t *uprob = b->uprob.as<int32_t>();
+        JS_CUDA(cudaEventRecordWithFlags(b->ev[0], cs, cudaEventRecordExternal));
+        b->sweep_nodes = 0;
+        for (size_t t = 0; t + 1 < b->mslot.size(); ++t) {
+            int64_t u0 = b->mslot[t], nu = b->mslot[t + 1] - b->mslot[t];
+            if (nu <= 0) continue;
+            const int64_t warps = (nu + b->apw - 1) / b->apw;
+            void *args[] = {(void *)&P, (void *)&S, (void *)&units, (void *)&uprob, (void *)&u0, (void *)&nu};
+            JS_CUDA(cudaLaunchKernel(lk, dim3((unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock)),
+                                     dim3(kWarpsPerBlock * 32), args, 0, cs));
+            ++b->sweep_nodes;
+        }
+        JS_CUDA(cudaEventRecordWithFlags(b->ev[1], cs, cudaEventRecordExternal));
+    } else {
     void *kern = b->maxf == 4 ? dd_kernel_a<T, R, SPLIT, 4>(b->apw)
                : b->maxf == 6 ? dd_kernel_a<T, R, SPLIT, 6>(b->apw)
                               : dd_kernel_a<T, R, SPLIT, 7>(b->apw);
@@ -548,6 +610,8 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     JS_CUDA(cudaEventRecordWithFlags(b->ev[0], cs, cudaEventRecordExternal));
     JS_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kWarpsPerBlock * 32), args, 0, cs));
     JS_CUDA(cudaEventRecordWithFlags(b->ev[1], cs, cudaEventRecordExternal));
+    b->sweep_nodes = 1;
+    }
     if (b->nlags > 0)
         k_lag_update_batch<T, R><<<grid_for(b->nlags, 256, 152 * 16), 256, 0, cs>>>(P, S, b->lpre.as<int64_t>(), K,
                                                                                     b->nlags);
@@ -557,7 +621,9 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     return JSWEEP_OK;
 }
 
-template <class T, int R> int launches_per_iteration(const Batch *b) { return b->nlags > 0 ? 5 : 4; }
+template <class T, int R> int64_t launches_per_iteration(const Batch *b) {
+    return b->sweep_nodes + (b->nlags > 0 ? 4 : 3);
+}
 
 // Up to n_sweeps iterations of the active problems, then the host mirrors
 // and the outputs of problems that finished.
@@ -618,7 +684,7 @@ template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, 
         set_error("batched sweep: a dependency wait exceeded %.3g s", b->opt.spin_timeout_s);
         return JSWEEP_ERR_DEVICE_TIMEOUT;
     }
-    int64_t still = 0;
+    int64_t still = 0, idle_units = 0;
     bool changed = false;
     for (int k = 0; k < K; ++k) {
         BatchProb &p = *b->probs[b->act[k]];
@@ -631,11 +697,12 @@ template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, 
                                     s));
         }
         still += p.st.active != 0;
+        if (!p.st.active) idle_units += b->tab_units[k];
     }
-    if (changed) {
-        JS_CUDA(cudaStreamSynchronize(s));
-        b->dirty = true;  // the next step sweeps only the problems still active
-    }
+    if (changed) JS_CUDA(cudaStreamSynchronize(s));
+    // finished problems stay in the table (their units are skipped) until they
+    // hold half of it; then the next step rebuilds it from the active ones
+    if (2 * idle_units > b->n_units) b->dirty = true;
     if (n_active) *n_active = still;
     return JSWEEP_OK;
 }
@@ -796,9 +863,8 @@ JSWEEP_API int jsweep_batch_remove(jsweep_batch_t batch, int64_t id) {
         return JSWEEP_ERR_INVALID_ARG;
     }
     cudaDeviceSynchronize();  // no batched launch may still use its buffers
-    const bool active = b->probs[pos]->st.active != 0;
     b->probs.erase(b->probs.begin() + (ptrdiff_t)pos);
-    if (active) b->dirty = true;
+    b->dirty = true;  // the tables refer to problems by position
     return JSWEEP_OK;
 }
 
@@ -858,14 +924,18 @@ JSWEEP_API int jsweep_batch_autotune(jsweep_batch_t batch, void *stream, double 
     Batch *b = bimpl(batch);
     cudaStream_t s = (cudaStream_t)stream;
     struct Cand {
-        int cells, apw, order;
+        int mode, cells, apw, order;
     };
-    static const Cand cands[] = {{32, 1, 1}, {32, 1, 0}, {16, 1, 1}, {16, 2, 1}, {8, 4, 1}, {16, 2, 0}, {8, 4, 0}};
+    static const Cand cands[] = {
+        {JSWEEP_MODE_LEVEL_SYNC, 32, 1, 1}, {JSWEEP_MODE_LEVEL_SYNC, 32, 1, 0}, {JSWEEP_MODE_LEVEL_SYNC, 16, 2, 1},
+        {JSWEEP_MODE_LEVEL_SYNC, 8, 4, 1},  {JSWEEP_MODE_PERSISTENT, 32, 1, 1}, {JSWEEP_MODE_PERSISTENT, 16, 2, 1},
+        {JSWEEP_MODE_PERSISTENT, 8, 4, 1},  {JSWEEP_MODE_PERSISTENT, 8, 4, 0}};
     const jsweep_options keep = b->opt;
     double best = INFINITY;
     jsweep_options chosen = keep;
     for (const Cand &c : cands) {
         b->opt = keep;
+        b->opt.sweep_mode = c.mode;
         b->opt.cluster_cells = c.cells;
         b->opt.angles_per_warp = c.apw;
         b->opt.unit_order = c.order;
@@ -901,6 +971,16 @@ JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double
     if (sweep_ms) *sweep_ms = bimpl(batch)->sweep_ms;
     if (iteration_ms) *iteration_ms = bimpl(batch)->iter_ms;
     if (launches) *launches = bimpl(batch)->launches;
+    return JSWEEP_OK;
+}
+
+JSWEEP_API int jsweep_batch_options(jsweep_batch_t batch, jsweep_options *out) {
+    js::clear_error();
+    if (!batch || !out) {
+        js::set_error("jsweep_batch_options: NULL");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    *out = bimpl(batch)->opt;
     return JSWEEP_OK;
 }
 

@@ -102,6 +102,7 @@ struct Quad {
 
 struct UnitTable {
     int mode = -1, priority = -1, cluster = -1, stagger = -1, order = -1;
+    int64_t warps = 0;             // patch tasks: the launch's warp count (unit t runs on warp t mod warps)
     DevBuf units;                  // int4 [n_units]: (m, pos0, ncells, wait target)
     int64_t n_units = 0;
     std::vector<int64_t> slot_ptr; // level-sync: units of level l are [slot_ptr[l], slot_ptr[l+1])
@@ -141,7 +142,7 @@ struct Dags {
     DevBuf phi_a, phi_b;  // [R][N] (SI ping-pong)
     DevBuf red;      // residual accumulators / flags
     DevBuf counters; // persistent schedule: error word
-    DevBuf flags;    // int32 [M][N]: sweep epoch at which (direction, cell) was last written
+    DevBuf flags;    // int32 [N][M]: sweep epoch at which (cell, direction) was last written
     int epoch = 0;
     DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
     UnitTable ut;
@@ -162,7 +163,7 @@ void dags_release(Dags *d);
 int build_dags(Dags *d, cudaStream_t s);
 
 // unit schedules and sweeps (sweep.cu)
-int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s);
+int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps = 0);
 int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s);  // FP64 directions as [M][4]
 int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source,
               const void *inflow, void *phi_out, void *psi_out, cudaStream_t s);

@@ -76,13 +76,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             ok = solve_cell<T, R, SPLIT, MAXF, true>(a, u.x, c, __ldg(a.mask + idx), sub, flags, want, err, timeout);
         }
         if constexpr (SPLIT == 1) {
-            if (c >= 0 && ok) st_release(flags + (int64_t)u.x * a.N + c, epoch);
+            if (c >= 0 && ok) st_release(flags + (int64_t)c * a.M + u.x, epoch);
         } else {
             // the lanes of a cell publish together: each makes its own stores
             // visible, then the first lane of the cell releases the flag
             __threadfence();
             __syncwarp();
-            if (c >= 0 && ok && sub == 0) st_release(flags + (int64_t)u.x * a.N + c, epoch);
+            if (c >= 0 && ok && sub == 0) st_release(flags + (int64_t)c * a.M + u.x, epoch);
         }
         if (__any_sync(0xffffffffu, !ok)) return;
     }
@@ -149,6 +149,83 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
             int32_t s = p0 + (int32_t)(j * U);
             units[pos] = make_int4((int)m, s, min(U, p1 - s), wait);
         }
+    }
+}
+
+// ---- patch tasks ------------------------------------------------------------------------
+// Triple i = (direction m, patch s, layer l), task-major: i = tri_off[m] + s * L_m + l.
+__device__ __forceinline__ void patch_triple(int64_t i, const int64_t *tri_off, int64_t M, const int32_t *nlev,
+                                             int64_t &m, int &s, int &l) {
+    int64_t lo = 0, hi = M;  // largest m with tri_off[m] <= i
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tri_off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    m = lo;
+    const int64_t r = i - tri_off[m];
+    const int L = nlev[m];
+    s = (int)(r / L);
+    l = (int)(r - (int64_t)s * L);
+}
+
+__device__ __forceinline__ int lower_bound_id(const int32_t *row, int lo, int hi, int32_t key) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (row[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Cells of layer l of direction m that lie in patch s: [a, b) in the layer-major
+// order (a layer's cells are sorted by id, and a patch is an id range).
+__device__ __forceinline__ void patch_run(const int32_t *order, const int32_t *lp, const int64_t *lp_off, int64_t N,
+                                          int nslab, int64_t m, int s, int l, int &a, int &b) {
+    const int32_t *row = order + m * N;
+    const int pa = lp[lp_off[m] + l], pb = lp[lp_off[m] + l + 1];
+    const int32_t lo_id = (int32_t)((int64_t)s * N / nslab), hi_id = (int32_t)((int64_t)(s + 1) * N / nslab);
+    a = lower_bound_id(row, pa, pb, lo_id);
+    b = lower_bound_id(row, a, pb, hi_id);
+}
+
+__global__ void k_patch_counts(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
+                               const int64_t *tri_off, int64_t M, int64_t N, int nslab, int U, int64_t total,
+                               int64_t *cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m;
+        int s, l, a, b;
+        patch_triple(i, tri_off, M, nlev, m, s, l);
+        patch_run(order, lp, lp_off, N, nslab, m, s, l, a, b);
+        cnt[i] = (b - a + U - 1) / U;
+    }
+}
+
+__global__ void k_patch_task_max(const int64_t *uoff, const int64_t *cnt, const int64_t *tri_off, const int32_t *nlev,
+                                 int64_t M, int nslab, unsigned long long *maxk) {
+    const int64_t tasks = M * nslab;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tasks; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = t / nslab, s = t - m * nslab;
+        const int64_t first = tri_off[m] + s * nlev[m], last = first + nlev[m] - 1;
+        atomicMax(maxk, (unsigned long long)(uoff[last] + cnt[last] - uoff[first]));
+    }
+}
+
+// Unit k of task (m, s) goes to table position task + W * k, so that the
+// data-driven kernel (unit t on warp t mod W) gives each task to one warp,
+// which runs the task's units in layer order.
+__global__ void k_patch_fill(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
+                             const int64_t *tri_off, int64_t M, int64_t N, int nslab, int U, int64_t total,
+                             const int64_t *uoff, int64_t W, int4 *units) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m;
+        int s, l, a, b;
+        patch_triple(i, tri_off, M, nlev, m, s, l);
+        patch_run(order, lp, lp_off, N, nslab, m, s, l, a, b);
+        const int64_t task = m * nslab + s;
+        const int64_t k0 = uoff[i] - uoff[tri_off[m] + (int64_t)s * nlev[m]];
+        for (int j = 0; a + j * U < b; ++j)
+            units[task + W * (k0 + j)] = make_int4((int)m, a + j * U, min(U, b - a - j * U), 0);
     }
 }
 
@@ -271,9 +348,80 @@ int pad_rhs(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8
 }  // namespace
 
 // ---- unit tables ------------------------------------------------------------------------
-int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
+// Patch-task table (JSWEEP_PRIO_PATCH): patches are id ranges; as many as
+// resident warps allow (directions x patches <= resident_warps).
+static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream_t s) {
+    const int64_t M = d->M, N = d->N;
+    if (resident_warps < M) {
+        set_error("patch tasks need at least one resident warp per direction (%lld directions, %lld warps)",
+                  (long long)M, (long long)resident_warps);
+        return JSWEEP_ERR_UNIMPLEMENTED;
+    }
+    const int nslab = (int)std::min<int64_t>(resident_warps / M, N);
+    const int64_t tasks = M * nslab;
+    const int64_t W = (tasks + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
+    UnitTable &ut = d->ut;
+    if (ut.mode == JSWEEP_MODE_PERSISTENT && ut.priority == JSWEEP_PRIO_PATCH && ut.cluster == U && ut.warps == W)
+        return JSWEEP_OK;
+    std::vector<int64_t> tri(M + 1, 0);
+    std::vector<int32_t> nl32(M);
+    for (int64_t m = 0; m < M; ++m) {
+        nl32[m] = (int32_t)d->slayers[m];
+        tri[m + 1] = tri[m] + (int64_t)nslab * d->slayers[m];
+    }
+    const int64_t total = tri[M];
+    DevBuf tri_d, nlev_d, lpoff_d, cnt, uoff, maxk;
+    JS_TRY(tri_d.alloc((M + 1) * 8, s));
+    JS_TRY(nlev_d.alloc(M * 4, s));
+    JS_TRY(lpoff_d.alloc((M + 1) * 8, s));
+    JS_TRY(cnt.alloc(total * 8, s));
+    JS_TRY(uoff.alloc(total * 8, s));
+    JS_TRY(maxk.alloc(8, s));
+    JS_CUDA(cudaMemcpyAsync(tri_d.p, tri.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(nlev_d.p, nl32.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(lpoff_d.p, d->sp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemsetAsync(maxk.p, 0, 8, s));
+    k_patch_counts<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(d->s_order, d->s_lp, lpoff_d.as<int64_t>(),
+                                                                  nlev_d.as<int32_t>(), tri_d.as<int64_t>(), M, N,
+                                                                  nslab, U, total, cnt.as<int64_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(scan_exclusive_i64(cnt.as<int64_t>(), uoff.as<int64_t>(), total, s));
+    k_patch_task_max<<<grid_for(tasks, 256, 4096), 256, 0, s>>>(uoff.as<int64_t>(), cnt.as<int64_t>(),
+                                                                tri_d.as<int64_t>(), nlev_d.as<int32_t>(), M, nslab,
+                                                                reinterpret_cast<unsigned long long *>(maxk.p));
+    JS_LAUNCH_CHECK();
+    unsigned long long kmax = 0;
+    JS_CUDA(cudaMemcpyAsync(&kmax, maxk.p, 8, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_units = W * (int64_t)kmax;
+    JS_TRY(ut.units.alloc((size_t)std::max<int64_t>(n_units, 1) * 16, s));
+    JS_CUDA(cudaMemsetAsync(ut.units.p, 0, (size_t)std::max<int64_t>(n_units, 1) * 16, s));  // empty units pad
+    k_patch_fill<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(d->s_order, d->s_lp, lpoff_d.as<int64_t>(),
+                                                                nlev_d.as<int32_t>(), tri_d.as<int64_t>(), M, N, nslab,
+                                                                U, total, uoff.as<int64_t>(), W, ut.units.as<int4>());
+    JS_LAUNCH_CHECK();
+    JS_CUDA(cudaStreamSynchronize(s));
+    ut.n_units = n_units;
+    ut.warps = W;
+    ut.slot_ptr.assign({0, n_units});
+    ut.mode = JSWEEP_MODE_PERSISTENT;
+    ut.priority = JSWEEP_PRIO_PATCH;
+    ut.cluster = U;
+    ut.stagger = 0;
+    ut.order = d->opt.unit_order;
+    if (d->graph) {
+        cudaGraphExecDestroy(d->graph);
+        d->graph = nullptr;
+        d->graph_key.clear();
+    }
+    return JSWEEP_OK;
+}
+
+int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps) {
     const int U = std::max(1, std::min(d->opt.cluster_cells, max_cells));
-    const int prio = d->opt.priority;
+    int prio = d->opt.priority;
+    if (prio == JSWEEP_PRIO_PATCH && mode != JSWEEP_MODE_PERSISTENT) prio = JSWEEP_PRIO_LEVEL;
+    if (prio == JSWEEP_PRIO_PATCH) return ensure_units_patch(d, U, resident_warps, s);
     int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Smax / 4);
     if (prio != JSWEEP_PRIO_OCTANT) stagger = 0;
     const int order = d->opt.unit_order;
@@ -359,6 +507,7 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s) {
     ut.slot_ptr[Tmax] = n_units;
     JS_CUDA(cudaStreamSynchronize(s));
     ut.n_units = n_units;
+    ut.warps = 0;
     ut.mode = mode;
     ut.priority = prio;
     ut.cluster = U;
@@ -471,6 +620,14 @@ int launch_dd(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
     int64_t grid = (int64_t)device_sm_count() * bps;
     const int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (grid > maxg) grid = std::max<int64_t>(1, maxg);
+    if (d->ut.priority == JSWEEP_PRIO_PATCH) {
+        // one warp per patch task: the table was laid out for exactly this many warps
+        if (d->ut.warps > (int64_t)device_sm_count() * bps * kWarpsPerBlock) {
+            set_error("patch tasks: %lld warps cannot all be resident", (long long)d->ut.warps);
+            return JSWEEP_ERR_INVALID_ARG;
+        }
+        grid = d->ut.warps / kWarpsPerBlock;
+    }
     // flags: one int per (direction, cell), stamped with the sweep epoch
     const size_t fbytes = (size_t)d->M * d->N * 4;
     if (!d->flags.p || d->flags.bytes < fbytes) {
@@ -492,6 +649,25 @@ int launch_dd(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
     JS_LAUNCH_CHECK();
     d->timing.sweep_launches = 1;
     return JSWEEP_OK;
+}
+
+// Warps of the data-driven kernel that can be resident at once (patch tasks).
+template <class T, int R> int64_t dd_resident_warps(const Dags *d) {
+    constexpr int SPLIT = split_of<T, R>();
+    const int FS = d->mesh->FS;
+    const void *kern = FS <= 4 ? reinterpret_cast<const void *>(k_sweep_dd<T, R, SPLIT, 4>)
+                     : FS <= 6 ? reinterpret_cast<const void *>(k_sweep_dd<T, R, SPLIT, 6>)
+                               : reinterpret_cast<const void *>(k_sweep_dd<T, R, SPLIT, 7>);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarpsPerBlock * 32, 0) != cudaSuccess) occ = 1;
+    int bps = d->opt.blocks_per_sm;
+    if (occ < 1) occ = 1;
+    if (bps <= 0 || bps > occ) bps = occ;
+    return (int64_t)device_sm_count() * bps * kWarpsPerBlock;
+}
+
+template <class T, int R> int64_t patch_warps(const Dags *d, int mode) {
+    return (mode == JSWEEP_MODE_PERSISTENT && d->opt.priority == JSWEEP_PRIO_PATCH) ? dd_resident_warps<T, R>(d) : 0;
 }
 
 template <class T, int R, int SPLIT, int MAXF>
@@ -596,7 +772,7 @@ template <class T, int R>
 static int run_sweep_t(Dags *d, int nrhs, const void *sigma_t, const void *ang_source, const void *inflow,
                        void *phi_out, void *psi_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, patch_warps<T, R>(d, mode)));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
                                   : reinterpret_cast<const T *>(d->mesh->vol32.p);
@@ -633,7 +809,7 @@ template <class T, int R>
 static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, const void *q, const void *inflow,
                     double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, patch_warps<T, R>(d, mode)));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
     JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)

@@ -164,15 +164,17 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
     }
     if constexpr (WAIT) {
         // wait until every active interior upwind cell of this direction is done
-        const int *fm = flags + (int64_t)m * a.N;
+        // (flags are cell-major, [N][M], like psi: the flags of one cell for
+        // the directions of an octant share a sector)
 #pragma unroll
         for (int k = 0; k < MAXF; ++k) {
             const int nb = nbr_bits<T>(gk[k]);
             if (((msk >> k) & 1u) && !((lagk >> k) & 1u) && nb >= 0) {
-                if (ld_acquire(fm + nb) != want) {
+                const int *fp = flags + (int64_t)nb * a.M + m;
+                if (ld_acquire(fp) != want) {
                     const long long t0 = clock64();
                     int ns = 32;
-                    while (ld_acquire(fm + nb) != want) {
+                    while (ld_acquire(fp) != want) {
                         if (ld_volatile(err) != 0) return false;
                         if (clock64() - t0 > timeout) {
                             atomicCAS(err, 0, 1);

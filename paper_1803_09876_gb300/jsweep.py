@@ -57,7 +57,8 @@ EXPORTED = [
     "jsweep_source_iterate_noalloc",
     "jsweep_batch_create", "jsweep_batch_problem_bytes", "jsweep_batch_add", "jsweep_batch_step",
     "jsweep_batch_query", "jsweep_batch_remove", "jsweep_batch_clear", "jsweep_batch_size",
-    "jsweep_batch_source_iterate", "jsweep_batch_autotune", "jsweep_batch_stats", "jsweep_batch_destroy",
+    "jsweep_batch_source_iterate", "jsweep_batch_autotune", "jsweep_batch_stats", "jsweep_batch_options",
+    "jsweep_batch_destroy",
 ]
 
 
@@ -105,6 +106,10 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_voi
 _lock = threading.Lock()
 _lib = None
 _callbacks = None
+# Every allocator ever installed stays referenced: a device buffer is released
+# through the free function of the allocator that produced it, which must
+# therefore outlive the buffer (see jsweep_set_allocator).
+_installed = []
 _exiting = False
 
 
@@ -169,6 +174,7 @@ def load(path: str = LIB_PATH):
             "jsweep_batch_source_iterate": (I, [P, P, P, P]),
             "jsweep_batch_autotune": (I, [P, P, P]),
             "jsweep_batch_stats": (I, [P, P, P, P]),
+            "jsweep_batch_options": (I, [P, P]),
             "jsweep_batch_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
@@ -209,9 +215,16 @@ def use_torch_allocator():
             pass
 
     cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
-    _check(lib().jsweep_set_allocator(ctypes.cast(cbs[0], ctypes.c_void_p),
-                                      ctypes.cast(cbs[1], ctypes.c_void_p), None), "set_allocator")
+    set_allocator(*cbs)
     _callbacks = cbs
+
+
+def set_allocator(alloc_cb, free_cb):
+    """Install ctypes allocator callbacks (_ALLOC_FN, _FREE_FN); they are kept
+    alive for the rest of the process."""
+    _installed.append((alloc_cb, free_cb))
+    _check(lib().jsweep_set_allocator(ctypes.cast(alloc_cb, ctypes.c_void_p),
+                                      ctypes.cast(free_cb, ctypes.c_void_p), None), "set_allocator")
 
 
 def jsweep_options_default(**overrides) -> jsweep_options:
@@ -525,6 +538,11 @@ class Batch:
         ms = ctypes.c_double()
         _check(lib().jsweep_batch_autotune(self._h, _stream(stream), ctypes.byref(ms)), "jsweep_batch_autotune")
         return ms.value
+
+    def options(self) -> jsweep_options:
+        o = jsweep_options()
+        _check(lib().jsweep_batch_options(self._h, ctypes.byref(o)), "jsweep_batch_options")
+        return o
 
     def stats(self):
         """(sweep launch ms, whole iteration ms) of the last batched iteration

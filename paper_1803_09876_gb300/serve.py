@@ -49,6 +49,7 @@ class Request:
     iters: int | None = None
     resid: float | None = None
     phi: np.ndarray | None = None
+    cancelled: bool = False
 
     @property
     def latency(self):
@@ -163,8 +164,31 @@ class Server:
         req.done = self.clock() - self._t0
         self.events.append((req.done, "done", req.rid))
 
-    def run(self, requests):
-        """Serve `requests` (sorted by arrival) in real time; returns them filled."""
+    def _cancel(self, rid, waiting, now):
+        """Drop request `rid`: out of the queue if it waits, out of the batch
+        (memory freed at once) if it iterates; a finished request is kept."""
+        for r in list(waiting):
+            if r.rid == rid:
+                waiting.remove(r)
+                r.cancelled = True
+                self.events.append((now, "cancel", rid))
+                return
+        for pid, (req, need) in list(self.active.items()):
+            if req.rid == rid:
+                self.be.remove(pid)
+                del self.active[pid]
+                self.reserved -= need
+                self.meshes.in_use[req.mesh_key] -= 1
+                req.cancelled = True
+                self.events.append((now, "cancel", rid))
+                return
+
+    def run(self, requests, cancels=()):
+        """Serve `requests` (sorted by arrival) in real time; returns them
+        filled.  `cancels` lists (time, request id): the client gives up on
+        that request at that time."""
+        cancels = sorted(cancels)
+        nc = 0
         reqs = sorted(requests, key=lambda r: r.arrival)
         for r in reqs:
             need = self.be.mesh_bytes_estimate(r.mesh_key) + self.be.request_bytes_estimate(r.mesh_key)
@@ -178,6 +202,9 @@ class Server:
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
                 waiting.append(reqs[nxt])
                 nxt += 1
+            while nc < len(cancels) and cancels[nc][0] <= now:
+                self._cancel(cancels[nc][1], waiting, now)
+                nc += 1
             # admission in arrival order while memory allows
             while waiting:
                 if not self._try_admit(waiting[0], now):
@@ -224,11 +251,14 @@ def run_one_at_a_time(backend, requests, clock=time.perf_counter, sleep=time.sle
 
 
 def summarize(reqs, cell_dir_updates: Callable[[Request], float]):
-    lat = [r.latency for r in reqs]
-    t_end = max(r.done for r in reqs)
+    """Latency percentiles and throughput over the requests that finished."""
+    done = [r for r in reqs if r.done is not None]
+    lat = [r.latency for r in done]
+    t_end = max(r.done for r in done)
     t_start = min(r.arrival for r in reqs)
-    work = sum(cell_dir_updates(r) for r in reqs)
-    return {"requests": len(reqs), "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+    work = sum(cell_dir_updates(r) for r in done)
+    return {"requests": len(done), "cancelled": sum(r.cancelled for r in reqs),
+            "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
             "mean_s": float(np.mean(lat)), "max_s": max(lat), "makespan_s": t_end - t_start,
             "requests_per_s": len(reqs) / (t_end - t_start),
             "cell_angle_updates_per_s": work / (t_end - t_start)}

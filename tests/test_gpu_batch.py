@@ -71,13 +71,14 @@ def _solo(js, d, tol, max_iters=500, allow=False):
     return phi.cpu().numpy().copy(), it, res
 
 
+@pytest.mark.parametrize("mode", [1, 2], ids=["level_sync", "persistent"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_batch_equals_solo_bitwise(prec):
+def test_batch_equals_solo_bitwise(prec, mode):
     torch = _torch()
     dtype = torch.float64 if prec == "f64" else torch.float32
     tol = 1e-8 if prec == "f64" else 1e-6
     js, data = _setup(dtype)
-    b = js.Batch(dtype, 1, js.jsweep_options_default(angles_per_warp=1))
+    b = js.Batch(dtype, 1, js.jsweep_options_default(angles_per_warp=1, sweep_mode=mode))
     ids = [b.add(d["g"], d["sig"], d["c"], d["q"], inflow=d["inflow"], tol=tol, max_iters=500) for d in data]
     its, res = b.source_iterate()
     for k, (pid, d) in enumerate(zip(ids, data)):
@@ -89,12 +90,13 @@ def test_batch_equals_solo_bitwise(prec):
         assert b.query(pid) == (js.JSWEEP_PROBLEM_CONVERGED, it_ref, res_ref)
 
 
-@pytest.mark.parametrize("apw,cells,order", [(2, 16, 1), (4, 8, 0), (4, 8, 1), (1, 5, 1)])
-def test_batch_angles_per_warp_fp32_against_oracle(apw, cells, order):
+@pytest.mark.parametrize("mode,apw,cells,order", [(2, 2, 16, 1), (2, 4, 8, 0), (1, 4, 8, 1), (1, 2, 16, 0),
+                                                  (2, 1, 5, 1)])
+def test_batch_angles_per_warp_fp32_against_oracle(mode, apw, cells, order):
     torch = _torch()
     js, data = _setup(torch.float32, nrhs=2)
     b = js.Batch(torch.float32, 2, js.jsweep_options_default(angles_per_warp=apw, cluster_cells=cells,
-                                                              unit_order=order))
+                                                              unit_order=order, sweep_mode=mode))
     ids = [b.add(d["g"], d["sig"], d["c"], d["q"], inflow=d["inflow"], tol=1e-6) for d in data]
     b.source_iterate()
     for pid, d in zip(ids, data):
@@ -123,13 +125,14 @@ def test_batch_fp64_eight_rhs_against_oracle():
         assert rel_err(b.phi(pid).cpu().numpy(), ref) < TOL_F64
 
 
-def test_continuous_batching_add_remove_between_steps():
+@pytest.mark.parametrize("mode", [1, 2], ids=["level_sync", "persistent"])
+def test_continuous_batching_add_remove_between_steps(mode):
     # problems join while others iterate and leave when done; every result
     # equals the problem solved alone
     torch = _torch()
     js, data = _setup(torch.float32)
     refs = [_solo(js, d, 1e-6) for d in data]
-    b = js.Batch(torch.float32, 1)
+    b = js.Batch(torch.float32, 1, js.jsweep_options_default(sweep_mode=mode))
     live = {}
     pending = list(range(len(data)))
     done = {}
@@ -225,25 +228,41 @@ def test_handle_outlives_destroy_while_in_batch():
 
 
 def test_problem_bytes_match_allocation():
+    # count the bytes the library requests through its allocator while adding
+    # a problem (torch's own statistics also count cached-block slack)
+    import ctypes
     torch = _torch()
     js, data = _setup(torch.float32, nrhs=8)
     d = data[1]
     b = js.Batch(torch.float32, 8)
     want = b.problem_bytes(d["g"], has_inflow=True)
     phi_out = torch.empty((8, d["N"]), dtype=torch.float32, device="cuda")
-    torch.cuda.synchronize()
-    before = torch.cuda.memory_allocated()
-    b.add(d["g"], d["sig"], d["c"], d["q"], inflow=d["inflow"], phi_out=phi_out, tol=1e-6)
-    torch.cuda.synchronize()
-    got = torch.cuda.memory_allocated() - before
-    assert want <= got <= want + 7 * 512  # seven workspaces, each rounded up to 512 bytes by torch
+    requested = []
+
+    def _alloc(nbytes, stream, ctx):
+        requested.append(int(nbytes))
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      torch.cuda.current_stream()))
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    js.set_allocator(js._ALLOC_FN(_alloc), js._FREE_FN(_free))  # kept alive by the binding
+    try:
+        pid = b.add(d["g"], d["sig"], d["c"], d["q"], inflow=d["inflow"], phi_out=phi_out, tol=1e-6)
+        b.remove(pid)
+    finally:
+        js.use_torch_allocator()
+    assert len(requested) == 7  # psi, flags, source records, lagged values, two phi buffers, inflow
+    assert want <= sum(requested) <= want + 7 * 255  # each request rounded up to 256 bytes
 
 
 def test_batch_timeout_reports_error_and_recovers():
     torch = _torch()
     js, data = _setup(torch.float32)
     d = data[1]  # hex grid, several layers per direction: the waits run out
-    b = js.Batch(torch.float32, 1, js.jsweep_options_default(debug_block_waits=1, spin_timeout_s=0.05))
+    b = js.Batch(torch.float32, 1, js.jsweep_options_default(debug_block_waits=1, spin_timeout_s=0.05,
+                                                              sweep_mode=2))
     b.add(d["g"], d["sig"], d["c"], d["q"], inflow=d["inflow"], tol=1e-6)
     with pytest.raises(js.JsweepError) as e:
         b.step(1)

@@ -12,7 +12,8 @@ from _gpu import J, TOL_F32, TOL_F64, build, rel_err, set_opts, tensor
 pytestmark = pytest.mark.gpu
 
 MODES = [dict(sweep_mode=1), dict(sweep_mode=2), dict(sweep_mode=2, priority=1, cluster_cells=7),
-         dict(sweep_mode=2, priority=2, cluster_cells=1), dict(sweep_mode=1, cluster_cells=5)]
+         dict(sweep_mode=2, priority=2, cluster_cells=1), dict(sweep_mode=1, cluster_cells=5),
+         dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=3, cluster_cells=3)]
 
 
 def _torch():
@@ -45,7 +46,7 @@ def test_fp64_two_sweeps_with_lag(opts, R):
         assert rel_err(psi_gpu.cpu().numpy().reshape(R, -1), psi_ref.reshape(R, -1)) < TOL_F64
 
 
-@pytest.mark.parametrize("opts", MODES[:3], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
+@pytest.mark.parametrize("opts", MODES[:3] + MODES[5:], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
 def test_fp32_sweep_tets_and_hex(opts):
     torch = _torch()
     for mesh, quad in ((kuhn_tets(8, 0.2, 2), (4, 4)), (hex_grid(10, 0.15, 5), (6, 6))):

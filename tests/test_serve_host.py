@@ -217,3 +217,23 @@ def test_percentile_and_poisson_stream_are_deterministic():
     # mean gap close to 1 / rate
     gaps = np.diff([r.arrival for r in poisson_stream(4000, 10.0, ["a"], mk, seed=1)])
     assert abs(gaps.mean() - 0.1) < 0.01
+
+
+def test_cancelled_requests_free_their_memory_and_others_finish():
+    clk = Clock()
+    be = FakeBackend(clk, budget=10_000)
+    reqs = [_req(0, 0.0, 2, 40), _req(1, 0.0, 1, 10), _req(2, 0.001, 3, 10), _req(3, 0.05, 1, 5)]
+    srv = Server(be, 10_000, clock=clk, sleep=clk.sleep)
+    # request 0 is cancelled while it iterates, request 3 just after it is admitted
+    out = srv.run(reqs, cancels=[(0.005, 0), (0.0505, 3)])
+    by = {r.rid: r for r in out}
+    assert by[0].cancelled and by[0].phi is None and by[0].done is None
+    assert not by[1].cancelled and by[1].iters == 10
+    assert not by[2].cancelled and by[2].iters == 10
+    assert len(be.probs) == 0 and srv.reserved == 0
+    assert be.allocated == sum(be.resident.values())
+    kinds = [(k, rid) for _, k, rid in srv.events]
+    assert ("cancel", 0) in kinds and ("done", 0) not in kinds
+    assert by[3].cancelled and ("cancel", 3) in kinds
+    s = summarize(out, lambda r: 1.0)
+    assert s["requests"] == 2 and s["cancelled"] == 2
