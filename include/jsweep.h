@@ -64,6 +64,15 @@ extern "C" {
 #define JSWEEP_MODE_AUTO 0       /* library picks */
 #define JSWEEP_MODE_LEVEL_SYNC 1 /* one launch per level index, replayed from a CUDA graph */
 #define JSWEEP_MODE_PERSISTENT 2 /* one grid-resident launch driven by dependency counters */
+/* Patch programs (Sec. V-A, V-B): the cells are grouped into compact patches
+ * of about patch_cells cells; one block runs a (patch, octant) program: it
+ * stages the patch's geometry and sources in shared memory once and sweeps
+ * every direction of the octant across the patch, layer by layer, waiting for
+ * the values that enter the patch from upwind patches.  Programs are taken
+ * from a device-wide queue; a direction whose inflow is not ready yet keeps
+ * its progress and the program is queued again (the data-driven execution of
+ * Listing 1 at patch granularity), so the schedule cannot deadlock. */
+#define JSWEEP_MODE_PATCH 3
 
 /* ---- schedule layers (jsweep_options.layering) ------------------------------
  * Both sweep schedules process the cells of a direction layer by layer; any
@@ -120,7 +129,8 @@ typedef struct {
                               1 = interleaved across the directions of an octant (default), so that
                               units covering the same cells for different directions run side by side
                               and share the cells' geometry and sources in cache */
-    int reserved[4];
+    int patch_cells;       /* JSWEEP_MODE_PATCH: target cells per patch (default 512, 32..4096) */
+    int reserved[3];
 } jsweep_options;
 
 /* Fill *opt with defaults. */
@@ -373,6 +383,8 @@ typedef struct {
     double build_phase_ms[6];   /* last build, device time per phase: [0] octant diagonals, [1] set-up and
                                    face classification, [2] frontier steps with cycle resolution,
                                    [3] level-major order, [4] lag lists, [5] schedule layers */
+    int64_t sweep_programs; /* JSWEEP_MODE_PATCH: (patch, octant) programs of the last sweep */
+    int64_t sweep_requeues; /* JSWEEP_MODE_PATCH: programs the last sweep queued again after a yield */
 } jsweep_timing;
 JSWEEP_API int jsweep_dags_timing(jsweep_dags_t dags, jsweep_timing *t);
 

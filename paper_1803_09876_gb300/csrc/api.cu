@@ -175,6 +175,7 @@ int jsweep_options_default(jsweep_options *opt) {
     opt->cycle_search_max = 256;
     opt->unit_order = 1;
     opt->angles_per_warp = 1;
+    opt->patch_cells = 512;
     return JSWEEP_OK;
 }
 
@@ -458,7 +459,7 @@ int check_options(const jsweep_options *opt, jsweep_options *o) {
                   (int)sizeof(jsweep_options));
         return JSWEEP_ERR_INVALID_ARG;
     }
-    if (opt->sweep_mode < 0 || opt->sweep_mode > JSWEEP_MODE_PERSISTENT || opt->priority < 0 ||
+    if (opt->sweep_mode < 0 || opt->sweep_mode > JSWEEP_MODE_PATCH || opt->priority < 0 ||
         opt->priority > JSWEEP_PRIO_PATCH || opt->cluster_cells > 32 ||
         opt->cycle_search_max > 1024 || opt->blocks_per_sm > 32) {
         set_error("jsweep_options: value out of range");
@@ -482,6 +483,11 @@ int check_options(const jsweep_options *opt, jsweep_options *o) {
         return JSWEEP_ERR_INVALID_ARG;
     }
     o->unit_order = opt->unit_order;
+    if (opt->patch_cells != 0 && (opt->patch_cells < 32 || opt->patch_cells > 4096)) {
+        set_error("jsweep_options.patch_cells=%d out of range (32..4096)", opt->patch_cells);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    if (opt->patch_cells > 0) o->patch_cells = opt->patch_cells;
     if (opt->angles_per_warp != 0 && opt->angles_per_warp != 1 && opt->angles_per_warp != 2 &&
         opt->angles_per_warp != 4) {
         set_error("jsweep_options.angles_per_warp=%d (1, 2 or 4)", opt->angles_per_warp);

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/jsweep.h"
@@ -75,6 +76,22 @@ struct DevBuf {
 // ---- handles ------------------------------------------------------------------
 constexpr int kMaxFaces = 7;  // faces per cell; bit 7 of the incoming mask flags a lagged face
 
+// Compact patches of a mesh (JSWEEP_MODE_PATCH), built once per target size.
+struct PatchPart {
+    int target = 0;
+    int64_t NP = 0;
+    int maxP = 0;                 // cells in the largest patch
+    std::vector<int32_t> ptr;     // host copy of d_ptr
+    DevBuf d_ptr;                 // int32 [NP+1]: patch p holds cells d_ids[ptr[p] .. ptr[p+1])
+    DevBuf d_ids;                 // int32 [N]: cells by patch, ascending id inside a patch
+    DevBuf d_pof;                 // int32 [N]: patch of a cell
+    DevBuf d_loc;                 // int32 [N]: position of a cell inside its patch
+    std::vector<int32_t> nbp;     // host [NP][kPatchNbrs]: neighbouring patches (-1 pads)
+    std::vector<int32_t> okey;    // host [8][NP]: lowest octant-diagonal level of each patch (-1: none)
+    DevBuf d_nbp;
+};
+constexpr int kPatchNbrs = 64;    // neighbours tracked per patch (dependency counters)
+
 struct Mesh {
     std::atomic<int> refs{1};
     int64_t N = 0, F = 0, Fb = 0;
@@ -88,6 +105,7 @@ struct Mesh {
     DevBuf geo64;    // double4 [N][GS]: outward vector area, w = nbr as double bits
     DevBuf vol64;    // double [N]
     DevBuf vol32;    // float [N]
+    std::unique_ptr<PatchPart> part;  // lazily built (patch programs)
 };
 
 struct Quad {
@@ -106,6 +124,28 @@ struct UnitTable {
     DevBuf units;                  // int4 [n_units]: (m, pos0, ncells, wait target)
     int64_t n_units = 0;
     std::vector<int64_t> slot_ptr; // level-sync: units of level l are [slot_ptr[l], slot_ptr[l+1])
+};
+
+// Patch-program schedule of a handle (JSWEEP_MODE_PATCH).
+struct PatchSched {
+    int target = 0;
+    int64_t NP = 0, n_tasks = 0, cap = 0;
+    int n_oct_max = 0;            // most directions in one octant
+    DevBuf entries;               // uint16 [M][N]: per direction, cells by (patch, level, id):
+                                  //   position inside the patch | bit 15 = first cell of a new level
+    DevBuf pmask;                 // uint8 [M][N]: incoming-face mask of each entry
+    DevBuf seg;                   // int32 [M][NP+1]: entries of (direction, patch)
+    DevBuf oct_dirs;              // int32 [8][n_oct_max]: directions of each octant
+    DevBuf oct_n;                 // int32 [8]
+    DevBuf q_init;                // int32 [n_tasks]: tasks (octant * NP + patch) in dispatch order
+    DevBuf queue;                 // int32 [cap]
+    DevBuf seq;                   // uint32 [cap]: slot i holds a task once seq = i + 1
+    DevBuf ctr;                   // uint32 [4]: dispatched, queued, finished, re-queued
+    DevBuf prog;                  // int32 [8 * NP][n_oct_max]: entries done per (task, direction)
+    DevBuf cnt_init, cnt;         // int32 [8 * NP]: upstream programs still to finish
+    DevBuf down_ptr, down;        // CSR [8 * NP + 1] / [edges]: downstream programs
+    int64_t n_ready0 = 0;         // programs queued at the start (no upstream program)
+    int64_t last_requeued = 0;
 };
 
 struct Dags {
@@ -146,6 +186,7 @@ struct Dags {
     int epoch = 0;
     DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
     UnitTable ut;
+    std::unique_ptr<PatchSched> ps;  // lazily built (patch programs)
     // CUDA graph of the level-synchronous sweep
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
@@ -161,6 +202,9 @@ void dags_release(Dags *d);
 
 // dag build (dag_build.cu)
 int build_dags(Dags *d, cudaStream_t s);
+// Graphs of the eight octant diagonals (1/sqrt3)(+-1, +-1, +-1) of d's mesh
+// (levels only; direction o has the sign bits of octant o); nullptr on failure.
+Dags *build_diagonals(Dags *d, cudaStream_t s);
 
 // unit schedules and sweeps (sweep.cu)
 int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps = 0);

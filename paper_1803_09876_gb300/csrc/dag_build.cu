@@ -792,7 +792,7 @@ static std::vector<int32_t> octant_of(const Dags *d) {
 // Dependency graphs of the 8 octant diagonals (+-1, +-1, +-1)/sqrt(3) over the
 // same mesh (a nested build with longest-path levels).  Returns nullptr (and no
 // error) if that build fails: the diagonals only serve the schedule.
-static Dags *build_diagonals(Dags *d, cudaStream_t s) {
+Dags *build_diagonals(Dags *d, cudaStream_t s) {
     Quad *dq = new Quad();
     dq->M = 8;
     std::vector<double> dd(24), dw(8, 1.0);

@@ -418,6 +418,7 @@ static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream
 }
 
 int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps) {
+    if (mode == JSWEEP_MODE_PATCH) return JSWEEP_OK;  // patch programs have their own schedule
     const int U = std::max(1, std::min(d->opt.cluster_cells, max_cells));
     int prio = d->opt.priority;
     if (prio == JSWEEP_PRIO_PATCH && mode != JSWEEP_MODE_PERSISTENT) prio = JSWEEP_PRIO_LEVEL;
@@ -722,18 +723,28 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         d->timing.sweep_launches = nodes;
         return JSWEEP_OK;
     }
+    if (mode == JSWEEP_MODE_PATCH) return launch_patch<T, R>(d, a, s);
     if (a.FS <= 4) return launch_dd<T, R, SPLIT, 4>(d, a, s);
     if (a.FS <= 6) return launch_dd<T, R, SPLIT, 6>(d, a, s);
     return launch_dd<T, R, SPLIT, 7>(d, a, s);
 }
 
 int check_sweep_error(Dags *d, cudaStream_t s, int mode) {
-    if (mode != JSWEEP_MODE_PERSISTENT) return JSWEEP_OK;
+    if (mode != JSWEEP_MODE_PERSISTENT && mode != JSWEEP_MODE_PATCH) return JSWEEP_OK;
+    if (mode == JSWEEP_MODE_PATCH) JS_TRY(patch_counts(d, s));
     int err = 0;
     JS_CUDA(cudaMemcpyAsync(&err, d->counters.p, 4, cudaMemcpyDeviceToHost, s));
     JS_CUDA(cudaStreamSynchronize(s));
-    if (err) {
+    if (err == 1) {
         set_error("persistent sweep: a dependency wait exceeded %.3g s", d->opt.spin_timeout_s);
+        return JSWEEP_ERR_DEVICE_TIMEOUT;
+    }
+    if (err == 2) {
+        set_error("patch programs: no progress for %.3g s", d->opt.spin_timeout_s);
+        return JSWEEP_ERR_DEVICE_TIMEOUT;
+    }
+    if (err) {
+        set_error("patch programs: the queue dispatched far more programs than the schedule needs");
         return JSWEEP_ERR_DEVICE_TIMEOUT;
     }
     return JSWEEP_OK;

@@ -277,4 +277,10 @@ __device__ __forceinline__ void phi_warp(const T *blk, const T *w, int M, int la
 }
 
 }  // namespace dev
+
+// Patch programs (patch.cu): one launch of the patch-program sweep.
+template <class T, int R> int launch_patch(Dags *d, const dev::SweepArgs<T> &a, cudaStream_t s);
+// Programs and re-queued programs of the last patch-program sweep (waits for the stream).
+int patch_counts(Dags *d, cudaStream_t s);
+
 }  // namespace js

@@ -38,6 +38,7 @@ JSWEEP_F32 = 1
 JSWEEP_MODE_AUTO = 0
 JSWEEP_MODE_LEVEL_SYNC = 1
 JSWEEP_MODE_PERSISTENT = 2
+JSWEEP_MODE_PATCH = 3
 
 JSWEEP_LAYERS_OCTANT = 0
 JSWEEP_LAYERS_LEVEL = 1
@@ -45,6 +46,7 @@ JSWEEP_LAYERS_LEVEL = 1
 JSWEEP_PRIO_LEVEL = 0
 JSWEEP_PRIO_DEPTH = 1
 JSWEEP_PRIO_OCTANT = 2
+JSWEEP_PRIO_PATCH = 3
 
 # every symbol include/jsweep.h declares
 EXPORTED = [
@@ -82,7 +84,8 @@ class jsweep_options(ctypes.Structure):
         ("layering", ctypes.c_int),
         ("angles_per_warp", ctypes.c_int),
         ("unit_order", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("patch_cells", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -97,6 +100,8 @@ class jsweep_timing(ctypes.Structure):
         ("build_steps", ctypes.c_int64),
         ("build_stall_rounds", ctypes.c_int64),
         ("build_phase_ms", ctypes.c_double * 6),
+        ("sweep_programs", ctypes.c_int64),
+        ("sweep_requeues", ctypes.c_int64),
     ]
 
 
@@ -348,7 +353,8 @@ class Dags:
         return {"build_ms": t.build_ms, "sweep_ms": t.sweep_ms, "phi_ms": t.phi_ms,
                 "sweep_launches": t.sweep_launches, "build_launches": t.build_launches,
                 "call_launches": t.call_launches, "build_steps": t.build_steps,
-                "build_stall_rounds": t.build_stall_rounds, "build_phase_ms": list(t.build_phase_ms)}
+                "build_stall_rounds": t.build_stall_rounds, "build_phase_ms": list(t.build_phase_ms),
+                "sweep_programs": t.sweep_programs, "sweep_requeues": t.sweep_requeues}
 
 
 def jsweep_mesh_create(n_cells, n_faces, face_cells, normals, areas, volumes) -> Mesh:

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 MODES = [dict(sweep_mode=1), dict(sweep_mode=2), dict(sweep_mode=2, priority=1, cluster_cells=7),
          dict(sweep_mode=2, priority=2, cluster_cells=1), dict(sweep_mode=1, cluster_cells=5),
-         dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=3, cluster_cells=3)]
+         dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=3, cluster_cells=3),
+         dict(sweep_mode=3), dict(sweep_mode=3, patch_cells=64)]
 
 
 def _torch():
@@ -235,12 +236,13 @@ def test_workload3_full_size_sampled_psi_and_phi_reduction():
     assert rel_err(phi.double().cpu().numpy(), acc.cpu().numpy()) < 1e-6
 
 
-def test_bounded_wait_times_out_and_context_survives():
+@pytest.mark.parametrize("mode", [2, 3], ids=["persistent", "patch_programs"])
+def test_bounded_wait_times_out_and_context_survives(mode):
     torch = _torch()
     js = J()
     mesh = hex_grid(6, 0.15, 1)
     dirs, w = oracle.product_quadrature(1, 3)
-    g = build(mesh, dirs, w, sweep_mode=2, debug_block_waits=1, spin_timeout_s=0.05)
+    g = build(mesh, dirs, w, sweep_mode=mode, debug_block_waits=1, spin_timeout_s=0.05, patch_cells=32)
     N = mesh["n_cells"]
     sig = tensor(np.ones(N), torch.float32)
     src = tensor(np.ones((1, N)), torch.float32)
@@ -248,7 +250,7 @@ def test_bounded_wait_times_out_and_context_survives():
         js.jsweep_sweep(g, sig, src)
     assert e.value.code == js.JSWEEP_ERR_DEVICE_TIMEOUT
     # the context is still usable
-    set_opts(g, sweep_mode=2)
+    set_opts(g, sweep_mode=mode, patch_cells=32)
     o = oracle.build_dags(mesh, dirs)
     phi_ref, _, _ = o.sweep(np.ones(N), np.ones((1, N)), w)
     phi = js.jsweep_sweep(g, sig, src)
@@ -285,3 +287,22 @@ def test_invalid_inputs_are_rejected():
         js.jsweep_sweep(g, tensor(np.ones(N), torch.float32), tensor(np.ones((1, N)), torch.float64))
     with pytest.raises(js.JsweepError):
         js.jsweep_quadrature_create(np.zeros((2, 3)), np.ones(2))
+
+
+@pytest.mark.parametrize("patch_cells", [32, 200, 512])
+def test_patch_programs_source_iteration_fp32_matches_oracle(patch_cells):
+    # patch programs on a cyclic hex mesh and on tets, through source iteration
+    torch = _torch()
+    js = J()
+    for mesh, quad in ((hex_grid(10, 0.3, 7), (6, 6)), (kuhn_tets(7, 0.2, 3), (4, 4))):
+        dirs, w = oracle.product_quadrature(*quad)
+        g = build(mesh, dirs, w, sweep_mode=3, patch_cells=patch_cells)
+        N = mesh["n_cells"]
+        rng = np.random.default_rng(patch_cells)
+        sig, c, q = rng.uniform(0.5, 2.0, N), np.full(N, 0.6), rng.uniform(0.0, 1.0, (2, N))
+        o = oracle.build_dags(mesh, dirs)
+        ref = o.source_iterate(sig, c, q, w, tol=1e-10, max_iters=2000)[0]
+        phi, it, res, ok = js.jsweep_source_iterate(g, tensor(sig, torch.float32), tensor(c, torch.float32),
+                                                    tensor(q, torch.float32), tol=1e-6, max_iters=500)
+        assert ok
+        assert rel_err(phi.cpu().numpy(), ref) < 5 * TOL_F32
