@@ -58,7 +58,8 @@ def parse():
                         "continuous-batching server")
     p.add_argument("--problems", type=int, default=256, help="batch: number of problems")
     p.add_argument("--requests", type=int, default=200, help="serve: number of requests")
-    p.add_argument("--rate", type=float, default=8.0, help="serve: Poisson arrival rate (requests/s)")
+    p.add_argument("--rates", default="8,24",
+                   help="serve: Poisson arrival rates (requests/s), comma-separated; the line's headline is the last")
     p.add_argument("--meshes", type=int, default=24, help="serve: meshes in the catalog")
     p.add_argument("--budget-gb", type=float, default=60.0, help="serve: device-memory budget")
     return p.parse_args()
@@ -655,15 +656,16 @@ def run_serve(args):
     def make_inputs(key, seed):
         return _serve_inputs(by_key[key][0]["n_cells"], seed)
 
-    def stream():
-        return poisson_stream(args.requests, args.rate, keys, make_inputs, seed=5000 + 100 * rank)
+    rates = [float(x) for x in args.rates.split(",") if x.strip()]
+
+    def stream(rate):
+        return poisson_stream(args.requests, rate, keys, make_inputs, seed=5000 + 100 * rank)
 
     tol, max_iters = 1e-6, 1000
     budget = args.budget_gb * 1e9
     be = GpuBackend(lambda k: by_key[k], dtype=torch.float32, tol=tol, max_iters=max_iters)
-    srv = Server(be, budget, sweeps_per_step=1)
     t0 = time.perf_counter()
-    resident = srv.warm(keys)  # meshes and graphs resident before the stream starts
+    resident = Server(be, budget).warm(keys)  # meshes and graphs resident before the stream starts
     torch.cuda.synchronize()
     warm_s = time.perf_counter() - t0
     from paper_1803_09876_gb300.serve import Request
@@ -682,45 +684,61 @@ def run_serve(args):
         warm.run(warm_requests())
 
     work = lambda r: float(r.iters) * by_key[r.mesh_key][0]["n_cells"] * len(by_key[r.mesh_key][1])  # noqa: E731
-    _, _, l0 = be.batch.stats()
-    clocks = ClockSampler(local)
-    clocks.start()
-    served = srv.run(stream())
-    clk = clocks.stop()
-    _, _, l1 = be.batch.stats()
-    s_served = summarize(served, work)
-
     solo_be = GpuBackend(lambda k: by_key[k], dtype=torch.float32, tol=tol, max_iters=max_iters)
     for _ in range(max(1, args.warmup)):
         run_one_at_a_time(solo_be, warm_requests(), meshes=resident)
-    alone = run_one_at_a_time(solo_be, stream(), meshes=resident)
-    s_alone = summarize(alone, work)
-    same = all(a.iters == b_.iters and np.array_equal(a.phi, b_.phi) for a, b_ in zip(
-        sorted(served, key=lambda r: r.rid), sorted(alone, key=lambda r: r.rid)))
+    by_rate = []
+    for rate in rates:
+        srv = Server(be, budget, sweeps_per_step=1)
+        srv.meshes = resident
+        l0 = sum(b.stats()[2] for b in be.batches)
+        clocks = ClockSampler(local)
+        clocks.start()
+        served = srv.run(stream(rate))
+        clk = clocks.stop()
+        l1 = sum(b.stats()[2] for b in be.batches)
+        s_served = summarize(served, work)
+        for _ in range(max(1, args.warmup)):  # the batch path changed the handles' unit tables
+            run_one_at_a_time(solo_be, warm_requests(), meshes=resident)
+        alone = run_one_at_a_time(solo_be, stream(rate), meshes=resident)
+        s_alone = summarize(alone, work)
+        same = all(a.iters == b_.iters and np.array_equal(a.phi, b_.phi) for a, b_ in zip(
+            sorted(served, key=lambda r: r.rid), sorted(alone, key=lambda r: r.rid)))
+        by_rate.append(dict(rate_per_s=rate, served=s_served, one_at_a_time=s_alone,
+                            p99_ratio_one_at_a_time_over_served=s_alone["p99_s"] / s_served["p99_s"],
+                            results_equal_one_at_a_time=bool(same), gpu_launches=int(l1 - l0), clocks=clk,
+                            peak_budget_used_gb=srv.peak_used / 1e9,
+                            h2d_bytes=int(sum((r.sigma_t.size + r.c_ratio.size + r.q.size) * 4 for r in served)),
+                            d2h_bytes=int(sum(r.phi.size * 4 for r in served))))
+        for _ in range(max(1, args.warmup)):  # and back for the next served run
+            warm.run(warm_requests())
+    head = by_rate[-1]
+    s_served = head["served"]
     if rank == 0:
         line = {
             "metric": METRIC, "value": s_served["cell_angle_updates_per_s"], "unit": "cell-angle updates/s",
             "n_gpus": ws, "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * s_served["makespan_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": SERVE_WORKLOAD, "requests": args.requests, "rate_per_s": args.rate,
+            "config": {"workload": SERVE_WORKLOAD, "requests": args.requests, "rate_per_s": head["rate_per_s"],
                        "catalog_meshes": len(cat), "budget_gb": args.budget_gb,
                        "catalog_cells": [int(by_key[k][0]["n_cells"]) for k in keys],
                        "catalog_dirs": [len(by_key[k][1]) for k in keys],
                        "timing": "wall clock per request: arrival to result in host memory",
+                       "lanes": "batches by cells x directions per iteration: < 3e6, < 3e7, larger; one stream each",
                        "parallelism": f"replicas x{ws}"},
             "latency_s": {"p50": s_served["p50_s"], "p99": s_served["p99_s"], "mean": s_served["mean_s"],
                           "max": s_served["max_s"]},
             "served": s_served,
-            "one_at_a_time": s_alone,
-            "p99_ratio_one_at_a_time_over_served": s_alone["p99_s"] / s_served["p99_s"],
-            "results_equal_one_at_a_time": bool(same),
-            "gpu_launches": int(l1 - l0),
-            "clocks": clk,
-            "peak_budget_used_gb": srv.peak_used / 1e9,
+            "one_at_a_time": head["one_at_a_time"],
+            "p99_ratio_one_at_a_time_over_served": head["p99_ratio_one_at_a_time_over_served"],
+            "results_equal_one_at_a_time": all(r["results_equal_one_at_a_time"] for r in by_rate),
+            "by_rate": by_rate,
+            "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"],
+            "peak_budget_used_gb": head["peak_budget_used_gb"],
             "setup_s": {"catalog_build": warm_s},
             "e2e": {"value": s_served["cell_angle_updates_per_s"], "unit": "cell-angle updates/s",
-                    "h2d_bytes_per_step": int(sum((r.sigma_t.size + r.c_ratio.size + r.q.size) * 4 for r in served)),
-                    "d2h_bytes_per_step": int(sum(r.phi.size * 4 for r in served))},
+                    "h2d_bytes_per_step": head["h2d_bytes"], "d2h_bytes_per_step": head["d2h_bytes"]},
         }
         print(json.dumps(line), flush=True)
 

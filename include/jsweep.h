@@ -298,8 +298,16 @@ JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision
  *     (JSWEEP_ERR_OOM if that fails; nothing is added then).
  *   jsweep_batch_step: up to n_sweeps source iterations of every active
  *     problem, then waits for them; a problem that finished during the call
- *     has phi_out written before the call returns.  *n_active (may be NULL)
- *     receives the number of problems still iterating.
+ *     has phi_out written (on the device, by the iteration that finished it)
+ *     before the call returns.  *n_active (may be NULL) receives the number
+ *     of problems still iterating.
+ *   jsweep_batch_launch / jsweep_batch_poll: jsweep_batch_step in two
+ *     halves, so that one host thread can keep several batches (each on its
+ *     own stream) busy at once: launch queues up to n_sweeps iterations and
+ *     returns; poll reports *done = 1 once they have finished (with wait != 0
+ *     it waits for them) and then updates the states and *n_active (may be
+ *     NULL).  A batch takes one launch at a time; the other batch calls wait
+ *     for a pending launch first.
  *   jsweep_batch_query: state (JSWEEP_PROBLEM_*), sweeps done and last
  *     residual of a problem (pointers may be NULL).
  *   jsweep_batch_remove: drops a problem and frees its workspaces.
@@ -328,6 +336,8 @@ JSWEEP_API int jsweep_batch_add(jsweep_batch_t batch, jsweep_dags_t dags, const 
                                 const void *c_ratio, const void *q, const void *inflow, void *phi_out,
                                 double tol, int max_iters, int64_t *id, void *stream);
 JSWEEP_API int jsweep_batch_step(jsweep_batch_t batch, int n_sweeps, int64_t *n_active, void *stream);
+JSWEEP_API int jsweep_batch_launch(jsweep_batch_t batch, int n_sweeps, void *stream);
+JSWEEP_API int jsweep_batch_poll(jsweep_batch_t batch, int wait, int *done, int64_t *n_active);
 JSWEEP_API int jsweep_batch_query(jsweep_batch_t batch, int64_t id, int *state, int *iters, double *resid);
 JSWEEP_API int jsweep_batch_remove(jsweep_batch_t batch, int64_t id);
 JSWEEP_API int jsweep_batch_clear(jsweep_batch_t batch);

@@ -44,7 +44,7 @@ struct ProbState {
     int old_ix;   // phi buffer holding the last iterate (-1: phi = 0)
     int epoch;    // flag stamp of the next sweep
     int state;    // JSWEEP_PROBLEM_*
-    int pad;
+    int done_now; // finished in the iteration that just ran (its phi goes to phi_out)
     double resid;  // residual of the last sweep
 };
 static_assert(sizeof(ProbState) == 32, "ProbState layout");
@@ -55,6 +55,7 @@ template <class T> struct ProbArgs {
     int *flags;  // [N][M] epoch stamps, cell-major like psi
     const T *sig, *cr, *q, *vol, *w;
     T *phi[2];
+    T *phi_out;  // the caller's output array
     const int32_t *lag_m, *lag_up;
     int64_t Tl;
     double tol;
@@ -248,6 +249,7 @@ __global__ void k_advance(const ProbArgs<T> *P, ProbState *S, int np, unsigned l
     if (p >= np) return;
     ProbState st = S[p];
     unsigned long long *ap = acc + (int64_t)p * kAccPerProb;
+    st.done_now = 0;
     if (st.active) {
         double worst = 0.0;
         for (int r = 0; r < P[p].nrhs; ++r) {
@@ -263,13 +265,28 @@ __global__ void k_advance(const ProbArgs<T> *P, ProbState *S, int np, unsigned l
         if (worst < P[p].tol) {
             st.active = 0;
             st.state = JSWEEP_PROBLEM_CONVERGED;
+            st.done_now = 1;
         } else if (st.iters >= P[p].max_iters) {
             st.active = 0;
             st.state = JSWEEP_PROBLEM_MAX_ITERS;
+            st.done_now = 1;
         }
-        S[p] = st;
     }
+    S[p] = st;
     for (int k = 0; k < kAccPerProb; ++k) ap[k] = 0ull;
+}
+
+// phi of the problems that finished in this iteration into the caller's arrays.
+template <class T>
+__global__ void k_deliver_batch(const ProbArgs<T> *P, const ProbState *S, const int64_t *pre, int np, int64_t total) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = find_seg(pre, np, i);
+        if (!S[p].done_now) continue;
+        const ProbArgs<T> &pp = P[p];
+        const int64_t c = i - pre[p], N = pp.a.N;
+        const T *src = pp.phi[S[p].old_ix];
+        for (int r = 0; r < pp.nrhs; ++r) pp.phi_out[(int64_t)r * N + c] = src[(int64_t)r * N + c];
+    }
 }
 
 // Merged unit table: unit li of table k (slot t) goes to base[t * K + k] + (li - slot_ptr_k[t]).
@@ -327,9 +344,17 @@ struct Batch {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double sweep_ms = 0.0, iter_ms = 0.0;
     int64_t launches = 0;  // kernels this batch launched (graph nodes counted per replay)
+    // launch / poll: states of the table's problems copied to pinned host memory
+    void *h_state = nullptr;
+    size_t h_state_bytes = 0;
+    bool pending = false;
+    int pending_k = 0;
+    cudaEvent_t ev_done = nullptr;
     int64_t sweep_nodes = 0;  // sweep launches in one iteration
     ~Batch() {
         cudaDeviceSynchronize();
+        if (h_state) cudaFreeHost(h_state);
+        if (ev_done) cudaEventDestroy(ev_done);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
         for (auto &e : ev)
@@ -405,6 +430,7 @@ template <class T> ProbArgs<T> prob_args(const Batch *b, BatchProb &p) {
     pa.q = static_cast<const T *>(p.q);
     pa.phi[0] = p.phi0.as<T>();
     pa.phi[1] = p.phi1.as<T>();
+    pa.phi_out = static_cast<T *>(p.phi_out);
     pa.lag_m = d->lag_m.as<int32_t>();
     pa.lag_up = d->lag_up.as<int32_t>();
     pa.Tl = d->T;
@@ -618,25 +644,25 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     k_phi_resid_batch<T, R><<<grid_for(b->ncells * 32, 256, 152 * 16), 256, 0, cs>>>(
         P, S, b->cpre.as<int64_t>(), K, b->ncells, b->acc.as<unsigned long long>());
     k_advance<T><<<(K + 127) / 128, 128, 0, cs>>>(P, S, K, b->acc.as<unsigned long long>());
+    k_deliver_batch<T><<<grid_for(b->ncells, 256, 152 * 16), 256, 0, cs>>>(P, S, b->cpre.as<int64_t>(), K,
+                                                                           b->ncells);
     return JSWEEP_OK;
 }
 
 template <class T, int R> int64_t launches_per_iteration(const Batch *b) {
-    return b->sweep_nodes + (b->nlags > 0 ? 4 : 3);
+    return b->sweep_nodes + (b->nlags > 0 ? 5 : 4);
 }
 
-// Up to n_sweeps iterations of the active problems, then the host mirrors
-// and the outputs of problems that finished.
-template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, cudaStream_t s) {
+// Queue up to n_sweeps iterations of the active problems and the copy of
+// their states to pinned host memory; returns without waiting.
+template <class T, int R> int launch_t(Batch *b, int n_sweeps, cudaStream_t s) {
     bool any = false;
     for (auto &p : b->probs) any |= p->st.active != 0;
-    if (!any) {
-        if (n_active) *n_active = 0;
-        return JSWEEP_OK;
-    }
+    if (!any) return JSWEEP_OK;
     if (b->dirty) JS_TRY((build_tables<T, R>(b, s)));
     if (!b->ev[0])
         for (auto &e : b->ev) JS_CUDA(cudaEventCreate(&e));
+    if (!b->ev_done) JS_CUDA(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming));
     if (!b->graph) {
         if (!b->cap) JS_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
         JS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -660,6 +686,14 @@ template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, 
         }
     }
     const int K = (int)b->act.size();
+    const size_t need = (size_t)K * sizeof(ProbState) + 16;
+    if (b->h_state_bytes < need) {
+        if (b->h_state) cudaFreeHost(b->h_state);
+        b->h_state = nullptr;
+        b->h_state_bytes = 0;
+        JS_CUDA(cudaMallocHost(&b->h_state, need));
+        b->h_state_bytes = need;
+    }
     for (int i = 0; i < n_sweeps; ++i) {
         if (i == n_sweeps - 1) JS_CUDA(cudaEventRecord(b->ev[2], s));
         JS_CUDA(cudaGraphLaunch(b->graph, s));
@@ -667,11 +701,22 @@ template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, 
         note_launches(launches_per_iteration<T, R>(b));
         b->launches += launches_per_iteration<T, R>(b);
     }
-    std::vector<ProbState> S(K);
+    JS_CUDA(cudaMemcpyAsync(b->h_state, b->pstate.p, (size_t)K * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaMemcpyAsync(static_cast<char *>(b->h_state) + (size_t)K * sizeof(ProbState), b->err.p, 4,
+                            cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaEventRecord(b->ev_done, s));
+    b->pending = true;
+    b->pending_k = K;
+    return JSWEEP_OK;
+}
+
+// The queued iterations have finished: update the host mirrors.
+int finish_launch(Batch *b, int64_t *n_active) {
+    b->pending = false;
+    const int K = b->pending_k;
+    const ProbState *S = static_cast<const ProbState *>(b->h_state);
     int errh = 0;
-    JS_CUDA(cudaMemcpyAsync(S.data(), b->pstate.p, (size_t)K * sizeof(ProbState), cudaMemcpyDeviceToHost, s));
-    JS_CUDA(cudaMemcpyAsync(&errh, b->err.p, 4, cudaMemcpyDeviceToHost, s));
-    JS_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&errh, static_cast<const char *>(b->h_state) + (size_t)K * sizeof(ProbState), 4);
     float ms_sweep = 0.f, ms_iter = 0.f;
     if (cudaEventElapsedTime(&ms_sweep, b->ev[0], b->ev[1]) != cudaSuccess) ms_sweep = 0.f;
     if (cudaEventElapsedTime(&ms_iter, b->ev[2], b->ev[3]) != cudaSuccess) ms_iter = 0.f;
@@ -679,31 +724,38 @@ template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, 
     b->sweep_ms = ms_sweep;
     b->iter_ms = ms_iter;
     if (errh) {
-        JS_CUDA(cudaMemsetAsync(b->err.p, 0, 16, s));
-        JS_CUDA(cudaStreamSynchronize(s));
+        JS_CUDA(cudaMemset(b->err.p, 0, 16));
         set_error("batched sweep: a dependency wait exceeded %.3g s", b->opt.spin_timeout_s);
         return JSWEEP_ERR_DEVICE_TIMEOUT;
     }
-    int64_t still = 0, idle_units = 0;
-    bool changed = false;
+    int64_t idle_units = 0;
     for (int k = 0; k < K; ++k) {
         BatchProb &p = *b->probs[b->act[k]];
-        const bool was = p.st.active != 0;
-        p.st = S[k];
-        if (was && !p.st.active) {
-            changed = true;
-            T *src = p.st.old_ix == 1 ? p.phi1.as<T>() : p.phi0.as<T>();
-            JS_CUDA(cudaMemcpyAsync(p.phi_out, src, (size_t)b->nrhs * p.d->N * sizeof(T), cudaMemcpyDeviceToDevice,
-                                    s));
-        }
-        still += p.st.active != 0;
+        p.st = S[k];  // a problem that finished had its phi delivered on the device
         if (!p.st.active) idle_units += b->tab_units[k];
     }
-    if (changed) JS_CUDA(cudaStreamSynchronize(s));
     // finished problems stay in the table (their units are skipped) until they
-    // hold half of it; then the next step rebuilds it from the active ones
+    // hold half of it; then the next launch rebuilds it from the active ones
     if (2 * idle_units > b->n_units) b->dirty = true;
-    if (n_active) *n_active = still;
+    if (n_active) {
+        int64_t all = 0;
+        for (auto &p : b->probs) all += p->st.active != 0;
+        *n_active = all;
+    }
+    return JSWEEP_OK;
+}
+
+// Wait for a queued launch, if any, and take its results.
+int settle(Batch *b, int64_t *n_active) {
+    if (b->pending) {
+        JS_CUDA(cudaEventSynchronize(b->ev_done));
+        return finish_launch(b, n_active);
+    }
+    if (n_active) {
+        int64_t all = 0;
+        for (auto &p : b->probs) all += p->st.active != 0;
+        *n_active = all;
+    }
     return JSWEEP_OK;
 }
 
@@ -725,8 +777,18 @@ template <class T, int R> int step_t(Batch *b, int n_sweeps, int64_t *n_active, 
         }                                                            \
     } while (0)
 
+int launch(Batch *b, int n_sweeps, cudaStream_t s) {
+    if (b->pending) {
+        set_error("jsweep_batch_launch: the previous launch has not been polled to completion");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    JS_BATCH_DISPATCH(launch_t, b, n_sweeps, s);
+}
+
 int step(Batch *b, int n_sweeps, int64_t *n_active, cudaStream_t s) {
-    JS_BATCH_DISPATCH(step_t, b, n_sweeps, n_active, s);
+    JS_TRY(settle(b, nullptr));
+    JS_TRY(launch(b, n_sweeps, s));
+    return settle(b, n_active);
 }
 
 int restart_all(Batch *b, cudaStream_t s) {
@@ -797,6 +859,7 @@ JSWEEP_API int jsweep_batch_add(jsweep_batch_t batch, jsweep_dags_t dags, const 
     }
     js::Dags *d = impl(dags);
     cudaStream_t s = (cudaStream_t)stream;
+    JS_TRY(js::settle(b, nullptr));
     auto p = std::make_unique<BatchProb>();
     const size_t es = b->prec == JSWEEP_F64 ? 8 : 4;
     const int64_t N = d->N, M = d->M, R = b->Rp;
@@ -841,6 +904,38 @@ JSWEEP_API int jsweep_batch_step(jsweep_batch_t batch, int n_sweeps, int64_t *n_
     return js::step(bimpl(batch), n_sweeps, n_active, (cudaStream_t)stream);
 }
 
+JSWEEP_API int jsweep_batch_launch(jsweep_batch_t batch, int n_sweeps, void *stream) {
+    js::clear_error();
+    if (!batch || n_sweeps < 1) {
+        js::set_error("jsweep_batch_launch: batch=%p n_sweeps=%d", (void *)batch, n_sweeps);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    return js::launch(bimpl(batch), n_sweeps, (cudaStream_t)stream);
+}
+
+JSWEEP_API int jsweep_batch_poll(jsweep_batch_t batch, int wait, int *done, int64_t *n_active) {
+    js::clear_error();
+    if (!batch || !done) {
+        js::set_error("jsweep_batch_poll: NULL argument");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    Batch *b = bimpl(batch);
+    if (b->pending && !wait) {
+        const cudaError_t q = cudaEventQuery(b->ev_done);
+        if (q == cudaErrorNotReady) {
+            (void)cudaGetLastError();
+            *done = 0;
+            return JSWEEP_OK;
+        }
+        if (q != cudaSuccess) {
+            js::set_error("jsweep_batch_poll: %s", cudaGetErrorString(q));
+            return JSWEEP_ERR_CUDA;
+        }
+    }
+    *done = 1;
+    return js::settle(b, n_active);
+}
+
 JSWEEP_API int jsweep_batch_query(jsweep_batch_t batch, int64_t id, int *state, int *iters, double *resid) {
     js::clear_error();
     BatchProb *p = batch ? js::find_id(bimpl(batch), id) : nullptr;
@@ -862,6 +957,7 @@ JSWEEP_API int jsweep_batch_remove(jsweep_batch_t batch, int64_t id) {
         js::set_error("jsweep_batch_remove: no problem with id %lld", (long long)id);
         return JSWEEP_ERR_INVALID_ARG;
     }
+    JS_TRY(js::settle(b, nullptr));
     cudaDeviceSynchronize();  // no batched launch may still use its buffers
     b->probs.erase(b->probs.begin() + (ptrdiff_t)pos);
     b->dirty = true;  // the tables refer to problems by position
@@ -874,6 +970,7 @@ JSWEEP_API int jsweep_batch_clear(jsweep_batch_t batch) {
         js::set_error("jsweep_batch_clear: NULL");
         return JSWEEP_ERR_INVALID_ARG;
     }
+    JS_TRY(js::settle(bimpl(batch), nullptr));
     cudaDeviceSynchronize();
     bimpl(batch)->probs.clear();
     bimpl(batch)->dirty = true;
@@ -898,6 +995,7 @@ JSWEEP_API int jsweep_batch_source_iterate(jsweep_batch_t batch, int *iters_out,
     }
     Batch *b = bimpl(batch);
     cudaStream_t s = (cudaStream_t)stream;
+    JS_TRY(js::settle(b, nullptr));
     JS_TRY(js::restart_all(b, s));
     int64_t n_active = (int64_t)b->probs.size();
     while (n_active > 0) JS_TRY(js::step(b, 1, &n_active, s));
@@ -923,6 +1021,7 @@ JSWEEP_API int jsweep_batch_autotune(jsweep_batch_t batch, void *stream, double 
     }
     Batch *b = bimpl(batch);
     cudaStream_t s = (cudaStream_t)stream;
+    JS_TRY(js::settle(b, nullptr));
     struct Cand {
         int mode, cells, apw, order;
     };

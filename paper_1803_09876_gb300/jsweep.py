@@ -58,6 +58,7 @@ EXPORTED = [
     "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
     "jsweep_source_iterate_noalloc",
     "jsweep_batch_create", "jsweep_batch_problem_bytes", "jsweep_batch_add", "jsweep_batch_step",
+    "jsweep_batch_launch", "jsweep_batch_poll",
     "jsweep_batch_query", "jsweep_batch_remove", "jsweep_batch_clear", "jsweep_batch_size",
     "jsweep_batch_source_iterate", "jsweep_batch_autotune", "jsweep_batch_stats", "jsweep_batch_options",
     "jsweep_batch_destroy",
@@ -172,6 +173,8 @@ def load(path: str = LIB_PATH):
             "jsweep_batch_problem_bytes": (I, [P, P, I, P]),
             "jsweep_batch_add": (I, [P, P, P, P, P, P, P, ctypes.c_double, I, P, P]),
             "jsweep_batch_step": (I, [P, I, P, P]),
+            "jsweep_batch_launch": (I, [P, I, P]),
+            "jsweep_batch_poll": (I, [P, I, P, P]),
             "jsweep_batch_query": (I, [P, I64, P, P, P]),
             "jsweep_batch_remove": (I, [P, I64]),
             "jsweep_batch_clear": (I, [P]),
@@ -508,6 +511,17 @@ class Batch:
         _check(lib().jsweep_batch_step(self._h, int(n_sweeps), ctypes.byref(n), _stream(stream)),
                "jsweep_batch_step")
         return n.value
+
+    def launch(self, n_sweeps: int = 1, stream=None):
+        """Queue up to n_sweeps iterations and return at once (see poll)."""
+        _check(lib().jsweep_batch_launch(self._h, int(n_sweeps), _stream(stream)), "jsweep_batch_launch")
+
+    def poll(self, wait: bool = False):
+        """(finished, problems still iterating) of the last launch."""
+        done, n = ctypes.c_int(), ctypes.c_int64()
+        _check(lib().jsweep_batch_poll(self._h, int(bool(wait)), ctypes.byref(done), ctypes.byref(n)),
+               "jsweep_batch_poll")
+        return bool(done.value), n.value
 
     def query(self, pid: int):
         """(state, iterations, residual) of a problem."""

@@ -213,7 +213,10 @@ class Server:
                     break
                 waiting.popleft()
             if self.active:
-                self.be.step(self.k)
+                if hasattr(self.be, "pump"):
+                    self.be.pump(self.k)  # returns once some lane has finished an iteration
+                else:
+                    self.be.step(self.k)
                 self.steps += 1
                 now = self.clock() - self._t0
                 for pid in list(self.active):
@@ -265,11 +268,18 @@ def summarize(reqs, cell_dir_updates: Callable[[Request], float]):
 
 
 class GpuBackend:
-    """The library's C ABI: graphs from jsweep_build_dags, requests in one
-    jsweep batch, the comparison through jsweep_source_iterate."""
+    """The library's C ABI: graphs from jsweep_build_dags, requests in jsweep
+    batches, the comparison through jsweep_source_iterate.
+
+    Requests are split by work per iteration (cells x directions) into lanes,
+    one batch and one CUDA stream per lane (``lanes`` gives the upper bounds
+    of all lanes but the last).  A small request then iterates at the pace of
+    the small requests, not of the largest mesh in the mix; the lanes run
+    concurrently on the device (jsweep_batch_launch / jsweep_batch_poll).
+    """
 
     def __init__(self, catalog: Callable[[Any], tuple], dtype=None, nrhs=1, tol=1e-6, max_iters=1000,
-                 options=None, batch_options=None):
+                 options=None, batch_options=None, lanes=(3e6, 3e7)):
         import torch
 
         from . import jsweep as J
@@ -281,10 +291,26 @@ class GpuBackend:
         self.tol = tol
         self.max_iters = max_iters
         self.options = options
-        self.batch = J.Batch(self.dtype, nrhs, batch_options)
+        self.bounds = list(lanes)
+        n = len(self.bounds) + 1
+        self.batches = [J.Batch(self.dtype, nrhs, batch_options) for _ in range(n)]
+        self.streams = [torch.cuda.Stream() for _ in range(n)]
+        self.active = [0] * n      # unfinished problems per lane
+        self.pending = [False] * n
         self.inputs = {}
         self._est = {}
         self.builds = 0
+
+    @property
+    def batch(self):  # the first lane (kept for single-lane use)
+        return self.batches[0]
+
+    def lane_of(self, handle):
+        work = handle.n_cells * handle.n_dirs
+        for i, b in enumerate(self.bounds):
+            if work < b:
+                return i
+        return len(self.bounds)
 
     # sizes
     def _shape(self, key):
@@ -331,7 +357,7 @@ class GpuBackend:
         es = 8 if self.dtype == self.torch.float64 else 4
         io = (2 * handle.n_cells + 2 * req.q.size) * es  # sigma_t, c, q, phi_out
         tables = 5 * handle.n_dirs * handle.n_cells  # merged and per-handle unit tables
-        return self.batch.problem_bytes(handle) + io + tables
+        return self.batches[self.lane_of(handle)].problem_bytes(handle) + io + tables
 
     def _tensors(self, req):
         t = self.torch
@@ -343,23 +369,57 @@ class GpuBackend:
 
     def add(self, handle, req):
         sig, c, q = self._tensors(req)
-        pid = self.batch.add(handle, sig, c, q, tol=self.tol, max_iters=self.max_iters)
+        lane = self.lane_of(handle)
+        pid = (lane, self.batches[lane].add(handle, sig, c, q, tol=self.tol, max_iters=self.max_iters))
         self.inputs[pid] = req
+        self.active[lane] += 1
         return pid
 
     def step(self, k):
-        return self.batch.step(k)
+        for lane in range(len(self.batches)):
+            if self.active[lane]:
+                self.active[lane] = self.batches[lane].step(k, stream=self.streams[lane])
+
+    def pump(self, k, spin_s=20e-6):
+        """Keep every lane with unfinished problems busy; return once at least
+        one lane has finished its queued iterations."""
+        while True:
+            for lane, b in enumerate(self.batches):
+                if self.active[lane] and not self.pending[lane]:
+                    b.launch(k, stream=self.streams[lane])
+                    self.pending[lane] = True
+            progressed = False
+            for lane, b in enumerate(self.batches):
+                if self.pending[lane]:
+                    done, n = b.poll()
+                    if done:
+                        self.pending[lane] = False
+                        self.active[lane] = n
+                        progressed = True
+            if progressed or not any(self.pending):
+                return
+            time.sleep(spin_s)
 
     def finished(self, pid):
-        return self.batch.query(pid)[0] != self.J.JSWEEP_PROBLEM_ACTIVE
+        lane, i = pid
+        return self.batches[lane].query(i)[0] != self.J.JSWEEP_PROBLEM_ACTIVE
 
     def result(self, pid):
-        st, it, res = self.batch.query(pid)
-        phi = self.batch.phi(pid).cpu().numpy()
+        lane, i = pid
+        st, it, res = self.batches[lane].query(i)
+        phi = self.batches[lane].phi(i).cpu().numpy()  # written by the lane's finished iteration
         return phi, it, res
 
     def remove(self, pid):
-        self.batch.remove(pid)
+        lane, i = pid
+        if self.pending[lane]:
+            done, n = self.batches[lane].poll(wait=True)
+            self.pending[lane] = False
+            self.active[lane] = n
+        was_active = self.batches[lane].query(i)[0] == self.J.JSWEEP_PROBLEM_ACTIVE
+        self.batches[lane].remove(i)
+        if was_active:
+            self.active[lane] = max(0, self.active[lane] - 1)
         self.inputs.pop(pid, None)
 
     def solve_alone(self, handle, req):

@@ -270,3 +270,39 @@ def test_batch_timeout_reports_error_and_recovers():
     # the context is still usable
     ref, it_ref, _ = _solo(js, d, 1e-6)
     assert it_ref > 1 and np.isfinite(ref).all()
+
+
+def test_launch_and_poll_two_batches_on_two_streams():
+    # one host thread keeps two batches busy at once; each result equals the
+    # problem solved alone
+    torch = _torch()
+    js, data = _setup(torch.float32)
+    refs = [_solo(js, d, 1e-6) for d in data]
+    lanes = [js.Batch(torch.float32, 1), js.Batch(torch.float32, 1)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ids = []
+    for k, d in enumerate(data):
+        b = lanes[k % 2]
+        ids.append((k % 2, b.add(d["g"], d["sig"], d["c"], d["q"], inflow=d["inflow"], tol=1e-6)))
+    active = [sum(1 for lane, _ in ids if lane == i) for i in range(2)]
+    pending = [False, False]
+    rounds = 0
+    while any(active) or any(pending):
+        for i, b in enumerate(lanes):
+            if active[i] and not pending[i]:
+                b.launch(1, stream=streams[i])
+                pending[i] = True
+        for i, b in enumerate(lanes):
+            if pending[i]:
+                done, n = b.poll()
+                if done:
+                    pending[i] = False
+                    active[i] = n
+        rounds += 1
+        assert rounds < 10_000_000
+    for (lane, pid), (ref, it_ref, res_ref) in zip(ids, refs):
+        st, it, res = lanes[lane].query(pid)
+        assert st == js.JSWEEP_PROBLEM_CONVERGED and it == it_ref and res == res_ref
+        assert np.array_equal(lanes[lane].phi(pid).cpu().numpy(), ref)
+    with pytest.raises(js.JsweepError):
+        lanes[0].launch(0)
