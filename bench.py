@@ -35,6 +35,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "cell-angle updates/s"
+# DRAM bytes (read + write) of one sweep of the dominant kernel, from the full-sweep ncu capture
+# summarised in profiles/k_sweep_level_hex128_full_sweep_dram.md; keyed by
+# (hex edge, sweep mode, priority, cluster cells, layering); valid while the kernel is unchanged
+SWEEP_TRAFFIC_BYTES = {(128, 1, 0, 32, 0): 1.615e11}
 UNIT = "cell-angle-rhs updates/s"
 WORKLOAD = "hex128_jitter0.15_288dirs_8rhs_fp32_si_tol1e-6"
 
@@ -56,9 +60,12 @@ def parse():
                    help="hex128: the single large problem (default line); batch: 256 independent tet problems "
                         "in one persistent launch per iteration; serve: Poisson request stream through the "
                         "continuous-batching server")
+    p.add_argument("--sweeps", type=int, default=0,
+                   help="profiling aid (hex128 workload): build the graphs, then run this many plain sweeps of the "
+                        "workload's right-hand sides (no source iteration) and print their times")
     p.add_argument("--problems", type=int, default=256, help="batch: number of problems")
     p.add_argument("--requests", type=int, default=200, help="serve: number of requests")
-    p.add_argument("--rates", default="8,24",
+    p.add_argument("--rates", default="8,24,48",
                    help="serve: Poisson arrival rates (requests/s), comma-separated; the line's headline is the last")
     p.add_argument("--meshes", type=int, default=24, help="serve: meshes in the catalog")
     p.add_argument("--budget-gb", type=float, default=60.0, help="serve: device-memory budget")
@@ -287,8 +294,10 @@ def run_gpu(args):
     achieved = alg_bytes / ((sw_ms + ph_ms) / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic = SWEEP_TRAFFIC_BYTES.get((args.n, args.mode, args.priority, args.cluster, args.layering))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": traffic,
+            "traffic_unit": "bytes per sweep (one launch sequence of the CUDA graph)",
             "kernel": ("sweep (level-synchronous CUDA graph)" if args.mode == 1 else "sweep (data-driven persistent)")
                       + " + phi reduction, one sweep of all directions",
             "alg_bytes_per_cell_dir": B, "sweep_ms": sw_ms, "phi_ms": ph_ms,
@@ -510,7 +519,7 @@ def run_batch(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = alg / (sw / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": None,  # no DRAM capture of the batched kernel yet
             "kernel": ("k_sweep_dd_batch, one persistent launch" if o.sweep_mode == J.JSWEEP_MODE_PERSISTENT
                        else "k_sweep_level_batch, one CUDA-graph node per merged slot")
                       + " over all problems and directions (one full iteration)",
@@ -743,8 +752,42 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_sweeps(args):
+    """Build the graphs of the workload once, then args.sweeps plain sweeps
+    (the launch sequence the per-kernel ncu captures in profiles/ skip into)."""
+    import torch
+
+    from inputs import make_workload
+    from paper_1803_09876_gb300 import build as libbuild
+    from paper_1803_09876_gb300 import jsweep as J
+
+    libbuild.build()
+    J.load()
+    J.use_torch_allocator()
+    wl = make_workload(3, n=args.n)
+    N, R = wl["n_cells"], wl["q"].shape[0]
+    dirs, w = J.jsweep_quadrature_product(*wl["spec"]["quad"])
+    M = len(dirs)
+    opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
+                                   layering=args.layering)
+    dags = J.jsweep_build_dags(J.mesh_from_dict(wl), J.jsweep_quadrature_create(dirs, w), opt)
+    sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device="cuda")
+    src = torch.as_tensor(wl["q"] / (4 * math.pi), dtype=torch.float32, device="cuda").contiguous()
+    phi = torch.empty((R, N), dtype=torch.float32, device="cuda")
+    out = []
+    for _ in range(args.sweeps):
+        J.jsweep_sweep(dags, sig, src, phi_out=phi)
+        tm = dags.timing()
+        out.append({"sweep_ms": tm["sweep_ms"], "phi_ms": tm["phi_ms"], "launches": tm["sweep_launches"]})
+    print(json.dumps({"workload": f"hex{args.n}_{M}dirs_{R}rhs", "mode": args.mode, "cells": N, "directions": M,
+                      "build_ms": dags.timing()["build_ms"], "sweeps": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweeps > 0 and args.impl != "reference":
+        run_sweeps(args)
+        return
     if args.impl == "reference":
         if args.workload == "hex128":
             run_reference(args)
