@@ -122,6 +122,7 @@ template <class T, int R, int SPLIT, int MAXF, int A>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sweep_level_batch(const ProbArgs<T> *__restrict__ P, const ProbState *__restrict__ S, const int4 *units,
                         const int32_t *uprob, int64_t u0, int64_t nu) {
+    pdl_launch_next();
     const int lane = threadIdx.x & 31;
     constexpr int LPU = 32 / A;
     const int a_ix = lane / LPU, ll = lane % LPU, cell = ll / SPLIT, sub = ll % SPLIT;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     if (cell < u.z && S[p].active) {
         const ProbArgs<T> &pp = P[p];
         const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
-        solve_cell<T, R, SPLIT, MAXF, false>(pp.a, u.x, __ldg(pp.a.order + idx), __ldg(pp.a.mask + idx), sub,
+        solve_cell<T, R, SPLIT, MAXF, false, true>(pp.a, u.x, __ldg(pp.a.order + idx), __ldg(pp.a.mask + idx), sub,
                                              nullptr, 0, nullptr, 0);
     }
 }
@@ -606,8 +607,19 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
             if (nu <= 0) continue;
             const int64_t warps = (nu + b->apw - 1) / b->apw;
             void *args[] = {(void *)&P, (void *)&S, (void *)&units, (void *)&uprob, (void *)&u0, (void *)&nu};
-            JS_CUDA(cudaLaunchKernel(lk, dim3((unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock)),
-                                     dim3(kWarpsPerBlock * 32), args, 0, cs));
+            // programmatic dependent launch: the next slot starts while this one drains
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock));
+            cfg.blockDim = dim3(kWarpsPerBlock * 32);
+            cfg.stream = cs;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            // the first slot reads the source records the emission kernel just
+            // wrote: it keeps a full dependency
+            cfg.numAttrs = b->sweep_nodes == 0 ? 0 : 1;
+            JS_CUDA(cudaLaunchKernelExC(&cfg, lk, args));
             ++b->sweep_nodes;
         }
         JS_CUDA(cudaEventRecordWithFlags(b->ev[1], cs, cudaEventRecordExternal));

@@ -40,6 +40,7 @@ namespace {
 // of 32 / SPLIT cells.
 template <class T, int R, int SPLIT, int MAXF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T> a, int64_t u0, int64_t nu) {
+    pdl_launch_next();
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (t >= nu) return;
@@ -47,8 +48,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T
     const int cell = lane / SPLIT, sub = lane % SPLIT;
     if (cell < u.z) {
         const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
-        solve_cell<T, R, SPLIT, MAXF, false>(a, u.x, __ldg(a.order + idx), __ldg(a.mask + idx), sub, nullptr, 0,
-                                             nullptr, 0);
+        solve_cell<T, R, SPLIT, MAXF, false, true>(a, u.x, __ldg(a.order + idx), __ldg(a.mask + idx), sub, nullptr,
+                                                   0, nullptr, 0);
     }
 }
 
@@ -674,11 +675,25 @@ template <class T, int R> int64_t patch_warps(const Dags *d, int mode) {
 template <class T, int R, int SPLIT, int MAXF>
 void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs) {
     const auto &sp = d->ut.slot_ptr;
+    bool first = true;
     for (size_t l = 0; l + 1 < sp.size(); ++l) {
         const int64_t nu = sp[l + 1] - sp[l];
         if (nu <= 0) continue;
         const int64_t blocks = (nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        k_sweep_level<T, R, SPLIT, MAXF><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, cs>>>(a, sp[l], nu);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(kWarpsPerBlock * 32);
+        cfg.stream = cs;
+        // slots after the first start early (programmatic dependent launch); the
+        // first keeps a full dependency on whatever preceded the sweep
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = first ? 0 : 1;
+        first = false;
+        int64_t u0 = sp[l];
+        cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
     }
 }
 

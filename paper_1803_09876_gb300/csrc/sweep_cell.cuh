@@ -131,7 +131,14 @@ template <class T, int MAXF> struct CellGeo {
 // then the upwind loads of all incoming faces, are in flight together.
 // WAIT: before reading an upwind cell's psi, spin (bounded) until that cell's
 // flag for this direction shows the current sweep epoch (data-driven schedule).
-template <class T, int R, int SPLIT, int MAXF, bool WAIT>
+// Programmatic dependent launch (level-synchronous slots): a slot kernel lets
+// the next slot's kernel start early; that kernel reads everything that does
+// not change during a sweep (unit, order, mask, geometry, sources) and waits
+// for the previous slots to complete only before it reads upwind psi.
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class T, int R, int SPLIT, int MAXF, bool WAIT, bool PDL = false>
 __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
                                            const int *flags, int want, int *err, long long timeout) {
     using V = typename V4<T>::type;
@@ -162,6 +169,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
             }
         }
     }
+    if constexpr (PDL) pdl_wait_prev();  // upwind values come from earlier slots
     if constexpr (WAIT) {
         // wait until every active interior upwind cell of this direction is done
         // (flags are cell-major, [N][M], like psi: the flags of one cell for
