@@ -130,7 +130,11 @@ typedef struct {
                               units covering the same cells for different directions run side by side
                               and share the cells' geometry and sources in cache */
     int patch_cells;       /* JSWEEP_MODE_PATCH: target cells per patch (default 512, 32..4096) */
-    int reserved[3];
+    int eager_search_max;  /* cells a cycle search may visit while its direction is still peeling (default
+                              64, at most cycle_search_max); a stalled direction searches up to
+                              cycle_search_max, and a build that cannot break a cycle this way is
+                              repeated once with cycle_search_max everywhere.  Lags do not depend on it. */
+    int reserved[2];
 } jsweep_options;
 
 /* Fill *opt with defaults. */

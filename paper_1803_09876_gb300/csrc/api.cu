@@ -1,3 +1,4 @@
+#include <algorithm>
 // C ABI entry points: errors, allocator, mesh and quadrature handles, option
 // handling and the dependency-graph handle's host-side accessors.
 #include <climits>
@@ -176,6 +177,7 @@ int jsweep_options_default(jsweep_options *opt) {
     opt->unit_order = 1;
     opt->angles_per_warp = 1;
     opt->patch_cells = 512;
+    opt->eager_search_max = 64;
     return JSWEEP_OK;
 }
 
@@ -488,6 +490,11 @@ int check_options(const jsweep_options *opt, jsweep_options *o) {
         return JSWEEP_ERR_INVALID_ARG;
     }
     if (opt->patch_cells > 0) o->patch_cells = opt->patch_cells;
+    if (opt->eager_search_max < 0 || opt->eager_search_max > 1024) {
+        set_error("jsweep_options.eager_search_max=%d out of range (0..1024)", opt->eager_search_max);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    if (opt->eager_search_max > 0) o->eager_search_max = opt->eager_search_max;
     if (opt->angles_per_warp != 0 && opt->angles_per_warp != 1 && opt->angles_per_warp != 2 &&
         opt->angles_per_warp != 4) {
         set_error("jsweep_options.angles_per_warp=%d (1, 2 or 4)", opt->angles_per_warp);
@@ -525,8 +532,28 @@ int jsweep_build_dags(jsweep_mesh_t mesh, jsweep_quad_t quad, const jsweep_optio
         set_error("jsweep_build_dags: problem too large");
         return JSWEEP_ERR_INVALID_ARG;
     }
+    // First attempt: eager cycle searches capped at eager_search_max cells (most
+    // components are a few cells; larger eager searches mostly run into cells
+    // that are not peeled yet).  If that leaves a component the stalled search
+    // cannot close, build again with the full cap everywhere.
     const int64_t l0 = g_kernel_launches.load();
+    d->eager_cap = std::min(d->opt.eager_search_max > 0 ? d->opt.eager_search_max : 64, d->opt.cycle_search_max);
     rc = build_dags(d, (cudaStream_t)stream);
+    if (rc == JSWEEP_ERR_CYCLE && d->eager_cap < d->opt.cycle_search_max) {
+        Dags *d2 = new Dags();
+        d2->opt = d->opt;
+        d2->mesh = d->mesh;
+        d2->mesh->refs.fetch_add(1);
+        d2->quad = d->quad;
+        d2->quad->refs.fetch_add(1);
+        d2->N = d->N;
+        d2->M = d->M;
+        d2->eager_cap = d->opt.cycle_search_max;
+        delete d;
+        d = d2;
+        clear_error();
+        rc = build_dags(d, (cudaStream_t)stream);
+    }
     d->timing.build_launches = g_kernel_launches.load() - l0;
     if (rc != JSWEEP_OK) {
         delete d;

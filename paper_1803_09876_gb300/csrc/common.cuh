@@ -150,6 +150,7 @@ struct PatchSched {
 
 struct Dags {
     std::atomic<int> refs{1};  // the handle and every batch problem that uses it
+    int eager_cap = 0;         // cells an eager (not stalled) cycle search may visit; 0 = cycle_search_max
     Mesh *mesh = nullptr;
     Quad *quad = nullptr;
     jsweep_options opt{};

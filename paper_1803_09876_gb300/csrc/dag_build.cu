@@ -301,7 +301,7 @@ __global__ void k_walk(BuildCtx c, int nxt, int walk_max) {
 // through its smallest cell).  Then the direction's candidate lists are
 // rotated.  Dynamic shared memory: per warp X[B] (int32), Sidx[B] (int32),
 // inS[B] (uint8).
-__global__ void k_resolve(BuildCtx c, int nxt, int B) {
+__global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
     const int64_t m = blockIdx.x;
     bool stalled;
     if (!resolve_active(c, m, nxt, &stalled)) return;
@@ -326,6 +326,12 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B) {
     int32_t *Sidx = X + B;
     uint8_t *inS = reinterpret_cast<uint8_t *>(Sidx + B);
     int my_lags = 0;
+    // Before a direction stalls, the backward closure of a cycle often runs into
+    // upstream cells that are merely not peeled yet and cannot close; an eager
+    // search therefore stops at Beager cells, a stalled direction searches up
+    // to B.  A closure that does not close is retried later, so the lags found
+    // do not depend on the caps (only whether the build succeeds can).
+    const int Bcap = stalled ? B : min(B, Beager);
     for (int si = warp; si < ns_total; si += kResolveWarps) {
         const int32_t seed = seeds[si];
         // ---- backward closure of the seed over unfinished cells, capped at B
@@ -349,7 +355,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B) {
                 todo &= todo - 1;
                 int32_t uu = __shfl_sync(0xffffffffu, u, src);
                 if (warp_find(X, size, uu, lane) < 0) {
-                    if (size == B) {
+                    if (size == Bcap) {
                         closed = false;
                         break;
                     }
@@ -1027,7 +1033,7 @@ int build_dags(Dags *d, cudaStream_t s) {
         int cur = (int)(step & 1);
         k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
         k_walk<<<dim3(8, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
-        k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B);
+        k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B, d->eager_cap > 0 ? d->eager_cap : B);
         k_commit<<<64, 256, 0, s>>>(c, cur ^ 1, cur);
         note_launches(3);  // peel, walk, resolve; the check below counts commit
         JS_LAUNCH_CHECK();

@@ -86,7 +86,8 @@ class jsweep_options(ctypes.Structure):
         ("angles_per_warp", ctypes.c_int),
         ("unit_order", ctypes.c_int),
         ("patch_cells", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("eager_search_max", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 

@@ -125,3 +125,13 @@ def test_workload2_full_size_sampled_directions_bit_exact():
     wl = make_workload(2)
     dirs, w = oracle.product_quadrature(*wl["spec"]["quad"])
     compare_all(wl, dirs, w, dir_sample=_sample_dirs(dirs, 3, 2))
+
+
+@pytest.mark.parametrize("eager", [1, 8, 1024])
+def test_eager_search_cap_does_not_change_the_graphs(eager):
+    # eager cycle searches capped at 1..1024 cells (a build that cannot break a
+    # cycle that way is repeated with the full cap): the graphs are the oracle's
+    mesh = hex_grid(16, 0.3, 5)
+    dirs, w = oracle.product_quadrature(6, 6)
+    _, n_lag = compare_all(mesh, dirs, w, eager_search_max=eager, cycle_search_max=max(256, eager))
+    assert n_lag > 100
