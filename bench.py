@@ -56,10 +56,11 @@ def parse():
     p.add_argument("--cluster", type=int, default=32)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve"],
+    p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve", "wl1", "wl2"],
                    help="hex128: the single large problem (default line); batch: 256 independent tet problems "
                         "in one persistent launch per iteration; serve: Poisson request stream through the "
-                        "continuous-batching server")
+                        "continuous-batching server; wl1: 16^3 hex FP64 source iteration to 1e-8 (launch-bound: "
+                        "time per solve); wl2: 48^3 Kuhn tets FP32 source iteration to 1e-6")
     p.add_argument("--sweeps", type=int, default=0,
                    help="profiling aid (hex128 workload): build the graphs, then run this many plain sweeps of the "
                         "workload's right-hand sides (no source iteration) and print their times")
@@ -752,6 +753,63 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_small(args):
+    """Workloads 1 and 2: one step = DAG build + source iteration, timed on the device."""
+    import torch
+
+    from inputs import make_workload
+    from paper_1803_09876_gb300 import build as libbuild
+    from paper_1803_09876_gb300 import jsweep as J
+
+    libbuild.build()
+    J.load()
+    J.use_torch_allocator()
+    wid = 1 if args.workload == "wl1" else 2
+    wl = make_workload(wid)
+    dtype = torch.float64 if wid == 1 else torch.float32
+    tol = wl["spec"]["tol"]
+    N, R = wl["n_cells"], wl["q"].shape[0]
+    dirs, w = J.jsweep_quadrature_product(*wl["spec"]["quad"])
+    M = len(dirs)
+    mesh = J.mesh_from_dict(wl)
+    quad = J.jsweep_quadrature_create(dirs, w)
+    opt = J.jsweep_options_default(sweep_mode=args.mode)
+    sig = torch.as_tensor(wl["sigma_t"], dtype=dtype, device="cuda")
+    cr = torch.as_tensor(wl["c_ratio"], dtype=dtype, device="cuda")
+    q = torch.as_tensor(wl["q"], dtype=dtype, device="cuda").contiguous()
+    phi = torch.empty((R, N), dtype=dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g = J.jsweep_build_dags(mesh, quad, opt)
+        _, it, res, _ = J.jsweep_source_iterate(g, sig, cr, q, tol=tol, max_iters=2000, phi_out=phi)
+        return g, it
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, build_ms, sweep_ms = 0, 0.0, []
+    for _ in range(args.steps):
+        g, it = step()
+        iters += it
+        tm = g.timing()
+        build_ms += tm["build_ms"]
+        sweep_ms.append(tm["sweep_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    line = {"metric": METRIC, "value": iters * N * M * R / (ms / 1e3), "unit": "cell-angle updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wid == 1 else "f32", "data": "synthetic",
+            "config": {"workload": wl["spec"]["name"], "cells": N, "directions": M, "rhs": R, "tol": tol,
+                       "sweep_mode": args.mode, "si_iterations_per_step": iters / args.steps},
+            "phases_ms": {"dag_build_mean": build_ms / args.steps, "last_sweep_kernel": sweep_ms[-1],
+                          "source_iteration_mean": ms / args.steps - build_ms / args.steps}}
+    print(json.dumps(line), flush=True)
+
+
 def run_sweeps(args):
     """Build the graphs of the workload once, then args.sweeps plain sweeps
     (the launch sequence the per-kernel ncu captures in profiles/ skip into)."""
@@ -797,6 +855,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload in ("wl1", "wl2"):
+        run_small(args)
     else:
         run_gpu(args)
 
