@@ -707,6 +707,7 @@ def run_serve(args):
         served = srv.run(stream(rate))
         clk = clocks.stop()
         l1 = sum(b.stats()[2] for b in be.batches)
+        setup = [b.setup_stats() for b in be.batches]
         s_served = summarize(served, work)
         for _ in range(max(1, args.warmup)):  # the batch path changed the handles' unit tables
             run_one_at_a_time(solo_be, warm_requests(), meshes=resident)
@@ -717,6 +718,8 @@ def run_serve(args):
         by_rate.append(dict(rate_per_s=rate, served=s_served, one_at_a_time=s_alone,
                             p99_ratio_one_at_a_time_over_served=s_alone["p99_s"] / s_served["p99_s"],
                             results_equal_one_at_a_time=bool(same), gpu_launches=int(l1 - l0), clocks=clk,
+                            lane_rebuild_ms_total=[round(x[0], 1) for x in setup],
+                            lane_rebuilds_total=[int(x[1]) for x in setup],
                             peak_budget_used_gb=srv.peak_used / 1e9,
                             h2d_bytes=int(sum((r.sigma_t.size + r.c_ratio.size + r.q.size) * 4 for r in served)),
                             d2h_bytes=int(sum(r.phi.size * 4 for r in served))))

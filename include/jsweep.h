@@ -326,8 +326,10 @@ JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision
  *   jsweep_batch_options: the batch's current options (after
  *     jsweep_batch_autotune: the chosen ones).
  *   jsweep_batch_stats: device time of the last batched sweep launch and of
- *     the whole last iteration, in ms, and the number of kernels the batch
- *     has launched since it was created (pointers may be NULL).
+ *     the whole last iteration, in ms, the number of kernels the batch has
+ *     launched since it was created, and the host time spent (and the number
+ *     of times) rebuilding its merged tables and captured iteration after the
+ *     problem set changed (pointers may be NULL).
  */
 #define JSWEEP_BATCH_MAX_PROBLEMS 65536
 #define JSWEEP_PROBLEM_ACTIVE 0    /* still iterating */
@@ -350,7 +352,7 @@ JSWEEP_API int jsweep_batch_source_iterate(jsweep_batch_t batch, int *iters_out,
                                            void *stream);
 JSWEEP_API int jsweep_batch_autotune(jsweep_batch_t batch, void *stream, double *best_ms);
 JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double *iteration_ms,
-                                  int64_t *launches);
+                                  int64_t *launches, double *setup_ms, int64_t *rebuilds);
 JSWEEP_API int jsweep_batch_options(jsweep_batch_t batch, jsweep_options *out);
 JSWEEP_API int jsweep_batch_destroy(jsweep_batch_t batch);
 

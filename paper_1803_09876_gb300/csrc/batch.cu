@@ -22,6 +22,7 @@
 // lane of the same warp.  The deadlock argument of the single-problem kernel
 // carries over: the merged order is topological for every problem.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -352,6 +353,8 @@ struct Batch {
     int pending_k = 0;
     cudaEvent_t ev_done = nullptr;
     int64_t sweep_nodes = 0;  // sweep launches in one iteration
+    double setup_ms = 0.0;     // host time spent rebuilding tables and capturing graphs
+    int64_t rebuilds = 0;
     ~Batch() {
         cudaDeviceSynchronize();
         if (h_state) cudaFreeHost(h_state);
@@ -671,6 +674,8 @@ template <class T, int R> int launch_t(Batch *b, int n_sweeps, cudaStream_t s) {
     bool any = false;
     for (auto &p : b->probs) any |= p->st.active != 0;
     if (!any) return JSWEEP_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool rebuilt = b->dirty || !b->graph;
     if (b->dirty) JS_TRY((build_tables<T, R>(b, s)));
     if (!b->ev[0])
         for (auto &e : b->ev) JS_CUDA(cudaEventCreate(&e));
@@ -696,6 +701,10 @@ template <class T, int R> int launch_t(Batch *b, int n_sweeps, cudaStream_t s) {
             set_error("batch graph instantiate failed: %s", cudaGetErrorString(e2));
             return JSWEEP_ERR_CUDA;
         }
+    }
+    if (rebuilt) {
+        b->setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        ++b->rebuilds;
     }
     const int K = (int)b->act.size();
     const size_t need = (size_t)K * sizeof(ProbState) + 16;
@@ -1073,7 +1082,8 @@ JSWEEP_API int jsweep_batch_autotune(jsweep_batch_t batch, void *stream, double 
     return JSWEEP_OK;
 }
 
-JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double *iteration_ms, int64_t *launches) {
+JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double *iteration_ms, int64_t *launches,
+                                  double *setup_ms, int64_t *rebuilds) {
     js::clear_error();
     if (!batch) {
         js::set_error("jsweep_batch_stats: NULL");
@@ -1082,6 +1092,8 @@ JSWEEP_API int jsweep_batch_stats(jsweep_batch_t batch, double *sweep_ms, double
     if (sweep_ms) *sweep_ms = bimpl(batch)->sweep_ms;
     if (iteration_ms) *iteration_ms = bimpl(batch)->iter_ms;
     if (launches) *launches = bimpl(batch)->launches;
+    if (setup_ms) *setup_ms = bimpl(batch)->setup_ms;
+    if (rebuilds) *rebuilds = bimpl(batch)->rebuilds;
     return JSWEEP_OK;
 }
 

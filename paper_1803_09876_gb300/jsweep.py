@@ -182,7 +182,7 @@ def load(path: str = LIB_PATH):
             "jsweep_batch_size": (I, [P, P]),
             "jsweep_batch_source_iterate": (I, [P, P, P, P]),
             "jsweep_batch_autotune": (I, [P, P, P]),
-            "jsweep_batch_stats": (I, [P, P, P, P]),
+            "jsweep_batch_stats": (I, [P, P, P, P, P, P]),
             "jsweep_batch_options": (I, [P, P]),
             "jsweep_batch_destroy": (I, [P]),
         }
@@ -569,9 +569,16 @@ class Batch:
         """(sweep launch ms, whole iteration ms) of the last batched iteration
         and the kernels launched by this batch so far."""
         a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-        _check(lib().jsweep_batch_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+        _check(lib().jsweep_batch_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n), None, None),
                "jsweep_batch_stats")
         return a.value, b.value, n.value
+
+    def setup_stats(self):
+        """(host ms spent rebuilding tables and captured iterations, rebuilds) so far."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().jsweep_batch_stats(self._h, None, None, None, ctypes.byref(ms), ctypes.byref(n)),
+               "jsweep_batch_stats")
+        return ms.value, n.value
 
 
 JSWEEP_NOALLOC_SCRATCH_BYTES = 64 << 20

@@ -93,7 +93,7 @@ def test_batch_host_side_errors(lib):
     assert lib.jsweep_batch_step(h, 1, ctypes.byref(n), None) == J.JSWEEP_OK and n.value == 0
     assert lib.jsweep_batch_source_iterate(h, None, None, None) == J.JSWEEP_OK
     a, b, nl = ctypes.c_double(-1), ctypes.c_double(-1), ctypes.c_int64(-1)
-    assert lib.jsweep_batch_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(nl)) == J.JSWEEP_OK
+    assert lib.jsweep_batch_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(nl), None, None) == J.JSWEEP_OK
     assert a.value == 0.0 and nl.value == 0
     assert lib.jsweep_batch_destroy(h) == J.JSWEEP_OK
     assert lib.jsweep_batch_destroy(None) == J.JSWEEP_OK
