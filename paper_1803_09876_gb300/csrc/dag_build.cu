@@ -1,3 +1,4 @@
+#include <cstdlib>
 // Per-direction dependency-graph build on the device (Sec. V-A; Listing 1
 // init/input/compute readiness), with cycle breaking and the level-major
 // reorder.
@@ -1029,12 +1030,44 @@ int build_dags(Dags *d, cudaStream_t s) {
     const int check_every = 8;
     int32_t last_remaining = -1;
     int no_progress_checks = 0;
+    // walks of a direction run in parallel over its candidates; a direction has
+    // up to tens of thousands of them in a step on large meshes
+    const int walk_blocks = (int)std::min<int64_t>(std::max<int64_t>(8, N / (256 * 16)), 64);
+    // JSWEEP_BUILD_PROFILE=1: device time of each kernel of the frontier loop
+    // (events around every launch; printed to stderr at the end of the build)
+    const bool prof = std::getenv("JSWEEP_BUILD_PROFILE") != nullptr;
+    std::vector<cudaEvent_t> pev;
+    double kms[4] = {0, 0, 0, 0};
+    auto prof_mark = [&](int k) {
+        if (!prof) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        pev.push_back(e);
+        (void)k;
+    };
     while (true) {
         int cur = (int)(step & 1);
+        prof_mark(0);
         k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
-        k_walk<<<dim3(8, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
+        prof_mark(1);
+        k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
+        prof_mark(2);
         k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B, d->eager_cap > 0 ? d->eager_cap : B);
+        prof_mark(3);
         k_commit<<<64, 256, 0, s>>>(c, cur ^ 1, cur);
+        prof_mark(4);
+        if (prof && pev.size() >= 500) {  // fold the events of a few steps into the totals
+            cudaStreamSynchronize(s);
+            for (size_t i = 0; i + 4 < pev.size(); i += 5)
+                for (int k = 0; k < 4; ++k) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, pev[i + k], pev[i + k + 1]);
+                    kms[k] += ms;
+                }
+            for (auto e : pev) cudaEventDestroy(e);
+            pev.clear();
+        }
         note_launches(3);  // peel, walk, resolve; the check below counts commit
         JS_LAUNCH_CHECK();
         ++step;
@@ -1061,6 +1094,18 @@ int build_dags(Dags *d, cudaStream_t s) {
         }
     }
 
+    if (prof) {
+        cudaStreamSynchronize(s);
+        for (size_t i = 0; i + 4 < pev.size(); i += 5)
+            for (int k = 0; k < 4; ++k) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, pev[i + k], pev[i + k + 1]);
+                kms[k] += ms;
+            }
+        for (auto e : pev) cudaEventDestroy(e);
+        std::fprintf(stderr, "frontier loop: %lld steps; peel %.1f ms, walk %.1f ms, resolve %.1f ms, commit %.1f ms\n",
+                     (long long)step, kms[0], kms[1], kms[2], kms[3]);
+    }
     JS_CUDA(cudaEventRecord(pe[3], s));
     // ---- levels per direction
     DevBuf lmax;
