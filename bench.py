@@ -66,7 +66,7 @@ def parse():
                         "workload's right-hand sides (no source iteration) and print their times")
     p.add_argument("--problems", type=int, default=256, help="batch: number of problems")
     p.add_argument("--requests", type=int, default=200, help="serve: number of requests")
-    p.add_argument("--rates", default="8,24,48",
+    p.add_argument("--rates", default="8,24,48,96",
                    help="serve: Poisson arrival rates (requests/s), comma-separated; the line's headline is the last")
     p.add_argument("--meshes", type=int, default=24, help="serve: meshes in the catalog")
     p.add_argument("--budget-gb", type=float, default=60.0, help="serve: device-memory budget")

@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import threading
 import time
 from typing import Any, Callable
 
@@ -133,20 +134,24 @@ class Server:
         return True
 
     def _try_admit(self, req, now):
+        """True if admitted; "memory" if it does not fit the budget now; "lane"
+        if its lane already runs as many requests as it may."""
         key = req.mesh_key
         handle = self.meshes.get(key)
         mesh_need = 0 if handle is not None else self.be.mesh_bytes_estimate(key)
         if handle is None:
             if not self._make_room(mesh_need + self.be.request_bytes_estimate(key)):
-                return False
+                return "memory"
             handle, nbytes = self.be.build_mesh(key)
             self.meshes.put(key, handle, nbytes)
+        if hasattr(self.be, "can_admit") and not self.be.can_admit(handle):
+            return "lane"
         need = self.be.request_bytes(handle, req)
         self.meshes.in_use[key] += 1  # pin the mesh while making room for the request
         ok = self._make_room(need)
         if not ok:
             self.meshes.in_use[key] -= 1
-            return False
+            return "memory"
         pid = self.be.add(handle, req)
         self.active[pid] = (req, need)
         self.reserved += need
@@ -205,13 +210,17 @@ class Server:
             while nc < len(cancels) and cancels[nc][0] <= now:
                 self._cancel(cancels[nc][1], waiting, now)
                 nc += 1
-            # admission in arrival order while memory allows
-            while waiting:
-                if not self._try_admit(waiting[0], now):
+            # admission in arrival order: a request whose lane is full lets later
+            # requests of other lanes pass; one that does not fit in memory stops
+            # the scan (so a large request is not starved by small ones)
+            for req in list(waiting):
+                res = self._try_admit(req, now)
+                if res is True:
+                    waiting.remove(req)
+                elif res == "memory":
                     if not self.active:
-                        raise RuntimeError(f"request {waiting[0].rid} does not fit the budget even when idle")
+                        raise RuntimeError(f"request {req.rid} does not fit the budget even when idle")
                     break
-                waiting.popleft()
             if self.active:
                 if hasattr(self.be, "pump"):
                     self.be.pump(self.k)  # returns once some lane has finished an iteration
@@ -276,10 +285,11 @@ class GpuBackend:
     of all lanes but the last).  A small request then iterates at the pace of
     the small requests, not of the largest mesh in the mix; the lanes run
     concurrently on the device (jsweep_batch_launch / jsweep_batch_poll).
+    ``lane_caps`` bounds how many requests a lane runs at once.
     """
 
     def __init__(self, catalog: Callable[[Any], tuple], dtype=None, nrhs=1, tol=1e-6, max_iters=1000,
-                 options=None, batch_options=None, lanes=(3e6, 3e7)):
+                 options=None, batch_options=None, lanes=(3e6, 3e7), lane_caps=(None, 8, 1), solo_last_lane=True):
         import torch
 
         from . import jsweep as J
@@ -293,6 +303,16 @@ class GpuBackend:
         self.options = options
         self.bounds = list(lanes)
         n = len(self.bounds) + 1
+        # requests a lane runs at once (None: no limit): small requests gain most
+        # from sharing iterations; large ones keep the device to themselves and
+        # finish in arrival order instead of all finishing late together
+        self.caps = list(lane_caps) + [None] * max(0, n - len(lane_caps))
+        # the largest requests gain nothing from sharing iterations: the last lane
+        # runs them through jsweep_source_iterate on its own stream, in a worker
+        # thread (the C calls release the interpreter), beside the batched lanes
+        self.solo_lane = n - 1 if solo_last_lane else None
+        self.solo_jobs = {}
+        self._solo_next = 0
         self.batches = [J.Batch(self.dtype, nrhs, batch_options) for _ in range(n)]
         self.streams = [torch.cuda.Stream() for _ in range(n)]
         self.active = [0] * n      # unfinished problems per lane
@@ -304,6 +324,10 @@ class GpuBackend:
     @property
     def batch(self):  # the first lane (kept for single-lane use)
         return self.batches[0]
+
+    def can_admit(self, handle):
+        lane = self.lane_of(handle)
+        return self.caps[lane] is None or self.active[lane] < self.caps[lane]
 
     def lane_of(self, handle):
         work = handle.n_cells * handle.n_dirs
@@ -367,9 +391,33 @@ class GpuBackend:
         q = t.as_tensor(np.ascontiguousarray(req.q), dtype=self.dtype).pin_memory().to(dev, non_blocking=True)
         return sig, c, q
 
+    def _solo_run(self, job, handle, req, stream):
+        torch = self.torch
+        try:
+            with torch.cuda.stream(stream):
+                sig, c, q = self._tensors(req)
+                phi, it, res, ok = self.J.jsweep_source_iterate(handle, sig, c, q, tol=self.tol,
+                                                                max_iters=self.max_iters, stream=stream,
+                                                                allow_not_converged=True)
+                job["result"] = (phi.cpu().numpy(), it, res)
+        except Exception as e:  # reported by result()
+            job["error"] = e
+        job["done"] = True
+
     def add(self, handle, req):
-        sig, c, q = self._tensors(req)
         lane = self.lane_of(handle)
+        if lane == self.solo_lane:
+            pid = ("solo", self._solo_next)
+            self._solo_next += 1
+            job = {"done": False, "result": None, "error": None, "stream": self.streams[lane]}
+            job["thread"] = threading.Thread(target=self._solo_run, args=(job, handle, req, self.streams[lane]),
+                                             daemon=True)
+            self.solo_jobs[pid] = job
+            self.inputs[pid] = req
+            self.active[lane] += 1
+            job["thread"].start()
+            return pid
+        sig, c, q = self._tensors(req)
         pid = (lane, self.batches[lane].add(handle, sig, c, q, tol=self.tol, max_iters=self.max_iters))
         self.inputs[pid] = req
         self.active[lane] += 1
@@ -377,7 +425,7 @@ class GpuBackend:
 
     def step(self, k):
         for lane in range(len(self.batches)):
-            if self.active[lane]:
+            if self.active[lane] and lane != self.solo_lane:
                 self.active[lane] = self.batches[lane].step(k, stream=self.streams[lane])
 
     def pump(self, k, spin_s=20e-6):
@@ -385,7 +433,7 @@ class GpuBackend:
         one lane has finished its queued iterations."""
         while True:
             for lane, b in enumerate(self.batches):
-                if self.active[lane] and not self.pending[lane]:
+                if lane != self.solo_lane and self.active[lane] and not self.pending[lane]:
                     b.launch(k, stream=self.streams[lane])
                     self.pending[lane] = True
             progressed = False
@@ -396,21 +444,39 @@ class GpuBackend:
                         self.pending[lane] = False
                         self.active[lane] = n
                         progressed = True
-            if progressed or not any(self.pending):
+            if any(j["done"] and not j.get("seen") for j in self.solo_jobs.values()):
+                for j in self.solo_jobs.values():
+                    j["seen"] = j["done"]
+                progressed = True
+            if progressed or not (any(self.pending) or self.solo_jobs):
                 return
             time.sleep(spin_s)
 
     def finished(self, pid):
+        if pid in self.solo_jobs:
+            return self.solo_jobs[pid]["done"]
         lane, i = pid
         return self.batches[lane].query(i)[0] != self.J.JSWEEP_PROBLEM_ACTIVE
 
     def result(self, pid):
+        if pid in self.solo_jobs:
+            job = self.solo_jobs[pid]
+            job["thread"].join()
+            if job["error"] is not None:
+                raise job["error"]
+            return job["result"]
         lane, i = pid
         st, it, res = self.batches[lane].query(i)
         phi = self.batches[lane].phi(i).cpu().numpy()  # written by the lane's finished iteration
         return phi, it, res
 
     def remove(self, pid):
+        if pid in self.solo_jobs:
+            job = self.solo_jobs.pop(pid)
+            job["thread"].join()  # a cancelled solve runs to its end; its result is dropped
+            self.active[self.solo_lane] -= 1
+            self.inputs.pop(pid, None)
+            return
         lane, i = pid
         if self.pending[lane]:
             done, n = self.batches[lane].poll(wait=True)

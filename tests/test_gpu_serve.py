@@ -34,13 +34,16 @@ def inputs_for(key, seed):
     return rng.uniform(0.5, 2.0, N), np.full(N, 0.5), rng.uniform(0.0, 1.0, (1, N))
 
 
-def test_served_results_equal_alone_within_budget():
+@pytest.mark.parametrize("lanes", [(3e6, 3e7), (1e4, 1e5)], ids=["one_lane", "three_lanes_with_solo"])
+def test_served_results_equal_alone_within_budget(lanes):
+    # with bounds (1e4, 1e5) the three stream meshes fall in three lanes, the
+    # largest (tet6, 128 directions) in the solo lane
     import torch
     from paper_1803_09876_gb300.serve import GpuBackend, Server, poisson_stream, run_one_at_a_time, summarize
 
     J()
     reqs = poisson_stream(14, 400.0, STREAM_KEYS, inputs_for, seed=5000)
-    be = GpuBackend(catalog, dtype=torch.float32, tol=1e-6, max_iters=500)
+    be = GpuBackend(catalog, dtype=torch.float32, tol=1e-6, max_iters=500, lanes=lanes)
     budget = 256 << 20
     srv = Server(be, budget, sweeps_per_step=1)
     torch.cuda.synchronize()

@@ -237,3 +237,24 @@ def test_cancelled_requests_free_their_memory_and_others_finish():
     assert by[3].cancelled and ("cancel", 3) in kinds
     s = summarize(out, lambda r: 1.0)
     assert s["requests"] == 2 and s["cancelled"] == 2
+
+
+def test_lane_caps_let_other_lanes_pass_and_keep_order_within_a_lane():
+    clk = Clock()
+
+    class LaneBackend(FakeBackend):
+        # lane = mesh key; lane 2 runs one request at a time
+        def can_admit(self, h):
+            return h[1] != 2 or sum(1 for p in self.probs.values() if p["h"][1] == 2 and p["it"] < p["target"]) < 1
+
+    be = LaneBackend(clk, budget=10_000)
+    reqs = [_req(0, 0.0, 2, 30), _req(1, 0.0, 2, 30), _req(2, 0.0, 1, 5), _req(3, 0.0, 2, 30)]
+    srv = Server(be, 10_000, clock=clk, sleep=clk.sleep)
+    srv.run(reqs)
+    admit = {rid: t for t, k, rid in srv.events if k == "admit"}
+    done = {rid: t for t, k, rid in srv.events if k == "done"}
+    # the small request passes the queued large ones; large ones run one at a time, in order
+    assert admit[2] == admit[0]
+    assert admit[1] >= done[0] and admit[3] >= done[1]
+    order = [rid for _, k, rid in srv.events if k == "admit" and rid != 2]
+    assert order == [0, 1, 3]
