@@ -37,8 +37,9 @@ if ROOT not in sys.path:
 METRIC = "cell-angle updates/s"
 # DRAM bytes (read + write) of one sweep of the dominant kernel, from the full-sweep ncu capture
 # summarised in profiles/k_sweep_level_hex128_full_sweep_dram.md; keyed by
-# (hex edge, sweep mode, priority, cluster cells, layering); valid while the kernel is unchanged
-SWEEP_TRAFFIC_BYTES = {(128, 1, 0, 32, 0): 1.615e11}
+# (hex edge, sweep mode, priority, cluster cells, layering, face stream); valid while the kernel is
+# unchanged (none yet for the current kernels)
+SWEEP_TRAFFIC_BYTES = {}
 UNIT = "cell-angle-rhs updates/s"
 WORKLOAD = "hex128_jitter0.15_288dirs_8rhs_fp32_si_tol1e-6"
 
@@ -54,6 +55,8 @@ def parse():
     p.add_argument("--priority", type=int, default=0)
     p.add_argument("--layering", type=int, default=0, help="0 octant-aligned layers, 1 longest-path levels")
     p.add_argument("--cluster", type=int, default=32)
+    p.add_argument("--no-face-stream", action="store_true",
+                   help="level-synchronous sweeps read the cell geometry instead of the precomputed face stream")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve", "wl1", "wl2"],
@@ -227,7 +230,7 @@ def run_gpu(args):
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
     opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
-                                   layering=args.layering)
+                                   layering=args.layering, no_face_stream=int(args.no_face_stream))
     dev = torch.device("cuda", local)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device=dev)
     cr = torch.as_tensor(wl["c_ratio"], dtype=torch.float32, device=dev)
@@ -295,11 +298,14 @@ def run_gpu(args):
     achieved = alg_bytes / ((sw_ms + ph_ms) / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic = SWEEP_TRAFFIC_BYTES.get((args.n, args.mode, args.priority, args.cluster, args.layering))
+    traffic = SWEEP_TRAFFIC_BYTES.get((args.n, args.mode, args.priority, args.cluster, args.layering,
+                                       int(not args.no_face_stream)))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
             "traffic_unit": "bytes per sweep (one launch sequence of the CUDA graph)",
-            "kernel": ("sweep (level-synchronous CUDA graph)" if args.mode == 1 else "sweep (data-driven persistent)")
+            "kernel": (("sweep (level-synchronous CUDA graph, "
+                        + ("geometry reads)" if args.no_face_stream else "face-coefficient stream)"))
+                       if args.mode == 1 else "sweep (data-driven persistent)")
                       + " + phi reduction, one sweep of all directions",
             "alg_bytes_per_cell_dir": B, "sweep_ms": sw_ms, "phi_ms": ph_ms,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
@@ -830,7 +836,7 @@ def run_sweeps(args):
     dirs, w = J.jsweep_quadrature_product(*wl["spec"]["quad"])
     M = len(dirs)
     opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
-                                   layering=args.layering)
+                                   layering=args.layering, no_face_stream=int(args.no_face_stream))
     dags = J.jsweep_build_dags(J.mesh_from_dict(wl), J.jsweep_quadrature_create(dirs, w), opt)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device="cuda")
     src = torch.as_tensor(wl["q"] / (4 * math.pi), dtype=torch.float32, device="cuda").contiguous()

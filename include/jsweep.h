@@ -134,7 +134,12 @@ typedef struct {
                               64, at most cycle_search_max); a stalled direction searches up to
                               cycle_search_max, and a build that cannot break a cycle this way is
                               repeated once with cycle_search_max everywhere.  Lags do not depend on it. */
-    int reserved[2];
+    int no_face_stream;    /* level-synchronous sweeps: 0 (default) reads each direction's face coefficients
+                              (Omega.A per face and the upwind neighbours, one record per cell-direction in
+                              sweep order, built at the handle's first such sweep: N x M x 32..96 bytes) as
+                              a sequential stream; nonzero computes them from the cell geometry in the
+                              sweep.  Results are bit-identical either way. */
+    int reserved[1];
 } jsweep_options;
 
 /* Fill *opt with defaults. */

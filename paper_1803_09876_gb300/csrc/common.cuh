@@ -186,6 +186,12 @@ struct Dags {
     DevBuf flags;    // int32 [N][M]: sweep epoch at which (cell, direction) was last written
     int epoch = 0;
     DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
+    // face-coefficient stream of the level-synchronous sweep (see coef_record_bytes)
+    DevBuf coef;
+    int coef_prec = -1, coef_maxf = 0;
+    const int32_t *coef_order = nullptr;  // the order and directions it was built for
+    const void *coef_dirs = nullptr;
+    bool coef_failed = false;             // allocation refused once: compute coefficients in the sweep
     UnitTable ut;
     std::unique_ptr<PatchSched> ps;  // lazily built (patch programs)
     // CUDA graph of the level-synchronous sweep

@@ -633,7 +633,7 @@ __device__ __forceinline__ int solve_cell_staged(const SweepArgs<T> &a, int m, i
     }
 #pragma unroll
     for (int k = 0; k < MAXF; ++k) {
-        const T d = ox * gk[k].x + oy * gk[k].y + oz * gk[k].z;
+        const T d = face_dot(ox, oy, oz, gk[k].x, gk[k].y, gk[k].z);
         if ((msk >> k) & 1u) {
             const T wf = fabs(d);
             const int nb = nbr_bits<T>(gk[k]);
@@ -651,7 +651,7 @@ __device__ __forceinline__ int solve_cell_staged(const SweepArgs<T> &a, int m, i
                     up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
             }
 #pragma unroll
-            for (int r = 0; r < RH; ++r) num[r] = num[r] + wf * up[r];
+            for (int r = 0; r < RH; ++r) num[r] = fma_rn(wf, up[r], num[r]);
         } else {
             den += d > T(0) ? d : T(0);
         }

@@ -53,6 +53,61 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T
     }
 }
 
+// Level-synchronous sweep reading the precomputed face coefficients.
+template <class T, int R, int SPLIT, int MAXF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sweep_level_coef(SweepArgs<T> a, int64_t u0, int64_t nu, const unsigned char *coef) {
+    pdl_launch_next();
+    constexpr int RB = coef_record_bytes<T, MAXF>();
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (t >= nu) return;
+    const int4 u = a.units[u0 + t];
+    const int cell = lane / SPLIT, sub = lane % SPLIT;
+    if (cell < u.z) {
+        const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
+        solve_cell_coef<T, R, SPLIT, MAXF>(a, u.x, __ldg(a.order + idx), __ldg(a.mask + idx), sub,
+                                           coef + idx * RB);
+    }
+}
+
+// Face-coefficient records of every (direction, position) of the sweep order.
+template <class T, int MAXF>
+__global__ void k_coef_fill(const int32_t *order, const typename V4<T>::type *geo, const T *dirs, int64_t N,
+                            int64_t M, int FS, int GS, unsigned char *coef) {
+    constexpr int RB = coef_record_bytes<T, MAXF>();
+    const int64_t total = N * M;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i / N;
+        const int32_t c = order[i];
+        const T ox = dirs[4 * m], oy = dirs[4 * m + 1], oz = dirs[4 * m + 2];
+        alignas(16) unsigned char rec[RB];
+        T dk[MAXF];
+        int32_t nbk[MAXF];
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            if (k < FS) {
+                const typename V4<T>::type g = geo[(int64_t)c * GS + k];
+                dk[k] = face_dot(ox, oy, oz, g.x, g.y, g.z);
+                nbk[k] = nbr_bits<T>(g);
+            } else {
+                dk[k] = T(0);
+                nbk[k] = INT32_MIN;
+            }
+        }
+        memset(rec, 0, RB);
+        memcpy(rec, dk, MAXF * sizeof(T));
+        memcpy(rec + MAXF * sizeof(T), nbk, MAXF * 4);
+        float4 *dst = reinterpret_cast<float4 *>(coef + i * RB);
+#pragma unroll
+        for (int w = 0; w < RB / 16; ++w) {
+            float4 v;
+            memcpy(&v, rec + 16 * w, 16);
+            dst[w] = v;
+        }
+    }
+}
+
 // Data-driven sweep (Listing 1's readiness, per cell): units are taken in
 // schedule order, unit t by resident warp t mod W; each cell waits only for
 // its own upwind cells' flags, then publishes its psi and its flag with
@@ -673,7 +728,7 @@ template <class T, int R> int64_t patch_warps(const Dags *d, int mode) {
 }
 
 template <class T, int R, int SPLIT, int MAXF>
-void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs) {
+void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsigned char *coef) {
     const auto &sp = d->ut.slot_ptr;
     bool first = true;
     for (size_t l = 0; l + 1 < sp.size(); ++l) {
@@ -693,18 +748,60 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs) {
         cfg.numAttrs = first ? 0 : 1;
         first = false;
         int64_t u0 = sp[l];
-        cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
+        if (coef) cudaLaunchKernelEx(&cfg, k_sweep_level_coef<T, R, SPLIT, MAXF>, a, u0, nu, coef);
+        else cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
     }
+}
+
+// The face-coefficient stream of the handle for precision T (built once per
+// handle and sweep order), or nullptr when it is switched off or its
+// allocation was refused (the sweep then reads the cell geometry).
+template <class T> const unsigned char *ensure_coef(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
+    if (d->opt.no_face_stream || d->coef_failed) return nullptr;
+    const int maxf = a.FS <= 4 ? 4 : a.FS <= 6 ? 6 : 7;
+    const int prec = sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32;
+    if (d->coef.p && d->coef_prec == prec && d->coef_maxf == maxf && d->coef_order == d->s_order &&
+        d->coef_dirs == (const void *)a.dirs)
+        return d->coef.as<unsigned char>();
+    const int rb = maxf == 4 ? coef_record_bytes<T, 4>() : maxf == 6 ? coef_record_bytes<T, 6>()
+                                                                     : coef_record_bytes<T, 7>();
+    if (d->coef.alloc((size_t)d->N * d->M * rb, s) != JSWEEP_OK) {
+        clear_error();
+        d->coef_failed = true;
+        return nullptr;
+    }
+    const int grid = grid_for(d->N * d->M, 256, 152 * 64);
+    if (maxf == 4)
+        k_coef_fill<T, 4><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS,
+                                               d->coef.as<unsigned char>());
+    else if (maxf == 6)
+        k_coef_fill<T, 6><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS,
+                                               d->coef.as<unsigned char>());
+    else
+        k_coef_fill<T, 7><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS,
+                                               d->coef.as<unsigned char>());
+    if (cudaGetLastError() != cudaSuccess) {
+        d->coef.release();
+        d->coef_failed = true;
+        return nullptr;
+    }
+    note_launches(1);
+    d->coef_prec = prec;
+    d->coef_maxf = maxf;
+    d->coef_order = d->s_order;
+    d->coef_dirs = a.dirs;
+    return d->coef.as<unsigned char>();
 }
 
 template <class T, int R>
 int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
     constexpr int SPLIT = split_of<T, R>();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
+        const unsigned char *coef = ensure_coef<T>(d, a, s);
         char key[512];
-        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld", (int)sizeof(T), R, (const void *)a.srcv,
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p", (int)sizeof(T), R, (const void *)a.srcv,
                  (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
-                 (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units);
+                 (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units, (const void *)coef);
         if (!d->graph || d->graph_key != key) {
             if (d->graph) {
                 cudaGraphExecDestroy(d->graph);
@@ -713,9 +810,9 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
             if (!d->capture_stream) JS_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
             cudaStream_t cs = d->capture_stream;
             JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            if (a.FS <= 4) capture_levels<T, R, SPLIT, 4>(d, a, cs);
-            else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6>(d, a, cs);
-            else capture_levels<T, R, SPLIT, 7>(d, a, cs);
+            if (a.FS <= 4) capture_levels<T, R, SPLIT, 4>(d, a, cs, coef);
+            else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6>(d, a, cs, coef);
+            else capture_levels<T, R, SPLIT, 7>(d, a, cs, coef);
             cudaGraph_t g;
             cudaError_t e = cudaStreamEndCapture(cs, &g);
             if (e != cudaSuccess) {

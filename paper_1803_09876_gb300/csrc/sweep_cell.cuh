@@ -115,6 +115,19 @@ __device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *
 // record is 8, 16, 32 or 64 bytes (FP32) and one DRAM transaction brings both.
 template <int R> constexpr int src_stride() { return R >= 4 ? 2 * R : (R == 2 ? 4 : 2); }
 
+// Omega . A of one face, rounded the same way in every kernel (explicit
+// round-to-nearest operations, no contraction), so that the per-cell solve and
+// the precomputed coefficient stream give bit-identical results.
+__device__ __forceinline__ float face_dot(float ox, float oy, float oz, float ax, float ay, float az) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(ox, ax), __fmul_rn(oy, ay)), __fmul_rn(oz, az));
+}
+__device__ __forceinline__ double face_dot(double ox, double oy, double oz, double ax, double ay, double az) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(ox, ax), __dmul_rn(oy, ay)), __dmul_rn(oz, az));
+}
+
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -197,7 +210,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
     }
 #pragma unroll
     for (int k = 0; k < MAXF; ++k) {
-        const T d = ox * gk[k].x + oy * gk[k].y + oz * gk[k].z;
+        const T d = face_dot(ox, oy, oz, gk[k].x, gk[k].y, gk[k].z);
         if ((msk >> k) & 1u) {
             const T wf = fabs(d);
             const int nb = nbr_bits<T>(gk[k]);
@@ -215,7 +228,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
                     up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
             }
 #pragma unroll
-            for (int r = 0; r < RH; ++r) num[r] = num[r] + wf * up[r];
+            for (int r = 0; r < RH; ++r) num[r] = fma_rn(wf, up[r], num[r]);
         } else {
             den += d > T(0) ? d : T(0);
         }
@@ -225,6 +238,81 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
     for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
     store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
     return true;
+}
+
+// ---- precomputed face coefficients (level-synchronous sweeps) ---------------------
+// Record of one (direction, position) in the sweep order: Omega.A of every
+// face slot (face_dot, T) then the slot's neighbour bits (int32), padded to
+// 16 bytes.  The sweep then reads one sequential record per cell-direction
+// instead of the cell's scattered geometry record.
+template <class T, int MAXF> constexpr int coef_record_bytes() {
+    return (MAXF * (int)sizeof(T) + MAXF * 4 + 15) / 16 * 16;
+}
+
+// The per-cell solve of solve_cell with the coefficients from the record
+// (same operations in the same order, so results are bit-identical).
+template <class T, int R, int SPLIT, int MAXF>
+__device__ __forceinline__ void solve_cell_coef(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
+                                                const unsigned char *rec) {
+    constexpr int RH = R / SPLIT;
+    constexpr int RB = coef_record_bytes<T, MAXF>();
+    T dk[MAXF];
+    int nbk[MAXF];
+    {
+        float4 w[RB / 16];
+#pragma unroll
+        for (int i = 0; i < RB / 16; ++i) w[i] = __ldg(reinterpret_cast<const float4 *>(rec) + i);
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(w);
+        memcpy(dk, b, MAXF * sizeof(T));
+        memcpy(nbk, b + MAXF * sizeof(T), MAXF * 4);
+    }
+    constexpr int RS = src_stride<R>();
+    T num[RH];
+    load_ro<T, RH>(a.srcv + (int64_t)c * RS + sub * RH, num);
+    T den = __ldg(a.srcv + (int64_t)c * RS + R);
+    unsigned lagk = 0;
+    int lagj[MAXF];
+    if (msk & 0x80u) {
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            lagj[k] = -1;
+            if (((msk >> k) & 1u) && nbk[k] >= 0) {
+                int j = lag_index(a.lag_ptr, a.lag_face, m, a.sface[(int64_t)c * a.FS + k] >> 1);
+                lagj[k] = j;
+                if (j >= 0) lagk |= 1u << k;
+            }
+        }
+    }
+    pdl_wait_prev();  // upwind values come from earlier slots
+#pragma unroll
+    for (int k = 0; k < MAXF; ++k) {
+        const T d = dk[k];
+        if ((msk >> k) & 1u) {
+            const T wf = fabs(d);
+            const int nb = nbk[k];
+            T up[RH];
+            if (nb >= 0) {
+                if ((lagk >> k) & 1u) {
+                    load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
+                } else {
+                    load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
+                }
+            } else {
+                const int b = -nb - 1;
+#pragma unroll
+                for (int r = 0; r < RH; ++r)
+                    up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
+            }
+#pragma unroll
+            for (int r = 0; r < RH; ++r) num[r] = fma_rn(wf, up[r], num[r]);
+        } else {
+            den += d > T(0) ? d : T(0);
+        }
+    }
+    T out[RH];
+#pragma unroll
+    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
+    store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
 }
 
 // phi[r][c] = sum_m w_m psi[c][m][r]: one warp per cell reads the cell's

@@ -87,7 +87,8 @@ class jsweep_options(ctypes.Structure):
         ("unit_order", ctypes.c_int),
         ("patch_cells", ctypes.c_int),
         ("eager_search_max", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("no_face_stream", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 

@@ -329,19 +329,45 @@ class GpuBackend:
         lane = self.lane_of(handle)
         return self.caps[lane] is None or self.active[lane] < self.caps[lane]
 
-    def lane_of(self, handle):
-        work = handle.n_cells * handle.n_dirs
+    def _lane_of_work(self, work):
         for i, b in enumerate(self.bounds):
             if work < b:
                 return i
         return len(self.bounds)
 
+    def lane_of(self, handle):
+        return self._lane_of_work(handle.n_cells * handle.n_dirs)
+
     # sizes
     def _shape(self, key):
         if key not in self._est:
             mesh, dirs, _ = self.catalog(key)
-            self._est[key] = (mesh["n_cells"], mesh["n_faces"], len(dirs), mesh.get("n_bfaces", 0))
+            fc = np.asarray(mesh["face_cells"]).ravel()
+            fs = int(np.bincount(fc[fc >= 0]).max()) if fc.size else 1
+            self._est[key] = (mesh["n_cells"], mesh["n_faces"], len(dirs), mesh.get("n_bfaces", 0), fs)
         return self._est[key]
+
+    def _rhs_padded(self):
+        return 1 if self.nrhs <= 1 else 2 if self.nrhs <= 2 else 4 if self.nrhs <= 4 else 8
+
+    def resident_extra_bytes(self, key):
+        """Device bytes a mesh's handle allocates at its first solve and keeps
+        until it is released, reserved with the mesh: its own unit table (one
+        16-byte unit per 8 or more (direction, cell) pairs), and for a mesh of
+        the solo lane the sweep state of jsweep_source_iterate (psi, sources,
+        inflow, phi, lagged psi, and the face-coefficient stream of 32 to 96
+        bytes per pair)."""
+        N, F, M, Fb, FS = self._shape(key)
+        extra = 2 * M * N
+        if self.solo_lane is not None and self._lane_of_work(N * M) == self.solo_lane:
+            es = 8 if self.dtype == self.torch.float64 else 4
+            R = self._rhs_padded()
+            RS = 2 * R if R >= 4 else (4 if R == 2 else 2)
+            maxf = 4 if FS <= 4 else 6 if FS <= 6 else 7
+            rb = -(-(maxf * es + maxf * 4) // 16) * 16
+            extra += (M * N * (R * es + rb) + N * (RS + 2 * self.nrhs) * es + (max(Fb, 1) + F) * R * es
+                      + (M + 8) * 8 + (1 << 20))
+        return extra
 
     def mesh_bytes_estimate(self, key):
         """Device bytes of a mesh and its graphs while they are being built
@@ -350,16 +376,16 @@ class GpuBackend:
         buffers; 92 bytes per pair measured on a 82,944-tet, 128-direction
         mesh, 16.5 bytes of which stay resident) and the per-cell and
         per-face mesh arrays."""
-        N, F, M, _ = self._shape(key)
-        return 104 * M * N + 256 * N + 64 * F + (64 << 20)
+        N, F, M, _, _ = self._shape(key)
+        return 104 * M * N + 256 * N + 64 * F + (64 << 20) + self.resident_extra_bytes(key)
 
     def request_bytes_estimate(self, key):
         """Batch workspaces, inputs and output, and the request's share of the
         merged unit table (at most one 20-byte unit per 8 (direction, cell)
         pairs, plus the handle's own table)."""
-        N, F, M, _ = self._shape(key)
+        N, F, M, _, _ = self._shape(key)
         es = 8 if self.dtype == self.torch.float64 else 4
-        R = 1 if self.nrhs <= 1 else 2 if self.nrhs <= 2 else 4 if self.nrhs <= 4 else 8
+        R = self._rhs_padded()
         return M * N * (R * es + 4 + 5) + N * (2 * R + 3 * self.nrhs + 4) * es + F * R * es + (1 << 20)
 
     def build_mesh(self, key):
@@ -372,7 +398,7 @@ class GpuBackend:
         g = self.J.jsweep_build_dags(m, qd, self.options)
         torch.cuda.synchronize()
         self.builds += 1
-        return g, torch.cuda.memory_allocated() - before
+        return g, torch.cuda.memory_allocated() - before + self.resident_extra_bytes(key)
 
     def release_mesh(self, handle):
         del handle  # the handle's destructor releases it (batch problems hold their own reference)
@@ -380,8 +406,11 @@ class GpuBackend:
     def request_bytes(self, handle, req):
         es = 8 if self.dtype == self.torch.float64 else 4
         io = (2 * handle.n_cells + 2 * req.q.size) * es  # sigma_t, c, q, phi_out
-        tables = 5 * handle.n_dirs * handle.n_cells  # merged and per-handle unit tables
-        return self.batches[self.lane_of(handle)].problem_bytes(handle) + io + tables
+        lane = self.lane_of(handle)
+        if lane == self.solo_lane:
+            return io  # the sweep state stays on the handle, reserved with the mesh
+        tables = 3 * handle.n_dirs * handle.n_cells  # the request's share of the merged unit table
+        return self.batches[lane].problem_bytes(handle) + io + tables
 
     def _tensors(self, req):
         t = self.torch

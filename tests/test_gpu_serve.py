@@ -87,5 +87,28 @@ def test_mesh_memory_estimate_bounds_the_build_peak():
         g, nbytes = be.build_mesh(key)
         torch.cuda.synchronize()
         peak = torch.cuda.max_memory_allocated() - base
-        assert 0 < nbytes <= peak <= be.mesh_bytes_estimate(key), (key, nbytes, peak, be.mesh_bytes_estimate(key))
+        built = nbytes - be.resident_extra_bytes(key)  # the reservation for state of the first solve
+        assert 0 < built <= peak <= be.mesh_bytes_estimate(key), (key, built, peak, be.mesh_bytes_estimate(key))
         del g
+
+
+def test_solo_lane_state_stays_within_the_mesh_reservation():
+    # a solo-lane request leaves its sweep state (psi, the face stream) on the
+    # mesh's handle; the reservation made with the mesh covers it
+    import torch
+    from paper_1803_09876_gb300.serve import GpuBackend, Request
+
+    J()
+    be = GpuBackend(catalog, dtype=torch.float32, tol=1e-6, max_iters=50, lanes=(1e4, 1e5))
+    key = "tet24_128"
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    g, nbytes = be.build_mesh(key)
+    assert be.lane_of(g) == be.solo_lane
+    sig, c, q = inputs_for(key, 7)
+    r = Request(rid=0, arrival=0.0, mesh_key=key, sigma_t=sig, c_ratio=c, q=q)
+    for _ in range(2):
+        be.solve_alone(g, r)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() - base <= nbytes
+    assert be.request_bytes(g, r) < be.resident_extra_bytes(key)

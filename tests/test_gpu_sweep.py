@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from inputs import column_mesh, hex_grid, kuhn_tets, make_workload
+from inputs import column_mesh, hex_grid, kuhn_tets, make_workload, pinwheel_mesh
 from _gpu import J, TOL_F32, TOL_F64, build, rel_err, set_opts, tensor
 
 pytestmark = pytest.mark.gpu
@@ -306,3 +306,60 @@ def test_patch_programs_source_iteration_fp32_matches_oracle(patch_cells):
                                                     tensor(q, torch.float32), tol=1e-6, max_iters=500)
         assert ok
         assert rel_err(phi.cpu().numpy(), ref) < 5 * TOL_F32
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_face_stream_and_every_schedule_give_the_same_bits(prec):
+    # each cell-direction is solved by the same operations in every kernel (the
+    # face coefficients Omega.A and the upwind sums are explicitly rounded), so
+    # the precomputed face stream, the geometry reads and the data-driven and
+    # patch-program schedules agree bit for bit, lagged faces included
+    torch = _torch()
+    dt = torch.float32 if prec == "f32" else torch.float64
+    for mesh, quad, R in ((hex_grid(6, 0.3, 3), (6, 6), 1), (kuhn_tets(6, 0.2, 4), (4, 4), 3),
+                          (column_mesh(40), (4, 4), 8), (pinwheel_mesh(), (6, 6), 2)):
+        dirs, w = oracle.product_quadrature(*quad)
+        N = mesh["n_cells"]
+        rng = np.random.default_rng(21)
+        sig = rng.lognormal(0.0, 1.0, N)
+        srcs = [rng.uniform(0.0, 1.0, (R, N)) for _ in range(2)]
+        outs = []
+        for opts in (dict(sweep_mode=1), dict(sweep_mode=1, no_face_stream=1), dict(sweep_mode=2),
+                     dict(sweep_mode=3, patch_cells=64)):
+            g = build(mesh, dirs, w, **opts)
+            outs.append([J().jsweep_sweep(g, tensor(sig, dt), tensor(s, dt)).cpu() for s in srcs])
+        for o in outs[1:]:
+            for a, b in zip(outs[0], o):
+                assert torch.equal(a, b)
+
+
+def test_face_stream_refused_falls_back_to_geometry_reads():
+    import torch
+    js = J()
+    mesh = kuhn_tets(6, 0.2, 4)
+    dirs, w = oracle.product_quadrature(4, 4)
+    N, M = mesh["n_cells"], len(dirs)
+    # FP32 tetrahedra: four Omega.A values and four neighbour ids, 32 bytes per
+    # record; the library rounds allocations up to 256 bytes
+    stream_bytes = (N * M * 32 + 255) // 256 * 256
+    g = build(mesh, dirs, w)
+    rng = np.random.default_rng(22)
+    sig, src = rng.uniform(0.5, 2.0, N), rng.uniform(0.0, 1.0, (1, N))
+    ref = J().jsweep_sweep(build(mesh, dirs, w, no_face_stream=1), tensor(sig, torch.float32),
+                           tensor(src, torch.float32)).cpu()
+
+    def _alloc(nbytes, stream, ctx):
+        if nbytes == stream_bytes:
+            return None
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      torch.cuda.current_stream()))
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    js.set_allocator(js._ALLOC_FN(_alloc), js._FREE_FN(_free))
+    try:
+        phi = js.jsweep_sweep(g, tensor(sig, torch.float32), tensor(src, torch.float32)).cpu()
+    finally:
+        js.use_torch_allocator()
+    assert torch.equal(phi, ref)
