@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--cluster", type=int, default=32)
     p.add_argument("--no-face-stream", action="store_true",
                    help="level-synchronous sweeps read the cell geometry instead of the precomputed face stream")
+    p.add_argument("--tail-units", type=int, default=0,
+                   help="level-synchronous sweeps: slots with fewer units run in one persistent launch "
+                        "(0 = none, the default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve", "wl1", "wl2"],
@@ -230,7 +233,8 @@ def run_gpu(args):
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
     opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
-                                   layering=args.layering, no_face_stream=int(args.no_face_stream))
+                                   layering=args.layering, no_face_stream=int(args.no_face_stream),
+                                   tail_units=args.tail_units)
     dev = torch.device("cuda", local)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device=dev)
     cr = torch.as_tensor(wl["c_ratio"], dtype=torch.float32, device=dev)
@@ -782,7 +786,8 @@ def run_small(args):
     M = len(dirs)
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
-    opt = J.jsweep_options_default(sweep_mode=args.mode)
+    opt = J.jsweep_options_default(sweep_mode=args.mode, no_face_stream=int(args.no_face_stream),
+                                   tail_units=args.tail_units)
     sig = torch.as_tensor(wl["sigma_t"], dtype=dtype, device="cuda")
     cr = torch.as_tensor(wl["c_ratio"], dtype=dtype, device="cuda")
     q = torch.as_tensor(wl["q"], dtype=dtype, device="cuda").contiguous()
@@ -836,7 +841,8 @@ def run_sweeps(args):
     dirs, w = J.jsweep_quadrature_product(*wl["spec"]["quad"])
     M = len(dirs)
     opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
-                                   layering=args.layering, no_face_stream=int(args.no_face_stream))
+                                   layering=args.layering, no_face_stream=int(args.no_face_stream),
+                                   tail_units=args.tail_units)
     dags = J.jsweep_build_dags(J.mesh_from_dict(wl), J.jsweep_quadrature_create(dirs, w), opt)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device="cuda")
     src = torch.as_tensor(wl["q"] / (4 * math.pi), dtype=torch.float32, device="cuda").contiguous()

@@ -139,6 +139,12 @@ typedef struct {
                               sweep order, built at the handle's first such sweep: N x M x 32..96 bytes) as
                               a sequential stream; nonzero computes them from the cell geometry in the
                               sweep.  Results are bit-identical either way. */
+    int tail_units;        /* level-synchronous sweeps with the face stream: > 0 runs the last slots that
+                              each hold fewer than this many work units as one persistent launch (the
+                              tail: warps take units in slot order, per-direction completion counters and
+                              bounded waits replace the launch boundaries) instead of one launch per
+                              slot; 0 (default) = no tail.  Results are bit-identical.  Measured slower
+                              than per-slot launches on every workload tried; kept as an option. */
     int reserved[1];
 } jsweep_options;
 
@@ -295,10 +301,16 @@ JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision
  *
  *   jsweep_batch_create: precision and nrhs shared by the batch's problems;
  *     opt (may be NULL) sets cluster_cells, angles_per_warp, unit_order,
- *     priority, spin_timeout_s and debug_block_waits of the batched launch.
+ *     priority, spin_timeout_s, debug_block_waits and no_face_stream of the
+ *     batched launch.  A level-synchronous batch whose problems all have one
+ *     face-slot count reads each handle's face-coefficient stream (built at the
+ *     first step that needs it, kept with the handle and shared by every
+ *     problem and sweep on it: N x M x 32..96 bytes); otherwise it reads the
+ *     cell geometry.  Results are bit-identical either way.
  *   jsweep_batch_problem_bytes: device bytes that jsweep_batch_add will
  *     allocate for a problem on this handle (its workspaces: psi, epoch flags,
- *     source records, lagged values, two phi buffers, inflow copy).
+ *     source records, lagged values, two phi buffers, inflow copy; not the
+ *     handle's face-coefficient stream).
  *   jsweep_batch_add: a built handle and the problem's device arrays, laid out
  *     as for jsweep_source_iterate (sigma_t, c_ratio [N], q [nrhs][N], inflow
  *     [nrhs][n_bfaces] or NULL, phi_out [nrhs][N]); they must stay valid until

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace js {
@@ -84,6 +86,19 @@ int device_sm_count() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
+}
+
+// SM clock (kHz) of the current device, queried once per device: the query is
+// slow enough to show between the events of a short sweep.
+int device_clock_khz() {
+    static std::atomic<int> cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 2000000;
+    int khz = dev < 64 ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (khz > 0) return khz;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) khz = 2000000;
+    if (dev < 64) cache[dev].store(khz, std::memory_order_relaxed);
+    return khz;
 }
 
 void mesh_release(Mesh *m) {
@@ -496,6 +511,7 @@ int check_options(const jsweep_options *opt, jsweep_options *o) {
     }
     if (opt->eager_search_max > 0) o->eager_search_max = opt->eager_search_max;
     o->no_face_stream = opt->no_face_stream ? 1 : 0;
+    o->tail_units = opt->tail_units;
     if (opt->angles_per_warp != 0 && opt->angles_per_warp != 1 && opt->angles_per_warp != 2 &&
         opt->angles_per_warp != 4) {
         set_error("jsweep_options.angles_per_warp=%d (1, 2 or 4)", opt->angles_per_warp);

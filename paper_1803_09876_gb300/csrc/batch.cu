@@ -54,6 +54,7 @@ static_assert(sizeof(ProbState) == 32, "ProbState layout");
 template <class T> struct ProbArgs {
     SweepArgs<T> a;
     int *flags;  // [N][M] epoch stamps, cell-major like psi
+    const unsigned char *coef;  // the handle's face-coefficient stream (level-synchronous), or null
     const T *sig, *cr, *q, *vol, *w;
     T *phi[2];
     T *phi_out;  // the caller's output array
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
 // Level-synchronous batched sweep: one launch per merged schedule slot; the
 // units of a slot are independent, so no waits and no flags.
-template <class T, int R, int SPLIT, int MAXF, int A>
+template <class T, int R, int SPLIT, int MAXF, int A, bool COEF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sweep_level_batch(const ProbArgs<T> *__restrict__ P, const ProbState *__restrict__ S, const int4 *units,
                         const int32_t *uprob, int64_t u0, int64_t nu) {
@@ -129,13 +130,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int a_ix = lane / LPU, ll = lane % LPU, cell = ll / SPLIT, sub = ll % SPLIT;
     const int64_t t = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * A + a_ix;
     if (t >= nu) return;
-    const int4 u = units[u0 + t];
-    const int p = uprob[u0 + t];
-    if (cell < u.z && S[p].active) {
-        const ProbArgs<T> &pp = P[p];
-        const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
-        solve_cell<T, R, SPLIT, MAXF, false, true>(pp.a, u.x, __ldg(pp.a.order + idx), __ldg(pp.a.mask + idx), sub,
-                                             nullptr, 0, nullptr, 0);
+    if constexpr (COEF) {
+        // every problem has its face stream: sequential coefficient records
+        const uint64_t pol_stream = l2_evict_first();
+        const int4 u = ldg_hint(units + u0 + t, pol_stream);
+        const int p = ldg_hint(uprob + u0 + t, pol_stream);
+        if (cell < u.z && S[p].active) {
+            const ProbArgs<T> &pp = P[p];
+            const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
+            solve_cell_coef<T, R, SPLIT, MAXF>(pp.a, u.x, ldg_hint(pp.a.order + idx, pol_stream),
+                                               ldg_hint(pp.a.mask + idx, pol_stream), sub,
+                                               pp.coef + idx * coef_record_bytes<T, MAXF>(), pol_stream, [] {
+                                                   pdl_wait_prev();  // upwind values come from earlier slots
+                                                   return true;
+                                               });
+        }
+    } else {
+        const int4 u = units[u0 + t];
+        const int p = uprob[u0 + t];
+        if (cell < u.z && S[p].active) {
+            const ProbArgs<T> &pp = P[p];
+            const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
+            solve_cell<T, R, SPLIT, MAXF, false, true>(pp.a, u.x, __ldg(pp.a.order + idx), __ldg(pp.a.mask + idx),
+                                                       sub, nullptr, 0, nullptr, 0);
+        }
     }
 }
 
@@ -162,7 +180,7 @@ __global__ void k_emission_batch(const ProbArgs<T> *P, const ProbState *S, const
         for (int r = 0; r < R; ++r) {
             if (r < pp.nrhs) {
                 const T ph = phi ? phi[(int64_t)r * N + c] : T(0);
-                out[r] = ((cs * ph + pp.q[(int64_t)r * N + c]) / four_pi) * V;
+                out[r] = (fma_rn(cs, ph, pp.q[(int64_t)r * N + c]) / four_pi) * V;  // as k_emission
             }
         }
         out[R] = sg * V;
@@ -338,6 +356,7 @@ struct Batch {
     DevBuf units, uprob, pargs, pstate, acc, cpre, lpre, err;
     int64_t n_units = 0, ncells = 0, nlags = 0;
     int maxf = 4, apw = 1, mode = JSWEEP_MODE_LEVEL_SYNC;
+    bool coef_all = false;  // every problem in the tables has its face stream (and one MAXF)
     std::vector<int64_t> mslot;  // merged table: slot t is [mslot[t], mslot[t + 1])
     std::vector<int64_t> tab_units;  // units of each problem in the table (by position in act)
     // the captured iteration
@@ -521,6 +540,18 @@ template <class T, int R> int build_tables(Batch *b, cudaStream_t s) {
     b->tab_units.assign(K, 0);
     for (int k = 0; k < K; ++k) b->tab_units[k] = uoff[k + 1] - uoff[k];
     b->mode = b->opt.sweep_mode == JSWEEP_MODE_PERSISTENT ? JSWEEP_MODE_PERSISTENT : JSWEEP_MODE_LEVEL_SYNC;
+    // level-synchronous batches read the handles' face streams when all have one
+    // built for the batch's face slot count (the records' layout depends on it)
+    b->coef_all = b->mode == JSWEEP_MODE_LEVEL_SYNC && !b->opt.no_face_stream;
+    const int mf = FS <= 4 ? 4 : FS <= 6 ? 6 : 7;
+    for (int k = 0; k < K && b->coef_all; ++k) {
+        Dags *d = b->probs[b->act[k]]->d;
+        const int dmf = d->mesh->FS <= 4 ? 4 : d->mesh->FS <= 6 ? 6 : 7;
+        P[k].coef = dmf == mf ? ensure_face_stream(d, b->prec, s) : nullptr;
+        b->coef_all = P[k].coef != nullptr;
+    }
+    if (!b->coef_all)
+        for (int k = 0; k < K; ++k) P[k].coef = nullptr;
     b->ncells = cpre[K];
     b->nlags = lpre[K];
     b->maxf = FS <= 4 ? 4 : FS <= 6 ? 6 : 7;
@@ -577,16 +608,17 @@ template <class T, int R, int SPLIT, int MAXF> void *dd_kernel_a(int A) {
     return dd_kernel<T, R, SPLIT, MAXF, 1>();
 }
 
-template <class T, int R, int SPLIT, int MAXF, int A> void *level_kernel() {
-    return reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A>);
+template <class T, int R, int SPLIT, int MAXF, int A> void *level_kernel(bool coef) {
+    return coef ? reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, true>)
+                : reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, false>);
 }
 
-template <class T, int R, int SPLIT, int MAXF> void *level_kernel_a(int A) {
+template <class T, int R, int SPLIT, int MAXF> void *level_kernel_a(int A, bool coef) {
     if constexpr (SPLIT == 1) {
-        if (A == 2) return level_kernel<T, R, SPLIT, MAXF, 2>();
-        if (A == 4) return level_kernel<T, R, SPLIT, MAXF, 4>();
+        if (A == 2) return level_kernel<T, R, SPLIT, MAXF, 2>(coef);
+        if (A == 4) return level_kernel<T, R, SPLIT, MAXF, 4>(coef);
     }
-    return level_kernel<T, R, SPLIT, MAXF, 1>();
+    return level_kernel<T, R, SPLIT, MAXF, 1>(coef);
 }
 
 // Queue one batched iteration on stream cs (captured into the graph).
@@ -598,9 +630,9 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     k_emission_batch<T, R><<<grid_for(b->ncells, 256, 152 * 16), 256, 0, cs>>>(P, S, b->cpre.as<int64_t>(), K,
                                                                                b->ncells);
     if (b->mode == JSWEEP_MODE_LEVEL_SYNC) {
-        void *lk = b->maxf == 4 ? level_kernel_a<T, R, SPLIT, 4>(b->apw)
-                 : b->maxf == 6 ? level_kernel_a<T, R, SPLIT, 6>(b->apw)
-                                : level_kernel_a<T, R, SPLIT, 7>(b->apw);
+        void *lk = b->maxf == 4 ? level_kernel_a<T, R, SPLIT, 4>(b->apw, b->coef_all)
+                 : b->maxf == 6 ? level_kernel_a<T, R, SPLIT, 6>(b->apw, b->coef_all)
+                                : level_kernel_a<T, R, SPLIT, 7>(b->apw, b->coef_all);
         const int4 *units = b->units.as<int4>();
         const int32_t *uprob = b->uprob.as<int32_t>();
         JS_CUDA(cudaEventRecordWithFlags(b->ev[0], cs, cudaEventRecordExternal));
@@ -636,10 +668,7 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     int64_t grid = (int64_t)device_sm_count() * occ;  // every warp resident
     const int64_t groups = (b->n_units + b->apw - 1) / b->apw;
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, (groups + kWarpsPerBlock - 1) / kWarpsPerBlock));
-    int dev = 0, khz = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-    if (khz <= 0) khz = 2000000;
+    const int khz = device_clock_khz();
     long long timeout = (long long)(b->opt.spin_timeout_s * (double)khz * 1000.0);
     const int4 *units = b->units.as<int4>();
     const int32_t *uprob = b->uprob.as<int32_t>();

@@ -186,12 +186,19 @@ struct Dags {
     DevBuf flags;    // int32 [N][M]: sweep epoch at which (cell, direction) was last written
     int epoch = 0;
     DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
-    // face-coefficient stream of the level-synchronous sweep (see coef_record_bytes)
-    DevBuf coef;
-    int coef_prec = -1, coef_maxf = 0;
-    const int32_t *coef_order = nullptr;  // the order and directions it was built for
-    const void *coef_dirs = nullptr;
-    bool coef_failed = false;             // allocation refused once: compute coefficients in the sweep
+    // face-coefficient streams of the level-synchronous sweeps, [0] FP32 and [1]
+    // FP64 (see coef_record_bytes); each lives as long as the handle, so batch
+    // problems may keep its address
+    struct FaceStream {
+        DevBuf buf;
+        int maxf = 0;
+        const int32_t *order = nullptr;  // the order and directions it was built for
+        const void *dirs = nullptr;
+        bool failed = false;             // allocation refused: sweeps read the cell geometry
+    } coef[2];
+    // tail of the level-synchronous sweep (persistent launch of the last, small slots)
+    DevBuf tail_pre;         // int32 [M]: units of each direction that run before the tail
+    int64_t tail_t0 = -1;    // first tail unit of the captured graph (-1: no tail)
     UnitTable ut;
     std::unique_ptr<PatchSched> ps;  // lazily built (patch programs)
     // CUDA graph of the level-synchronous sweep
@@ -216,6 +223,9 @@ Dags *build_diagonals(Dags *d, cudaStream_t s);
 // unit schedules and sweeps (sweep.cu)
 int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps = 0);
 int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s);  // FP64 directions as [M][4]
+// Face-coefficient stream of a handle (level-synchronous sweeps), built on
+// first use; nullptr when the option is off or its allocation was refused.
+const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s);
 int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source,
               const void *inflow, void *phi_out, void *psi_out, cudaStream_t s);
 int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio,
@@ -236,6 +246,7 @@ inline int grid_for(int64_t n, int block, int64_t cap = 1 << 20) {
 }
 
 int device_sm_count();
+int device_clock_khz();  // SM clock of the current device (cached)
 int check_options(const jsweep_options *opt, jsweep_options *o);
 
 }  // namespace js

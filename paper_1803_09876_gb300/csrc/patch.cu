@@ -898,9 +898,7 @@ template <class T, int R> int launch_patch(Dags *d, const SweepArgs<T> &a, cudaS
                                                             ps.queue.as<int32_t>(), ps.seq.as<uint32_t>(),
                                                             ps.ctr.as<uint32_t>());
     JS_LAUNCH_CHECK();
-    int khz = 0;
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-    if (khz <= 0) khz = 2000000;
+    const int khz = device_clock_khz();
     PatchArgs<T> pa;
     pa.a = a;
     pa.pc_ptr = pp.d_ptr.as<int32_t>();

@@ -62,12 +62,82 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (t >= nu) return;
-    const int4 u = a.units[u0 + t];
+    const uint64_t pol_stream = l2_evict_first();
+    const int4 u = ldg_hint(a.units + u0 + t, pol_stream);
     const int cell = lane / SPLIT, sub = lane % SPLIT;
     if (cell < u.z) {
         const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
-        solve_cell_coef<T, R, SPLIT, MAXF>(a, u.x, __ldg(a.order + idx), __ldg(a.mask + idx), sub,
-                                           coef + idx * RB);
+        solve_cell_coef<T, R, SPLIT, MAXF>(a, u.x, ldg_hint(a.order + idx, pol_stream),
+                                           ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB, pol_stream, [] {
+                                               pdl_wait_prev();  // upwind values come from earlier slots
+                                               return true;
+                                           });
+    }
+}
+
+// The tail of a level-synchronous sweep: the last slots, too small to fill the
+// GPU, run in one persistent launch instead of one launch each.  Warps take
+// tail units in slot order from a shared counter (*next), each taking its next
+// unit before it solves the current one.  done[m] counts the finished tail
+// units of direction m; a unit of direction m needs the units of m's earlier
+// layers: u.w of them in all, pre[m] of which ran before the tail (before this
+// launch), so it waits until done[m] >= u.w - pre[m].  A unit only finishes
+// after its own wait, so once done[m] reaches that count every earlier layer
+// is complete.  Every unit a warp holds has its producers at smaller indices,
+// taken earlier by running warps, so the smallest unfinished unit can always
+// proceed: the launch cannot deadlock even when only part of the grid is
+// resident.  Waits are bounded (timeout in clock cycles, error flag *err).
+template <class T, int R, int SPLIT, int MAXF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sweep_tail(SweepArgs<T> a, int64_t t0, int64_t nt, const unsigned char *coef, const int *pre,
+                 int *done, int *next, int *err, long long timeout, int debug_extra) {
+    constexpr int RB = coef_record_bytes<T, MAXF>();
+    const int lane = threadIdx.x & 31;
+    const int cell = lane / SPLIT, sub = lane % SPLIT;
+    const uint64_t pol_stream = l2_evict_first();
+    int t = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 1) : 0, 0);
+    while (t < nt) {
+        const int t_next = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 1) : 0, 0);
+        const int4 u = ldg_hint(a.units + t0 + t, pol_stream);
+        // debug_extra (test hook): one more finished unit than can exist, so every wait runs out
+        const int need = u.w - __ldg(pre + u.x) + debug_extra;
+        const int *cnt = done + u.x;
+        bool ok = true;
+        if (cell < u.z) {
+            const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
+            ok = solve_cell_coef<T, R, SPLIT, MAXF>(
+                a, u.x, ldg_hint(a.order + idx, pol_stream), ldg_hint(a.mask + idx, pol_stream), sub,
+                coef + idx * RB, pol_stream, [&]() -> bool {
+                    pdl_wait_prev();  // the level-synchronous slots before the tail
+                    if (ld_acquire(cnt) >= need) return true;
+                    const long long c0 = clock64();
+                    int ns = 32;
+                    while (ld_acquire(cnt) < need) {
+                        if (ld_volatile(err) != 0) return false;
+                        if (clock64() - c0 > timeout) {
+                            atomicCAS(err, 0, 1);
+                            return false;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 128 ? 2 * ns : 128;
+                    }
+                    return true;
+                });
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        // the warp's psi stores are ordered before the first lane's release
+        __syncwarp();
+        if (lane == 0) red_release_add(done + u.x, 1);
+        t = t_next;
+    }
+}
+
+// pre[m] = the smallest wait target among direction m's tail units (the units
+// of m that ran before the tail); pre is filled with INT_MAX first.
+__global__ void k_tail_pre(const int4 *units, int64_t nt, int *pre) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int4 u = units[i];
+        atomicMin(pre + u.x, u.w);
     }
 }
 
@@ -301,7 +371,7 @@ __global__ void k_emission(const T *sig, const T *cr, const T *q, const T *phi, 
         for (int r = 0; r < R; ++r) {
             if (r < nrhs) {
                 T p = phi ? phi[(int64_t)r * N + c] : T(0);
-                out[r] = ((cs * p + q[(int64_t)r * N + c]) / four_pi) * V;
+                out[r] = (fma_rn(cs, p, q[(int64_t)r * N + c]) / four_pi) * V;  // as k_emission_batch
             }
         }
         out[R] = s * V;
@@ -669,10 +739,7 @@ int launch_dd(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
     JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarpsPerBlock * 32, 0));
     if (occ < 1) occ = 1;
     if (bps <= 0 || bps > occ) bps = occ;  // every warp must be resident
-    int dev = 0, khz = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-    if (khz <= 0) khz = 2000000;
+    const int khz = device_clock_khz();
     const long long timeout = (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
     int64_t grid = (int64_t)device_sm_count() * bps;
     const int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -727,11 +794,42 @@ template <class T, int R> int64_t patch_warps(const Dags *d, int mode) {
     return (mode == JSWEEP_MODE_PERSISTENT && d->opt.priority == JSWEEP_PRIO_PATCH) ? dd_resident_warps<T, R>(d) : 0;
 }
 
-template <class T, int R, int SPLIT, int MAXF>
-void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsigned char *coef) {
+// Blocks of the tail kernel that can be resident at once.
+template <class T, int R, int SPLIT, int MAXF> int64_t tail_resident_blocks() {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_tail<T, R, SPLIT, MAXF>, kWarpsPerBlock * 32,
+                                                      0) != cudaSuccess)
+        occ = 1;
+    return (int64_t)device_sm_count() * std::max(occ, 1);
+}
+
+// First slot of the tail: the slots from it to the end each hold fewer than
+// tail_units units.  Returns the number of slots when there is no tail.
+int64_t tail_slot(const Dags *d) {
     const auto &sp = d->ut.slot_ptr;
+    const int64_t Tn = (int64_t)sp.size() - 1;
+    if (d->opt.tail_units <= 0 || Tn <= 0) return std::max<int64_t>(Tn, 0);
+    const int64_t thr = d->opt.tail_units;
+    int64_t S = Tn;
+    while (S > 0 && sp[S] - sp[S - 1] < thr) --S;
+    while (S < Tn && sp[Tn] - sp[S] > INT32_MAX / 2) ++S;  // the tail's unit counter is 32-bit
+    return S;
+}
+
+long long spin_timeout_cycles(const Dags *d) {
+    const int khz = device_clock_khz();
+    return (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
+}
+
+// Records the sweep's launches on the capture stream: one launch per slot
+// before the tail slot S, then (S < number of slots) the persistent tail.
+template <class T, int R, int SPLIT, int MAXF>
+void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsigned char *coef, int64_t S) {
+    const auto &sp = d->ut.slot_ptr;
+    const int64_t Tn = (int64_t)sp.size() - 1;
+    if (S < Tn) cudaMemsetAsync(d->counters.p, 0, (size_t)(d->M + 8) * 4, cs);  // error flag and done[]
     bool first = true;
-    for (size_t l = 0; l + 1 < sp.size(); ++l) {
+    for (int64_t l = 0; l < std::min(S, Tn); ++l) {
         const int64_t nu = sp[l + 1] - sp[l];
         if (nu <= 0) continue;
         const int64_t blocks = (nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -751,68 +849,96 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         if (coef) cudaLaunchKernelEx(&cfg, k_sweep_level_coef<T, R, SPLIT, MAXF>, a, u0, nu, coef);
         else cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
     }
+    if (S < Tn) {
+        const int64_t t0 = sp[S], nt = sp[Tn] - sp[S];
+        const int64_t blocks = std::min(tail_resident_blocks<T, R, SPLIT, MAXF>(),
+                                        (nt + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::max<int64_t>(blocks, 1));
+        cfg.blockDim = dim3(kWarpsPerBlock * 32);
+        cfg.stream = cs;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = first ? 0 : 1;
+        // counters: [0] error flag, [1] next unit, [8, 8 + M) finished units per direction
+        int *err = reinterpret_cast<int *>(d->counters.p);
+        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF>, a, t0, nt, coef,
+                           (const int *)d->tail_pre.as<int>(), err + 8, err + 1, err, spin_timeout_cycles(d),
+                           d->opt.debug_block_waits ? 1 : 0);
+    }
 }
 
-// The face-coefficient stream of the handle for precision T (built once per
-// handle and sweep order), or nullptr when it is switched off or its
-// allocation was refused (the sweep then reads the cell geometry).
+// The face-coefficient stream of the handle for precision T, built on first
+// use (callers check the no_face_stream option), or nullptr when its
+// allocation was refused (the sweep then reads the cell geometry).  It is
+// built for the handle's sweep order and directions, which do not change
+// after the build, so its address stays valid for the handle's life.
 template <class T> const unsigned char *ensure_coef(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
-    if (d->opt.no_face_stream || d->coef_failed) return nullptr;
+    Dags::FaceStream &fs = d->coef[sizeof(T) == 8 ? 1 : 0];
+    if (fs.failed) return nullptr;
     const int maxf = a.FS <= 4 ? 4 : a.FS <= 6 ? 6 : 7;
-    const int prec = sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32;
-    if (d->coef.p && d->coef_prec == prec && d->coef_maxf == maxf && d->coef_order == d->s_order &&
-        d->coef_dirs == (const void *)a.dirs)
-        return d->coef.as<unsigned char>();
+    if (fs.buf.p && fs.maxf == maxf && fs.order == d->s_order && fs.dirs == (const void *)a.dirs)
+        return fs.buf.as<unsigned char>();
     const int rb = maxf == 4 ? coef_record_bytes<T, 4>() : maxf == 6 ? coef_record_bytes<T, 6>()
                                                                      : coef_record_bytes<T, 7>();
-    if (d->coef.alloc((size_t)d->N * d->M * rb, s) != JSWEEP_OK) {
+    if (fs.buf.alloc((size_t)d->N * d->M * rb, s) != JSWEEP_OK) {
         clear_error();
-        d->coef_failed = true;
+        fs.failed = true;
         return nullptr;
     }
+    unsigned char *out = fs.buf.as<unsigned char>();
     const int grid = grid_for(d->N * d->M, 256, 152 * 64);
-    if (maxf == 4)
-        k_coef_fill<T, 4><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS,
-                                               d->coef.as<unsigned char>());
-    else if (maxf == 6)
-        k_coef_fill<T, 6><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS,
-                                               d->coef.as<unsigned char>());
-    else
-        k_coef_fill<T, 7><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS,
-                                               d->coef.as<unsigned char>());
+    if (maxf == 4) k_coef_fill<T, 4><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, out);
+    else if (maxf == 6) k_coef_fill<T, 6><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, out);
+    else k_coef_fill<T, 7><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, out);
     if (cudaGetLastError() != cudaSuccess) {
-        d->coef.release();
-        d->coef_failed = true;
+        fs.buf.release();
+        fs.failed = true;
         return nullptr;
     }
     note_launches(1);
-    d->coef_prec = prec;
-    d->coef_maxf = maxf;
-    d->coef_order = d->s_order;
-    d->coef_dirs = a.dirs;
-    return d->coef.as<unsigned char>();
+    fs.maxf = maxf;
+    fs.order = d->s_order;
+    fs.dirs = a.dirs;
+    return out;
 }
 
 template <class T, int R>
 int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
     constexpr int SPLIT = split_of<T, R>();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
-        const unsigned char *coef = ensure_coef<T>(d, a, s);
+        const unsigned char *coef = d->opt.no_face_stream ? nullptr : ensure_coef<T>(d, a, s);
+        const int64_t Tn = (int64_t)d->ut.slot_ptr.size() - 1;
+        const int64_t S = coef ? tail_slot(d) : Tn;  // the tail runs on the face stream
         char key[512];
-        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p", (int)sizeof(T), R, (const void *)a.srcv,
-                 (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
-                 (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units, (const void *)coef);
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld/%p/%lld/%d", (int)sizeof(T), R,
+                 (const void *)a.srcv, (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
+                 (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units, (const void *)coef,
+                 (long long)S, d->counters.p, spin_timeout_cycles(d), d->opt.debug_block_waits);
         if (!d->graph || d->graph_key != key) {
             if (d->graph) {
                 cudaGraphExecDestroy(d->graph);
                 d->graph = nullptr;
             }
             if (!d->capture_stream) JS_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
+            d->tail_t0 = -1;
+            if (S < Tn) {
+                // units of each direction that run before the tail
+                const int64_t t0 = d->ut.slot_ptr[S], nt = d->ut.slot_ptr[Tn] - t0;
+                JS_TRY(d->tail_pre.ensure((size_t)d->M * 4, s));
+                JS_CUDA(cudaMemsetAsync(d->tail_pre.p, 0x7f, (size_t)d->M * 4, s));
+                k_tail_pre<<<grid_for(nt, 256, 152 * 8), 256, 0, s>>>(d->ut.units.as<int4>() + t0, nt,
+                                                                      d->tail_pre.as<int>());
+                JS_LAUNCH_CHECK();
+                d->tail_t0 = t0;
+            }
             cudaStream_t cs = d->capture_stream;
             JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            if (a.FS <= 4) capture_levels<T, R, SPLIT, 4>(d, a, cs, coef);
-            else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6>(d, a, cs, coef);
-            else capture_levels<T, R, SPLIT, 7>(d, a, cs, coef);
+            if (a.FS <= 4) capture_levels<T, R, SPLIT, 4>(d, a, cs, coef, S);
+            else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6>(d, a, cs, coef, S);
+            else capture_levels<T, R, SPLIT, 7>(d, a, cs, coef, S);
             cudaGraph_t g;
             cudaError_t e = cudaStreamEndCapture(cs, &g);
             if (e != cudaSuccess) {
@@ -829,8 +955,8 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
             d->graph_key = key;
         }
         JS_CUDA(cudaGraphLaunch(d->graph, s));
-        int64_t nodes = 0;
-        for (size_t l = 0; l + 1 < d->ut.slot_ptr.size(); ++l) nodes += d->ut.slot_ptr[l + 1] > d->ut.slot_ptr[l];
+        int64_t nodes = S < Tn ? 1 : 0;
+        for (int64_t l = 0; l < S; ++l) nodes += d->ut.slot_ptr[l + 1] > d->ut.slot_ptr[l];
         note_launches(nodes);
         d->timing.sweep_launches = nodes;
         return JSWEEP_OK;
@@ -842,6 +968,16 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
 }
 
 int check_sweep_error(Dags *d, cudaStream_t s, int mode) {
+    if (mode == JSWEEP_MODE_LEVEL_SYNC && d->tail_t0 >= 0) {
+        int err = 0;
+        JS_CUDA(cudaMemcpyAsync(&err, d->counters.p, 4, cudaMemcpyDeviceToHost, s));
+        JS_CUDA(cudaStreamSynchronize(s));
+        if (err) {
+            set_error("level-synchronous sweep tail: a dependency wait exceeded %.3g s", d->opt.spin_timeout_s);
+            return JSWEEP_ERR_DEVICE_TIMEOUT;
+        }
+        return JSWEEP_OK;
+    }
     if (mode != JSWEEP_MODE_PERSISTENT && mode != JSWEEP_MODE_PATCH) return JSWEEP_OK;
     if (mode == JSWEEP_MODE_PATCH) JS_TRY(patch_counts(d, s));
     int err = 0;
@@ -883,6 +1019,30 @@ int one_sweep(Dags *d, int mode, bool has_inflow, const T *wts, T *phi_dst, int 
 }
 
 }  // namespace
+
+// The handle's face-coefficient stream for precision prec, built from the
+// handle's own geometry and directions (the ones its sweeps and batches use),
+// or nullptr when switched off or refused.
+const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s) {
+    if (prec == JSWEEP_F64) {
+        if (ensure_dirs64x4(d, d->dirs4_64, s) != JSWEEP_OK) {
+            clear_error();
+            return nullptr;
+        }
+        SweepArgs<double> a{};
+        a.FS = d->mesh->FS;
+        a.GS = d->mesh->GS;
+        a.geo = d->mesh->geo64.as<double4>();
+        a.dirs = d->dirs4_64.as<double>();
+        return ensure_coef<double>(d, a, s);
+    }
+    SweepArgs<float> a{};
+    a.FS = d->mesh->FS;
+    a.GS = d->mesh->GS;
+    a.geo = d->mesh->geo32.as<float4>();
+    a.dirs = reinterpret_cast<const float *>(d->quad->dirs32.p);
+    return ensure_coef<float>(d, a, s);
+}
 
 // FP64 directions in [M][4] layout (the FP32 copy lives in the quadrature).
 static int dirs64x4(Dags *d, cudaStream_t s, const double **out) {

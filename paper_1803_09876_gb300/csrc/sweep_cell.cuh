@@ -101,6 +101,41 @@ template <class T, int R> __device__ __forceinline__ void store_cg(T *p, const T
     }
 }
 
+// ---- L2 eviction priority of read-once streams ---------------------------------------
+// A level-synchronous slot reads its unit, order, mask and face-coefficient
+// records once per sweep; they are loaded evict-first so that they leave L2
+// to the psi values and source records that other slots read again.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ float4 ldg_hint(const float4 *p, uint64_t pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int4 ldg_hint(const int4 *p, uint64_t pol) {
+    int4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ldg_hint(const int32_t *p, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ unsigned ldg_hint(const uint8_t *p, uint64_t pol) {
+    unsigned v;
+    asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Index of the lagged face f of direction m in the lag list, or -1.
 __device__ __forceinline__ int lag_index(const int32_t *lag_ptr, const int32_t *lag_face, int m, int32_t f) {
     int lo = lag_ptr[m], hi = lag_ptr[m + 1];
@@ -127,9 +162,19 @@ __device__ __forceinline__ double face_dot(double ox, double oy, double oz, doub
 
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+// round-to-nearest sums and differences that the compiler may not fuse with a
+// neighbouring product or rearrange
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_release_add(int *p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Per-cell geometry and bookkeeping shared by the sweep kernels.
@@ -251,9 +296,13 @@ template <class T, int MAXF> constexpr int coef_record_bytes() {
 
 // The per-cell solve of solve_cell with the coefficients from the record
 // (same operations in the same order, so results are bit-identical).
-template <class T, int R, int SPLIT, int MAXF>
-__device__ __forceinline__ void solve_cell_coef(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
-                                                const unsigned char *rec) {
+// `upwind_ready()` is called after every load that does not depend on other
+// cells and before the upwind psi reads; it returns false to abandon the cell
+// (a bounded wait that gave up).
+template <class T, int R, int SPLIT, int MAXF, class Ready>
+__device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
+                                                const unsigned char *rec, uint64_t pol_stream,
+                                                Ready upwind_ready) {
     constexpr int RH = R / SPLIT;
     constexpr int RB = coef_record_bytes<T, MAXF>();
     T dk[MAXF];
@@ -261,7 +310,7 @@ __device__ __forceinline__ void solve_cell_coef(const SweepArgs<T> &a, int m, in
     {
         float4 w[RB / 16];
 #pragma unroll
-        for (int i = 0; i < RB / 16; ++i) w[i] = __ldg(reinterpret_cast<const float4 *>(rec) + i);
+        for (int i = 0; i < RB / 16; ++i) w[i] = ldg_hint(reinterpret_cast<const float4 *>(rec) + i, pol_stream);
         const unsigned char *b = reinterpret_cast<const unsigned char *>(w);
         memcpy(dk, b, MAXF * sizeof(T));
         memcpy(nbk, b + MAXF * sizeof(T), MAXF * 4);
@@ -283,7 +332,7 @@ __device__ __forceinline__ void solve_cell_coef(const SweepArgs<T> &a, int m, in
             }
         }
     }
-    pdl_wait_prev();  // upwind values come from earlier slots
+    if (!upwind_ready()) return false;
 #pragma unroll
     for (int k = 0; k < MAXF; ++k) {
         const T d = dk[k];
@@ -313,6 +362,7 @@ __device__ __forceinline__ void solve_cell_coef(const SweepArgs<T> &a, int m, in
 #pragma unroll
     for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
     store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
+    return true;
 }
 
 // phi[r][c] = sum_m w_m psi[c][m][r]: one warp per cell reads the cell's
@@ -322,9 +372,9 @@ __device__ __forceinline__ void solve_cell_coef(const SweepArgs<T> &a, int m, in
 // operation is fixed, so phi does not depend on the sweep's schedule.
 template <class T>
 __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
-    s = a + b;
-    T bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = add_rn(a, b);
+    const T bb = sub_rn(s, a);
+    e = add_rn(sub_rn(a, sub_rn(s, bb)), sub_rn(b, bb));
 }
 
 // phi of one cell: lane l sums directions l, l+32, ... of the cell's
@@ -344,13 +394,15 @@ __device__ __forceinline__ void phi_warp(const T *blk, const T *w, int M, int la
         const T wm = w[m];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
+            // explicit fused multiply-adds: the compiler may not contract these
+            // differently in the kernels that share this reduction
             if constexpr (sizeof(T) == 4) {
-                T y = wm * x[r] - comp[r];
-                T t = s[r] + y;
-                comp[r] = (t - s[r]) - y;
+                const T y = fma_rn(wm, x[r], -comp[r]);
+                const T t = add_rn(s[r], y);
+                comp[r] = sub_rn(sub_rn(t, s[r]), y);
                 s[r] = t;
             } else {
-                s[r] = s[r] + wm * x[r];
+                s[r] = fma_rn(wm, x[r], s[r]);
             }
         }
     }
@@ -366,9 +418,9 @@ __device__ __forceinline__ void phi_warp(const T *blk, const T *w, int M, int la
             T ss, ee;
             two_sum(lower ? v : ov, lower ? ov : v, ss, ee);
             v = ss;
-            e = (lower ? e : oe) + (lower ? oe : e) + ee;
+            e = add_rn(add_rn(lower ? e : oe, lower ? oe : e), ee);
         }
-        out[r] = v + e;
+        out[r] = add_rn(v, e);
     }
 }
 

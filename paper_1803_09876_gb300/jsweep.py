@@ -88,6 +88,7 @@ class jsweep_options(ctypes.Structure):
         ("patch_cells", ctypes.c_int),
         ("eager_search_max", ctypes.c_int),
         ("no_face_stream", ctypes.c_int),
+        ("tail_units", ctypes.c_int),
         ("reserved", ctypes.c_int * 1),
     ]
 

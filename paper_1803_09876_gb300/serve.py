@@ -353,19 +353,19 @@ class GpuBackend:
     def resident_extra_bytes(self, key):
         """Device bytes a mesh's handle allocates at its first solve and keeps
         until it is released, reserved with the mesh: its own unit table (one
-        16-byte unit per 8 or more (direction, cell) pairs), and for a mesh of
-        the solo lane the sweep state of jsweep_source_iterate (psi, sources,
-        inflow, phi, lagged psi, and the face-coefficient stream of 32 to 96
-        bytes per pair)."""
+        16-byte unit per 8 or more (direction, cell) pairs), its face-coefficient
+        stream (32 to 96 bytes per pair, read by level-synchronous sweeps and
+        batches), and for a mesh of the solo lane the sweep state of
+        jsweep_source_iterate (psi, sources, inflow, phi, lagged psi)."""
         N, F, M, Fb, FS = self._shape(key)
-        extra = 2 * M * N
+        es = 8 if self.dtype == self.torch.float64 else 4
+        maxf = 4 if FS <= 4 else 6 if FS <= 6 else 7
+        rb = -(-(maxf * es + maxf * 4) // 16) * 16
+        extra = (2 + rb) * M * N
         if self.solo_lane is not None and self._lane_of_work(N * M) == self.solo_lane:
-            es = 8 if self.dtype == self.torch.float64 else 4
             R = self._rhs_padded()
             RS = 2 * R if R >= 4 else (4 if R == 2 else 2)
-            maxf = 4 if FS <= 4 else 6 if FS <= 6 else 7
-            rb = -(-(maxf * es + maxf * 4) // 16) * 16
-            extra += (M * N * (R * es + rb) + N * (RS + 2 * self.nrhs) * es + (max(Fb, 1) + F) * R * es
+            extra += (M * N * R * es + N * (RS + 2 * self.nrhs) * es + (max(Fb, 1) + F) * R * es
                       + (M + 8) * 8 + (1 << 20))
         return extra
 

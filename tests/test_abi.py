@@ -49,6 +49,7 @@ def test_version_and_options(lib):
     assert o.cluster_cells == 32 and o.spin_timeout_s > 0 and o.cycle_search_max == 256
     assert o.debug_block_waits == 0
     assert o.eager_search_max == 64 and o.patch_cells == 512
+    assert o.no_face_stream == 0 and o.tail_units == 0
 
 
 @pytest.mark.parametrize("npol,naz", [(1, 3), (2, 3), (3, 4), (4, 4), (6, 6), (8, 2)])

@@ -90,6 +90,34 @@ def test_batch_equals_solo_bitwise(prec, mode):
         assert b.query(pid) == (js.JSWEEP_PROBLEM_CONVERGED, it_ref, res_ref)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_of_one_cell_shape_reads_face_streams_bitwise(prec):
+    # all problems on tetrahedra: the level-synchronous batch reads every
+    # handle's face-coefficient stream; with the stream off it reads the cell
+    # geometry; both give the single-problem bits
+    torch = _torch()
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    tol = 1e-8 if prec == "f64" else 1e-6
+    js = J()
+    rng = np.random.default_rng(78)
+    data = []
+    for n, quad in ((5, (1, 3)), (3, (3, 4)), (7, (4, 4)), (6, (2, 2))):
+        mesh = kuhn_tets(n, 0.2, 20 + n)
+        dirs, w = oracle.product_quadrature(*quad)
+        N = mesh["n_cells"]
+        data.append(dict(g=build(mesh, dirs, w), sig=tensor(rng.uniform(0.5, 2.0, N), dtype),
+                         c=tensor(np.full(N, 0.5), dtype), q=tensor(rng.uniform(0.0, 1.0, (2, N)), dtype),
+                         inflow=None, N=N))
+    solo = [js.jsweep_source_iterate(d["g"], d["sig"], d["c"], d["q"], tol=tol, max_iters=500) for d in data]
+    for no_stream in (0, 1):
+        b = js.Batch(dtype, 2, js.jsweep_options_default(sweep_mode=1, no_face_stream=no_stream))
+        ids = [b.add(d["g"], d["sig"], d["c"], d["q"], tol=tol, max_iters=500) for d in data]
+        its, _ = b.source_iterate()
+        for k, pid in enumerate(ids):
+            assert its[k] == solo[k][1]
+            assert torch.equal(b.phi(pid), solo[k][0])
+
+
 @pytest.mark.parametrize("mode,apw,cells,order", [(2, 2, 16, 1), (2, 4, 8, 0), (1, 4, 8, 1), (1, 2, 16, 0),
                                                   (2, 1, 5, 1)])
 def test_batch_angles_per_warp_fp32_against_oracle(mode, apw, cells, order):

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 MODES = [dict(sweep_mode=1), dict(sweep_mode=2), dict(sweep_mode=2, priority=1, cluster_cells=7),
          dict(sweep_mode=2, priority=2, cluster_cells=1), dict(sweep_mode=1, cluster_cells=5),
          dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=3, cluster_cells=3),
-         dict(sweep_mode=3), dict(sweep_mode=3, patch_cells=64)]
+         dict(sweep_mode=3), dict(sweep_mode=3, patch_cells=64), dict(sweep_mode=1, tail_units=64)]
 
 
 def _torch():
@@ -236,13 +236,15 @@ def test_workload3_full_size_sampled_psi_and_phi_reduction():
     assert rel_err(phi.double().cpu().numpy(), acc.cpu().numpy()) < 1e-6
 
 
-@pytest.mark.parametrize("mode", [2, 3], ids=["persistent", "patch_programs"])
+@pytest.mark.parametrize("mode", [2, 3, 1], ids=["persistent", "patch_programs", "level_sync_tail"])
 def test_bounded_wait_times_out_and_context_survives(mode):
     torch = _torch()
     js = J()
     mesh = hex_grid(6, 0.15, 1)
     dirs, w = oracle.product_quadrature(1, 3)
-    g = build(mesh, dirs, w, sweep_mode=mode, debug_block_waits=1, spin_timeout_s=0.05, patch_cells=32)
+    # level-synchronous: every slot in the persistent tail, whose waits are bounded
+    g = build(mesh, dirs, w, sweep_mode=mode, debug_block_waits=1, spin_timeout_s=0.05, patch_cells=32,
+              tail_units=1 << 30)
     N = mesh["n_cells"]
     sig = tensor(np.ones(N), torch.float32)
     src = tensor(np.ones((1, N)), torch.float32)
@@ -324,8 +326,9 @@ def test_face_stream_and_every_schedule_give_the_same_bits(prec):
         sig = rng.lognormal(0.0, 1.0, N)
         srcs = [rng.uniform(0.0, 1.0, (R, N)) for _ in range(2)]
         outs = []
-        for opts in (dict(sweep_mode=1), dict(sweep_mode=1, no_face_stream=1), dict(sweep_mode=2),
-                     dict(sweep_mode=3, patch_cells=64)):
+        for opts in (dict(sweep_mode=1), dict(sweep_mode=1, no_face_stream=1),
+                     dict(sweep_mode=1, tail_units=1 << 30), dict(sweep_mode=1, tail_units=40),
+                     dict(sweep_mode=2), dict(sweep_mode=3, patch_cells=64)):
             g = build(mesh, dirs, w, **opts)
             outs.append([J().jsweep_sweep(g, tensor(sig, dt), tensor(s, dt)).cpu() for s in srcs])
         for o in outs[1:]:
