@@ -36,10 +36,10 @@ if ROOT not in sys.path:
 
 METRIC = "cell-angle updates/s"
 # DRAM bytes (read + write) of one sweep of the dominant kernel, from the full-sweep ncu capture
-# summarised in profiles/k_sweep_level_hex128_full_sweep_dram.md; keyed by
+# summarised in profiles/k_sweep_level_coef_hex128_full_sweep_dram.md; keyed by
 # (hex edge, sweep mode, priority, cluster cells, layering, face stream); valid while the kernel is
-# unchanged (none yet for the current kernels)
-SWEEP_TRAFFIC_BYTES = {}
+# unchanged
+SWEEP_TRAFFIC_BYTES = {(128, 1, 0, 32, 0, 1): 1.582e11}
 UNIT = "cell-angle-rhs updates/s"
 WORKLOAD = "hex128_jitter0.15_288dirs_8rhs_fp32_si_tol1e-6"
 
