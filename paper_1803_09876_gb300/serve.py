@@ -276,6 +276,33 @@ def summarize(reqs, cell_dir_updates: Callable[[Request], float]):
             "cell_angle_updates_per_s": work / (t_end - t_start)}
 
 
+def face_record_bytes(faces_per_cell: int, elem_bytes: int) -> int:
+    """Bytes of one face-coefficient record of a handle's stream: Omega.A of
+    every face slot (4 slots up to 4 faces, 6 up to 6, else 7) and the slot's
+    neighbour id (int32), padded to 16 bytes."""
+    slots = 4 if faces_per_cell <= 4 else 6 if faces_per_cell <= 6 else 7
+    return -(-(slots * elem_bytes + slots * 4) // 16) * 16
+
+
+def handle_resident_bytes(n_cells: int, n_faces: int, n_dirs: int, n_bfaces: int, faces_per_cell: int,
+                          elem_bytes: int, nrhs: int, solo: bool) -> int:
+    """Device bytes a handle allocates at its first solve and keeps while it
+    lives: its own unit table (one 16-byte unit per 8 or more (direction,
+    cell) pairs, 2 bytes per pair), its face-coefficient stream (one record
+    per pair), and, when its requests run through jsweep_source_iterate (the
+    solo lane), that call's sweep state: psi, source records, phi ping-pong,
+    inflow and lagged psi, the residual and counter scratch and 1 MiB of
+    slack."""
+    N, F, M = n_cells, n_faces, n_dirs
+    extra = (2 + face_record_bytes(faces_per_cell, elem_bytes)) * M * N
+    if solo:
+        R = 1 if nrhs <= 1 else 2 if nrhs <= 2 else 4 if nrhs <= 4 else 8
+        RS = 2 * R if R >= 4 else (4 if R == 2 else 2)
+        extra += (M * N * R * elem_bytes + N * (RS + 2 * nrhs) * elem_bytes
+                  + (max(n_bfaces, 1) + F) * R * elem_bytes + (M + 8) * 8 + (1 << 20))
+    return extra
+
+
 class GpuBackend:
     """The library's C ABI: graphs from jsweep_build_dags, requests in jsweep
     batches, the comparison through jsweep_source_iterate.
@@ -352,22 +379,11 @@ class GpuBackend:
 
     def resident_extra_bytes(self, key):
         """Device bytes a mesh's handle allocates at its first solve and keeps
-        until it is released, reserved with the mesh: its own unit table (one
-        16-byte unit per 8 or more (direction, cell) pairs), its face-coefficient
-        stream (32 to 96 bytes per pair, read by level-synchronous sweeps and
-        batches), and for a mesh of the solo lane the sweep state of
-        jsweep_source_iterate (psi, sources, inflow, phi, lagged psi)."""
+        until it is released, reserved with the mesh (handle_resident_bytes)."""
         N, F, M, Fb, FS = self._shape(key)
         es = 8 if self.dtype == self.torch.float64 else 4
-        maxf = 4 if FS <= 4 else 6 if FS <= 6 else 7
-        rb = -(-(maxf * es + maxf * 4) // 16) * 16
-        extra = (2 + rb) * M * N
-        if self.solo_lane is not None and self._lane_of_work(N * M) == self.solo_lane:
-            R = self._rhs_padded()
-            RS = 2 * R if R >= 4 else (4 if R == 2 else 2)
-            extra += (M * N * R * es + N * (RS + 2 * self.nrhs) * es + (max(Fb, 1) + F) * R * es
-                      + (M + 8) * 8 + (1 << 20))
-        return extra
+        solo = self.solo_lane is not None and self._lane_of_work(N * M) == self.solo_lane
+        return handle_resident_bytes(N, F, M, Fb, FS, es, self.nrhs, solo)
 
     def mesh_bytes_estimate(self, key):
         """Device bytes of a mesh and its graphs while they are being built

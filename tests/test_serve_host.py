@@ -5,8 +5,8 @@ a virtual clock: no GPU."""
 import numpy as np
 import pytest
 
-from paper_1803_09876_gb300.serve import (Request, Server, percentile, poisson_stream, run_one_at_a_time,
-                                          summarize)
+from paper_1803_09876_gb300.serve import (Request, Server, face_record_bytes, handle_resident_bytes, percentile,
+                                          poisson_stream, run_one_at_a_time, summarize)
 
 
 class Clock:
@@ -258,3 +258,19 @@ def test_lane_caps_let_other_lanes_pass_and_keep_order_within_a_lane():
     assert admit[1] >= done[0] and admit[3] >= done[1]
     order = [rid for _, k, rid in srv.events if k == "admit" and rid != 2]
     assert order == [0, 1, 3]
+
+
+def test_face_record_sizes_and_handle_reservation():
+    # records: Omega.A per face slot and an int32 neighbour id, padded to 16 bytes
+    assert [face_record_bytes(f, 4) for f in (4, 5, 6, 7)] == [32, 48, 48, 64]
+    assert [face_record_bytes(f, 8) for f in (4, 6, 7)] == [48, 80, 96]
+    N, F, M, Fb = 1000, 2200, 48, 300
+    batched = handle_resident_bytes(N, F, M, Fb, 4, 4, 1, solo=False)
+    assert batched == (2 + 32) * M * N  # unit table and FP32 tet stream
+    solo = handle_resident_bytes(N, F, M, Fb, 4, 4, 1, solo=True)
+    # plus psi (R = 1), source records (2 values) and two phi rows, inflow and lagged psi, scratch
+    assert solo - batched == M * N * 4 + N * (2 + 2) * 4 + (Fb + F) * 4 + (M + 8) * 8 + (1 << 20)
+    # 3 rhs are padded to 4 for psi and the source records (8 values), phi keeps 3 rows
+    s3 = handle_resident_bytes(N, F, M, Fb, 6, 8, 3, solo=True)
+    assert s3 - handle_resident_bytes(N, F, M, Fb, 6, 8, 3, solo=False) == (
+        M * N * 4 * 8 + N * (8 + 6) * 8 + (Fb + F) * 4 * 8 + (M + 8) * 8 + (1 << 20))
