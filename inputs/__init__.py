@@ -13,6 +13,7 @@ from .workloads import (  # noqa: F401
     lognormal_blocks_sigma,
     batch_problem_specs,
     make_batch_problem,
+    multigroup_materials,
     tets_edge_for_cells,
     QUAD_BY_NDIRS,
 )

@@ -127,10 +127,36 @@ def make_batch_problem(spec):
     return out
 
 
+def multigroup_materials(n_cells, n_groups=4, seed=0, upscatter=0.05):
+    """Seeded multigroup cross sections of the shape of the paper's JSNT-U
+    runs (4 energy groups): sigma_t [G, N] lognormal per group, growing with
+    the group index (slower particles collide more), and an isotropic
+    scattering matrix sigma_s [G, G, N] whose entry [g_from, g_to] is the
+    rate from group g_from into group g_to.  Each group scatters a fraction
+    0.3-0.8 of sigma_t, mostly into itself and the groups below it
+    (downscatter), a fraction ``upscatter`` of it into the groups above; the
+    outgoing scattering of a group stays below its sigma_t, so every group is
+    subcritical on its own."""
+    rng = np.random.default_rng(seed)
+    G, N = n_groups, n_cells
+    sigma_t = rng.lognormal(0.0, 0.5, (G, N)) * (1.0 + 0.5 * np.arange(G))[:, None]
+    frac = rng.uniform(0.3, 0.8, (G, N))  # scattering fraction of each group
+    shares = np.zeros((G, G, N))
+    for g in range(G):
+        for h in range(G):
+            if h >= g:
+                shares[g, h] = rng.uniform(0.5, 1.0, N) * (2.0 if h == g else 1.0)
+            else:
+                shares[g, h] = upscatter * rng.uniform(0.5, 1.0, N)
+    shares /= shares.sum(axis=1, keepdims=True)
+    sigma_s = shares * (frac * sigma_t)[:, None, :]
+    return sigma_t, sigma_s
+
+
 def tets_edge_for_cells(n_cells_target):
     """Edge n of a 6 n^3 Kuhn mesh closest to a target cell count."""
     return max(1, int(round((n_cells_target / 6.0) ** (1.0 / 3.0))))
 
 
 __all__ = ["WORKLOADS", "make_workload", "lognormal_blocks_sigma", "batch_problem_specs",
-           "make_batch_problem", "tets_edge_for_cells", "QUAD_BY_NDIRS"]
+           "make_batch_problem", "multigroup_materials", "tets_edge_for_cells", "QUAD_BY_NDIRS"]

@@ -10,7 +10,8 @@ oracle never imports the library.  Its arithmetic lives in
 Parity pins (tests/test_oracle_*.py) tie it to the paper and to mathematics:
 the 1D upwind recurrence, the uniform-solution invariant, a dense linear
 solve of the discrete system, brute-force levels, a hand-worked cyclic mesh,
-and quadrature moments.
+quadrature moments, and for the multigroup iteration its one-group and
+uncoupled limits, an infinite-medium fixed point and a dense block solve.
 """
 
 from __future__ import annotations
@@ -70,6 +71,9 @@ def _load():
             lib.od_source_iterate.restype = ctypes.c_int
             lib.od_source_iterate.argtypes = [_p, _i64, _p, _p, _p, _p, _p, ctypes.c_double, _i64,
                                               _p, _p, _p, _p, ctypes.c_int]
+            lib.od_source_iterate_mg.restype = ctypes.c_int
+            lib.od_source_iterate_mg.argtypes = [_p, _i64, _p, _p, _p, _p, _p, ctypes.c_double, _i64,
+                                                 _p, _p, _p, _p, ctypes.c_int]
             lib.od_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -178,6 +182,34 @@ class OracleDags:
                                          int(nthreads))
         if rc not in (OD_OK, OD_NOT_CONVERGED):
             raise RuntimeError(f"oracle source iteration failed ({rc})")
+        return phi, int(it.value), float(res.value), rc == OD_OK, hist[: it.value]
+
+
+    def multigroup_source_iterate(self, sigma_t, sigma_s, q, weights, tol, max_iters, inflow=None,
+                                  nthreads=1):
+        """Multigroup source iteration from phi = 0 (the appendix's transport
+        equation over energy groups, Alg. 1): every iteration forms each
+        group's scattering source from the previous iterate of all groups,
+        S_g = (sum_h sigma_s[h, g] phi_h + q_g) / (4 pi), sweeps each group with
+        its own sigma_t, and stops when every group's relative max-norm change
+        is below tol.  sigma_t [G, N]; sigma_s [G, G, N] with [h, g] the rate
+        from group h into group g; q [G, N]; inflow [G, n_bfaces] or None.
+        Returns (phi [G, N], iters, resid, converged, history)."""
+        sig = _f64(sigma_t).reshape(-1, self.n_cells)
+        G = sig.shape[0]
+        ss = _f64(sigma_s).reshape(G, G, self.n_cells)
+        q = _f64(q).reshape(G, self.n_cells)
+        inf = None if inflow is None else _f64(inflow).reshape(G, self.n_bfaces)
+        w = _f64(weights)
+        phi = np.empty((G, self.n_cells))
+        it = ctypes.c_int64(0)
+        res = ctypes.c_double(0.0)
+        hist = np.zeros(max(int(max_iters), 1))
+        rc = self._lib.od_source_iterate_mg(self._h, G, _ptr(sig), _ptr(ss), _ptr(q), _ptr(inf), _ptr(w),
+                                            float(tol), int(max_iters), _ptr(phi), ctypes.byref(it),
+                                            ctypes.byref(res), _ptr(hist), int(nthreads))
+        if rc not in (OD_OK, OD_NOT_CONVERGED):
+            raise RuntimeError(f"oracle multigroup source iteration failed ({rc})")
         return phi, int(it.value), float(res.value), rc == OD_OK, hist[: it.value]
 
 

@@ -138,3 +138,29 @@ def si_fixed_point(mesh, dirs, weights, sigma_t, c_ratio, q, inflow=None):
             rhs = rhs + B @ inflow
         f += weights[m] * Ainv @ rhs
     return np.linalg.solve(np.eye(N) - K, f)
+
+
+def mg_fixed_point(mesh, dirs, weights, sigma_t, sigma_s, q, inflow=None):
+    """Converged multigroup scalar flux as one dense block solve.
+
+    phi_g = sum_m w_m A_{m,g}^{-1} (V (sum_h sigma_s[h, g] phi_h + q_g) / (4 pi)
+                                     + B_m inflow_g)
+    with A_{m,g} the step-scheme matrix of direction m for sigma_t[g].
+    """
+    N = mesh["n_cells"]
+    G = sigma_t.shape[0]
+    V = mesh["volumes"]
+    K = np.zeros((G * N, G * N))
+    f = np.zeros(G * N)
+    for g in range(G):
+        for m in range(dirs.shape[0]):
+            A, B = transport_matrix(mesh, dirs[m], sigma_t[g])
+            Ainv = np.linalg.inv(A)
+            for h in range(G):
+                K[g * N:(g + 1) * N, h * N:(h + 1) * N] += (
+                    weights[m] * Ainv @ np.diag(V * sigma_s[h, g] / (4 * np.pi)))
+            rhs = V * q[g] / (4 * np.pi)
+            if inflow is not None:
+                rhs = rhs + B @ inflow[g]
+            f[g * N:(g + 1) * N] += weights[m] * Ainv @ rhs
+    return np.linalg.solve(np.eye(G * N) - K, f).reshape(G, N)
