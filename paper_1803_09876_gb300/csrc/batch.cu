@@ -1,13 +1,17 @@
 // Batches: many independent source-iteration problems advanced together.
 //
 // Sec. V-B keeps every angle of a patch in flight at once; here the same idea
-// spans problems.  One iteration of a batch is five launches over all active
-// problems, replayed from a CUDA graph:
-//   k_emission_batch   source records S V (scattering + fixed source) and sigma_t V
-//   k_sweep_dd_batch   data-driven sweep of every (problem, direction), one launch
-//   k_lag_update_batch lagged upwind values for the next sweep (cycle breaking)
-//   k_phi_resid_batch  phi = sum_m w_m psi_m and the FP64 residual accumulators
-//   k_advance          each problem's convergence test, iteration count, epoch
+// spans problems.  One iteration of a batch is a handful of launches over all
+// active problems, replayed from a CUDA graph:
+//   k_emission_batch    source records S V (scattering + fixed source) and sigma_t V
+//   k_sweep_level_batch level-synchronous sweep, one launch per merged slot (reading
+//                       the handles' face-coefficient streams when they all have one
+//                       face-slot count), or
+//   k_sweep_dd_batch    data-driven sweep of every (problem, direction), one launch
+//   k_lag_update_batch  lagged upwind values for the next sweep (cycle breaking)
+//   k_phi_resid_batch   phi = sum_m w_m psi_m and the FP64 residual accumulators
+//   k_advance           each problem's convergence test, iteration count, epoch
+//   k_deliver_batch     phi of the problems that finished into the callers' arrays
 // Each problem owns its workspaces (psi, epoch flags, source records, lagged
 // values, phi ping-pong), so problems that share a mesh and its graphs (one
 // handle) are independent.  The per-cell solve and the phi reduction are the

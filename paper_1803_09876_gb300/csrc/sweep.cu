@@ -9,7 +9,14 @@
 // together):
 //   level-synchronous: one launch per schedule slot covering that slot's
 //     layers of all directions; the launches are captured once into a CUDA
-//     graph and replayed.
+//     graph and replayed, each slot starting early (programmatic dependent
+//     launch) and waiting only before its upwind reads.  By default the slot
+//     kernel (k_sweep_level_coef) reads each cell-direction's face
+//     coefficients (Omega.A per face slot and the upwind ids) from a stream
+//     laid out in sweep order (k_coef_fill, once per handle); k_sweep_level
+//     computes them from the cell geometry instead (no_face_stream).  With
+//     tail_units, the last small slots run as one persistent launch
+//     (k_sweep_tail) with per-direction completion counters.
 //   data-driven (persistent): one launch of resident warps; unit t of the
 //     slot-ordered table goes to warp t mod W, and each cell waits (bounded
 //     spin, acquire) for its own upwind cells' epoch flags, then releases its
@@ -21,7 +28,8 @@
 //
 // Layouts: psi [N][M][R] (cell-major: a cell's directions are contiguous, the
 // R right-hand sides of one cell-direction form one 16/32-byte piece), source
-// records [N][RS] (S V of each rhs, then sigma_t V), lagged values [T][R].
+// records [N][RS] (S V of each rhs, then sigma_t V), lagged values [T][R],
+// face-coefficient records [M][N] in sweep order (coef_record_bytes each).
 #include <climits>
 #include <cmath>
 #include <cstring>

@@ -1,6 +1,10 @@
 // Device code shared by the single-problem sweeps (sweep.cu) and the batched
 // sweeps (batch.cu): the argument block of one problem, cached/uncached vector
-// loads, the per-cell upwind solve and the warp reduction of phi.
+// loads, the per-cell upwind solve (from the cell geometry, solve_cell, or
+// from a face-coefficient record, solve_cell_coef) and the warp reduction of
+// phi.  Every floating-point step that two kernels share is written with
+// explicitly rounded operations, so all schedules, batches and right-hand-side
+// counts give the same bits.
 #pragma once
 
 #include <climits>
