@@ -16,6 +16,12 @@ L2 flush is needed between steps.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on a bounded sample of the same workload on the host cores.
+
+Other workloads (--workload): batch (256 independent tet problems, batched
+against one-at-a-time), serve (a Poisson request stream, served against one
+at a time), wl1 / wl2 (workloads 1 and 2 per solve), mg (multigroup source
+iteration, 4 groups on workload 2's mesh and directions).  --sweeps K only
+runs K plain sweeps of the default workload (a profiling aid).
 """
 
 from __future__ import annotations
@@ -62,7 +68,7 @@ def parse():
                         "(0 = none, the default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve", "wl1", "wl2"],
+    p.add_argument("--workload", default="hex128", choices=["hex128", "batch", "serve", "wl1", "wl2", "mg"],
                    help="hex128: the single large problem (default line); batch: 256 independent tet problems "
                         "in one persistent launch per iteration; serve: Poisson request stream through the "
                         "continuous-batching server; wl1: 16^3 hex FP64 source iteration to 1e-8 (launch-bound: "
@@ -824,6 +830,123 @@ def run_small(args):
     print(json.dumps(line), flush=True)
 
 
+MG_GROUPS = 4
+MG_WORKLOAD = "tet48x6_128dirs_4groups_fp32_si_tol1e-6"
+
+
+def mg_workload():
+    """Workload 2's mesh and directions (48^3 x 6 tets, 128 directions) with 4
+    energy groups: seeded materials (inputs.multigroup_materials, seed 202) and
+    a uniform random source per group (seed 2002)."""
+    import numpy as np
+
+    from inputs import make_workload, multigroup_materials
+
+    wl = make_workload(2)
+    N = wl["n_cells"]
+    sig, ss = multigroup_materials(N, MG_GROUPS, seed=202)
+    q = np.random.default_rng(2002).uniform(0.0, 1.0, (MG_GROUPS, N))
+    return wl, sig, ss, q
+
+
+def run_mg(args):
+    """Multigroup source iteration (jsweep_source_iterate_mg), FP32, tol 1e-6:
+    one step = DAG build + iteration from phi = 0, timed on the device.
+    Value = iterations x cells x directions x groups / time."""
+    import torch
+
+    from paper_1803_09876_gb300 import build as libbuild
+    from paper_1803_09876_gb300 import jsweep as J
+
+    libbuild.build()
+    J.load()
+    J.use_torch_allocator()
+    wl, sig_np, ss_np, q_np = mg_workload()
+    N, G = wl["n_cells"], MG_GROUPS
+    dirs, w = J.jsweep_quadrature_product(*wl["spec"]["quad"])
+    M = len(dirs)
+    mesh = J.mesh_from_dict(wl)
+    quad = J.jsweep_quadrature_create(dirs, w)
+    opt = J.jsweep_options_default(sweep_mode=args.mode, no_face_stream=int(args.no_face_stream))
+    dt = torch.float32
+    sig = torch.as_tensor(sig_np, dtype=dt, device="cuda").contiguous()
+    ss = torch.as_tensor(ss_np, dtype=dt, device="cuda").contiguous()
+    q = torch.as_tensor(q_np, dtype=dt, device="cuda").contiguous()
+    phi = torch.empty((G, N), dtype=dt, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g = J.jsweep_build_dags(mesh, quad, opt)
+        _, it, _, _ = J.jsweep_source_iterate_mg(g, sig, ss, q, tol=1e-6, max_iters=2000, phi_out=phi)
+        return g, it
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, build_ms = 0, 0.0
+    for _ in range(args.steps):
+        g, it = step()
+        iters += it
+        build_ms += g.timing()["build_ms"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    unit = "cell-angle-group updates/s"
+    value = iters * N * M * G / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": MG_WORKLOAD, "cells": N, "directions": M,
+                       "groups": G, "sweep_mode": args.mode, "si_iterations_per_step": iters / args.steps,
+                       "groups_swept": "one after the other, each a single-rhs sweep"},
+            "phases_ms": {"dag_build_mean": build_ms / args.steps,
+                          "source_iteration_mean": ms / args.steps - build_ms / args.steps}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_mg(args):
+    """The oracle's multigroup iteration on a bounded sample of the multigroup
+    workload: per step, the DAG build of a subset of the directions and one
+    iteration (all groups) over them, on all host threads."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    wl, sig, ss, q = mg_workload()
+    N, G = wl["n_cells"], MG_GROUPS
+    dirs, w = oracle.product_quadrature(*wl["spec"]["quad"])
+    nt = oracle.max_threads()
+    nd = max(2, min(len(dirs), nt))
+
+    def sample():
+        t0 = time.perf_counter()
+        o = oracle.build_dags(wl, dirs[:nd])
+        o.multigroup_source_iterate(sig, ss, q, w[:nd], 0.0, 1, nthreads=nt)
+        return N * nd * G, time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        sample()
+    tot_u, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        u, sec = sample()
+        tot_u += u
+        tot_s += sec
+    value = tot_u / tot_s
+    unit = "cell-angle-group updates/s"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": MG_WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": nt, "kind": "oracle",
+                             "sample": f"per step: oracle DAG build of {nd} of {len(dirs)} directions and one "
+                                       f"{G}-group iteration over them, full {N}-cell mesh, {nt} OpenMP threads"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_sweeps(args):
     """Build the graphs of the workload once, then args.sweeps plain sweeps
     (the launch sequence the per-kernel ncu captures in profiles/ skip into)."""
@@ -864,6 +987,8 @@ def main():
     if args.impl == "reference":
         if args.workload == "hex128":
             run_reference(args)
+        elif args.workload == "mg":
+            run_reference_mg(args)
         else:
             run_reference_batch(args)
     elif args.workload == "batch":
@@ -872,6 +997,8 @@ def main():
         run_serve(args)
     elif args.workload in ("wl1", "wl2"):
         run_small(args)
+    elif args.workload == "mg":
+        run_mg(args)
     else:
         run_gpu(args)
 

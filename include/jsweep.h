@@ -277,6 +277,25 @@ JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision
                           int max_iters, void *phi_out, int *iters_out, double *resid_out,
                           void *stream);
 
+/* ---- multigroup source iteration (the appendix's transport equation over
+ * energy groups g and its source-iteration algorithm) -------------------------
+ * phi^0 = 0, lagged values 0; repeat { S_g = (sum_h sigma_s[h][g] phi_h + q_g)
+ * / (4 pi) for every group from the previous iterate of all groups; one sweep
+ * per group with sigma_t[g] and the group's own lagged values; residual as in
+ * jsweep_source_iterate, per group } until every group's residual < tol.
+ *   n_groups G in 1..8; sigma_t [G][n_cells]; sigma_s [G][G][n_cells] with
+ *   entry [h][g][c] the isotropic scattering rate from group h into group g in
+ *   cell c (up- and downscatter allowed); q [G][n_cells] (total isotropic
+ *   source); inflow [G][n_bfaces] or NULL for vacuum; phi_out [G][n_cells].
+ *   All arrays are device arrays of the given precision.
+ *   iters_out, resid_out (host, may be NULL): iterations, final residual.
+ * Leaves the handle's lagged values at 0 (see jsweep_sweep).
+ * Returns JSWEEP_ERR_NOT_CONVERGED (phi_out filled) after max_iters
+ * iterations, JSWEEP_ERR_INVALID_ARG for a NULL array or G outside 1..8. */
+JSWEEP_API int jsweep_source_iterate_mg(jsweep_dags_t dags, int n_groups, int precision, const void *sigma_t,
+                             const void *sigma_s, const void *q, const void *inflow, double tol,
+                             int max_iters, void *phi_out, int *iters_out, double *resid_out, void *stream);
+
 /* ---- batches: many independent problems in one persistent launch ----------
  * Sec. V-B runs the (patch, angle) programs of all angles at once; a batch
  * extends that to many independent problems (meshes, direction sets,

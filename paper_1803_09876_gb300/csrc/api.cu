@@ -746,4 +746,28 @@ int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const voi
     return rc;
 }
 
+int jsweep_source_iterate_mg(jsweep_dags_t dags, int n_groups, int precision, const void *sigma_t,
+                             const void *sigma_s, const void *q, const void *inflow, double tol, int max_iters,
+                             void *phi_out, int *iters_out, double *resid_out, void *stream) {
+    clear_error();
+    if (!dags || !sigma_t || !sigma_s || !q || !phi_out) {
+        set_error("jsweep_source_iterate_mg: NULL argument");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    if (n_groups < 1 || n_groups > 8) {
+        set_error("jsweep_source_iterate_mg: n_groups=%d outside 1..8", n_groups);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    JS_TRY(check_prec(1, precision));
+    if (!(tol >= 0.0) || max_iters < 1) {
+        set_error("jsweep_source_iterate_mg: tol=%g max_iters=%d", tol, max_iters);
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    const int64_t l0 = g_kernel_launches.load();
+    int rc = run_source_iteration_mg(impl(dags), n_groups, precision, sigma_t, sigma_s, q, inflow, tol, max_iters,
+                                     phi_out, iters_out, resid_out, (cudaStream_t)stream);
+    impl(dags)->timing.call_launches = g_kernel_launches.load() - l0;
+    return rc;
+}
+
 }  // extern "C"

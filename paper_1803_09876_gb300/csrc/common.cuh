@@ -231,6 +231,9 @@ int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_
 int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio,
                          const void *q, const void *inflow, double tol, int max_iters,
                          void *phi_out, int *iters_out, double *resid_out, cudaStream_t s);
+int run_source_iteration_mg(Dags *d, int n_groups, int prec, const void *sigma_t, const void *sigma_s,
+                            const void *q, const void *inflow, double tol, int max_iters, void *phi_out,
+                            int *iters_out, double *resid_out, cudaStream_t s);
 
 // shared device helpers
 int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);

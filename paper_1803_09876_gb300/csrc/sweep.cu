@@ -388,6 +388,24 @@ __global__ void k_emission(const T *sig, const T *cr, const T *q, const T *phi, 
     }
 }
 
+// Multigroup scattering source (the multigroup transport equation of the
+// appendix, Alg. 1 step 2.1): every group's angular source from the previous
+// iterate of all groups, S_g = (sum_h sigma_s[h][g] phi_h + q_g) / (4 pi),
+// h in increasing order.  sigma_s [G][G][N] ([h][g]: rate from group h into
+// group g), q and src [G][N], phi [G][N] or null (phi = 0).
+template <class T>
+__global__ void k_emission_mg(const T *sigma_s, const T *q, const T *phi, int64_t N, int G, T *src) {
+    const T four_pi = T(4.0 * 3.141592653589793);
+    const int64_t total = (int64_t)G * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = i / N, c = i - g * N;
+        T sum = T(0);
+        if (phi)
+            for (int h = 0; h < G; ++h) sum = fma_rn(sigma_s[((int64_t)h * G + g) * N + c], phi[(int64_t)h * N + c], sum);
+        src[i] = add_rn(sum, q[i]) / four_pi;
+    }
+}
+
 // Angular source given directly: records of S V and sigma_t V.
 template <class T, int R>
 __global__ void k_source_prep(const T *sig, const T *src, const T *vol, int64_t N, int nrhs, T *srcv) {
@@ -1158,6 +1176,114 @@ static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio,
         return JSWEEP_ERR_NOT_CONVERGED;
     }
     return JSWEEP_OK;
+}
+
+// Multigroup source iteration (the appendix's transport equation over energy
+// groups, Alg. 1): phi^0 = 0; each iteration forms every group's source from
+// the previous iterate of all groups (k_emission_mg), then sweeps the groups
+// one after the other as single-rhs sweeps with their own sigma_t, and stops
+// when every group's relative max-norm change is below tol.  The groups share
+// the handle's psi, source-record, inflow and lagged-value buffers (so the
+// captured level-synchronous graph serves all of them): a group's inflow and
+// lagged values are copied in before its sweep and its lagged values copied
+// out after it.
+template <class T>
+static int run_si_mg_t(Dags *d, int G, const void *sigma_t, const void *sigma_s, const void *q, const void *inflow,
+                       double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
+    const int mode = resolve_mode(d);
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, 1>(), s, patch_warps<T, 1>(d, mode)));
+    JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, 1, 1, s));
+    const int64_t N = d->N, Fb = d->mesh->Fb, Tl = d->T;
+    const size_t es = sizeof(T);
+    const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
+                                  : reinterpret_cast<const T *>(d->mesh->vol32.p);
+    const T *w = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->quad->w64.p)
+                                : reinterpret_cast<const T *>(d->quad->w32.p);
+    const double *d64 = nullptr;
+    if (sizeof(T) == 8) JS_TRY(dirs64x4(d, s, &d64));
+    DevBuf src_d, phi_d0, phi_d1, lag_d;
+    // the loop runs in a lambda so that every exit, error or not, waits for the
+    // stream before the local buffers above are released
+    const int rc = [&]() -> int {
+        JS_TRY(src_d.alloc((size_t)G * N * es, s));
+        JS_TRY(phi_d0.alloc((size_t)G * N * es, s));
+        JS_TRY(phi_d1.alloc((size_t)G * N * es, s));
+        JS_TRY(lag_d.alloc((size_t)G * std::max<int64_t>(Tl, 1) * es, s));
+        JS_CUDA(cudaMemsetAsync(lag_d.p, 0, lag_d.bytes, s));
+        const bool has_inflow = inflow != nullptr;
+        T *bufs[2] = {phi_d0.as<T>(), phi_d1.as<T>()};
+        T *phi_old = nullptr;  // phi^0 = 0
+        T *phi_new = bufs[0];
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(d->red.p);
+        double *resid_d = reinterpret_cast<double *>(acc + 32);
+        double resid_h[9] = {0};
+        int it = 0;
+        bool conv = false;
+        for (it = 1; it <= max_iters; ++it) {
+            phi_new = bufs[(it - 1) & 1];
+            k_emission_mg<T><<<grid_for((int64_t)G * N, 256, 152 * 16), 256, 0, s>>>(
+                (const T *)sigma_s, (const T *)q, phi_old, N, G, src_d.as<T>());
+            JS_LAUNCH_CHECK();
+            for (int g = 0; g < G; ++g) {
+                k_source_prep<T, 1><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(
+                    (const T *)sigma_t + (int64_t)g * N, src_d.as<T>() + (int64_t)g * N, vol, N, 1, d->srcv.as<T>());
+                JS_LAUNCH_CHECK();
+                if (has_inflow && Fb > 0)
+                    JS_CUDA(cudaMemcpyAsync(d->inflow.p, (const T *)inflow + (int64_t)g * Fb, (size_t)Fb * es,
+                                            cudaMemcpyDeviceToDevice, s));
+                if (Tl > 0)
+                    JS_CUDA(cudaMemcpyAsync(d->psi_lag.p, lag_d.as<T>() + (int64_t)g * Tl, (size_t)Tl * es,
+                                            cudaMemcpyDeviceToDevice, s));
+                JS_TRY((one_sweep<T, 1>(d, mode, has_inflow, w, phi_new + (int64_t)g * N, 1, s, (const T *)d64)));
+                JS_TRY(check_sweep_error(d, s, mode));  // the next group's launch clears the error flag
+                if (Tl > 0)
+                    JS_CUDA(cudaMemcpyAsync(lag_d.as<T>() + (int64_t)g * Tl, d->psi_lag.p, (size_t)Tl * es,
+                                            cudaMemcpyDeviceToDevice, s));
+            }
+            JS_CUDA(cudaMemsetAsync(acc, 0, 2 * 8 * 8, s));
+            k_resid<T><<<dim3(grid_for(N, 256, 152 * 4), G), 256, 0, s>>>(phi_new, phi_old, N, acc);
+            JS_LAUNCH_CHECK();
+            k_resid_final<<<1, 32, 0, s>>>(acc, G, resid_d);
+            JS_LAUNCH_CHECK();
+            JS_CUDA(cudaMemcpyAsync(resid_h, resid_d, (size_t)(G + 1) * 8, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaStreamSynchronize(s));
+            phi_old = phi_new;
+            if (resid_h[G] < tol) {
+                conv = true;
+                break;
+            }
+        }
+        if (it > max_iters) it = max_iters;
+        JS_CUDA(cudaMemcpyAsync(phi_out, phi_new, (size_t)G * N * es, cudaMemcpyDeviceToDevice, s));
+        // the handle's lagged values belonged to the last group: start later sweeps from 0
+        JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
+        JS_CUDA(cudaStreamSynchronize(s));
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, d->ev[0], d->ev[1]);
+        cudaEventElapsedTime(&b, d->ev[2], d->ev[3]);
+        d->timing.sweep_ms = a;
+        d->timing.phi_ms = b;
+        if (iters_out) *iters_out = it;
+        if (resid_out) *resid_out = resid_h[G];
+        if (!conv) {
+            set_error("multigroup source iteration did not reach tol %g in %d iterations (residual %g)", tol,
+                      max_iters, resid_h[G]);
+            return JSWEEP_ERR_NOT_CONVERGED;
+        }
+        return JSWEEP_OK;
+    }();
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+int run_source_iteration_mg(Dags *d, int n_groups, int prec, const void *sigma_t, const void *sigma_s,
+                            const void *q, const void *inflow, double tol, int max_iters, void *phi_out,
+                            int *iters_out, double *resid_out, cudaStream_t s) {
+    if (prec == JSWEEP_F64)
+        return run_si_mg_t<double>(d, n_groups, sigma_t, sigma_s, q, inflow, tol, max_iters, phi_out, iters_out,
+                                   resid_out, s);
+    return run_si_mg_t<float>(d, n_groups, sigma_t, sigma_s, q, inflow, tol, max_iters, phi_out, iters_out,
+                              resid_out, s);
 }
 
 int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source, const void *inflow,

@@ -56,7 +56,7 @@ EXPORTED = [
     "jsweep_build_dags", "jsweep_dags_destroy", "jsweep_dags_info", "jsweep_dags_nlevels",
     "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
     "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
-    "jsweep_source_iterate_noalloc",
+    "jsweep_source_iterate_noalloc", "jsweep_source_iterate_mg",
     "jsweep_batch_create", "jsweep_batch_problem_bytes", "jsweep_batch_add", "jsweep_batch_step",
     "jsweep_batch_launch", "jsweep_batch_poll",
     "jsweep_batch_query", "jsweep_batch_remove", "jsweep_batch_clear", "jsweep_batch_size",
@@ -172,6 +172,7 @@ def load(path: str = LIB_PATH):
             "jsweep_source_iterate": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
             "jsweep_dags_timing": (I, [P, P]),
             "jsweep_source_iterate_noalloc": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
+            "jsweep_source_iterate_mg": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
             "jsweep_batch_create": (I, [I, I, P, P]),
             "jsweep_batch_problem_bytes": (I, [P, P, I, P]),
             "jsweep_batch_add": (I, [P, P, P, P, P, P, P, ctypes.c_double, I, P, P]),
@@ -452,6 +453,31 @@ def jsweep_source_iterate(dags: Dags, sigma_t, c_ratio, q, inflow=None, tol=1e-8
     if rc == JSWEEP_ERR_NOT_CONVERGED and allow_not_converged:
         return phi_out, it.value, res.value, False
     _check(rc, "jsweep_source_iterate")
+    return phi_out, it.value, res.value, True
+
+
+def jsweep_source_iterate_mg(dags: Dags, sigma_t, sigma_s, q, inflow=None, tol=1e-8, max_iters=1000,
+                             phi_out=None, stream=None, allow_not_converged=False):
+    """Multigroup source iteration from phi = 0: sigma_t [G, N], sigma_s [G, G, N]
+    ([h, g]: rate from group h into group g), q [G, N], inflow [G, n_bfaces] or
+    None.  Returns (phi [G, N], iterations, residual, converged)."""
+    import torch
+    N, Fb = dags.n_cells, dags.mesh.n_bfaces
+    G = q.shape[0] if q.dim() == 2 else 1
+    dt = q.dtype
+    prec = _prec(dt)
+    if phi_out is None:
+        phi_out = torch.empty((G, N), dtype=dt, device=q.device)
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    rc = lib().jsweep_source_iterate_mg(dags._h, G, prec, _dptr(sigma_t, dt, G * N, "sigma_t"),
+                                        _dptr(sigma_s, dt, G * G * N, "sigma_s"), _dptr(q, dt, G * N, "q"),
+                                        _dptr(inflow, dt, G * Fb, "inflow"), float(tol), int(max_iters),
+                                        _dptr(phi_out, dt, G * N, "phi_out"), ctypes.byref(it), ctypes.byref(res),
+                                        _stream(stream))
+    if rc == JSWEEP_ERR_NOT_CONVERGED and allow_not_converged:
+        return phi_out, it.value, res.value, False
+    _check(rc, "jsweep_source_iterate_mg")
     return phi_out, it.value, res.value, True
 
 

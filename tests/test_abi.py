@@ -75,6 +75,27 @@ def test_error_message_is_thread_local_and_cleared(lib):
     assert lib.jsweep_last_error() == b""
 
 
+def test_multigroup_host_side_errors(lib):
+    # argument checks of jsweep_source_iterate_mg return before any device work
+    P = ctypes.c_void_p
+    fake = P(16)  # never dereferenced: every call below fails its argument checks first
+    f = lib.jsweep_source_iterate_mg
+    assert f(None, 4, J.JSWEEP_F32, fake, fake, fake, None, 1e-6, 10, fake, None, None, None) == \
+        J.JSWEEP_ERR_INVALID_ARG
+    assert b"NULL argument" in lib.jsweep_last_error()
+    assert f(fake, 4, J.JSWEEP_F32, fake, None, fake, None, 1e-6, 10, fake, None, None, None) == \
+        J.JSWEEP_ERR_INVALID_ARG
+    for G in (0, 9):
+        assert f(fake, G, J.JSWEEP_F32, fake, fake, fake, None, 1e-6, 10, fake, None, None, None) == \
+            J.JSWEEP_ERR_INVALID_ARG
+        assert b"n_groups" in lib.jsweep_last_error()
+    assert f(fake, 4, 7, fake, fake, fake, None, 1e-6, 10, fake, None, None, None) == J.JSWEEP_ERR_INVALID_ARG
+    assert f(fake, 4, J.JSWEEP_F64, fake, fake, fake, None, -1.0, 10, fake, None, None, None) == \
+        J.JSWEEP_ERR_INVALID_ARG
+    assert f(fake, 4, J.JSWEEP_F64, fake, fake, fake, None, 1e-6, 0, fake, None, None, None) == \
+        J.JSWEEP_ERR_INVALID_ARG
+
+
 def test_batch_host_side_errors(lib):
     # host-only paths of the batch entry points (no device work is queued)
     P = ctypes.c_void_p
