@@ -29,7 +29,7 @@ def test_multigroup_fixed_iterations_match_oracle(prec, mode):
     import torch
     dt = torch.float64 if prec == "f64" else torch.float32
     mesh = hex_grid(5, 0.3, 11)  # cyclic: lagged faces, kept per group
-    dirs, w, o, sig, ss, q, inflow = _case(mesh, (2, 3), 4, 40, True)
+    dirs, w, o, sig, ss, q, inflow = _case(mesh, (3, 4), 4, 40, True)
     assert o.n_lag_total > 0
     g = build(mesh, dirs, w, sweep_mode=mode)
     for k in (1, 6):
