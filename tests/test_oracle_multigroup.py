@@ -95,3 +95,16 @@ def test_converged_multigroup_equals_dense_block_solve(mesh_fn):
     if mesh["n_cells"] == 4:
         assert g.n_lag_total > 0
     assert np.all(np.diff(hist[:5]) < 0)  # contraction from phi = 0
+
+
+def test_multigroup_materials_are_seeded_and_subcritical_per_group():
+    sig, ss = multigroup_materials(500, 4, seed=3, upscatter=0.1)
+    sig2, ss2 = multigroup_materials(500, 4, seed=3, upscatter=0.1)
+    assert np.array_equal(sig, sig2) and np.array_equal(ss, ss2)
+    assert sig.shape == (4, 500) and ss.shape == (4, 4, 500)
+    assert np.all(sig > 0) and np.all(ss >= 0)
+    out = ss.sum(axis=1)  # all scattering out of each group
+    assert np.all(out < sig) and np.all(out >= 0.3 * sig - 1e-12)
+    # mostly downscatter: each group sends less to the groups above it than to itself and below
+    for g in range(4):
+        assert np.all(ss[g, :g].sum(axis=0) < ss[g, g:].sum(axis=0))
