@@ -138,7 +138,8 @@ typedef struct {
                               (Omega.A per face and the upwind neighbours, one record per cell-direction in
                               sweep order, built at the handle's first such sweep: N x M x 32..96 bytes) as
                               a sequential stream; nonzero computes them from the cell geometry in the
-                              sweep.  Results are bit-identical either way. */
+                              sweep.  Results are bit-identical either way.  Once built, the stream stays
+                              with the handle until it is destroyed (batches on the handle may read it). */
     int tail_units;        /* level-synchronous sweeps with the face stream: > 0 runs the last slots that
                               each hold fewer than this many work units as one persistent launch (the
                               tail: warps take units in slot order, per-direction completion counters and
