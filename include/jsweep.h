@@ -140,12 +140,11 @@ typedef struct {
                               a sequential stream; nonzero computes them from the cell geometry in the
                               sweep.  Results are bit-identical either way.  Once built, the stream stays
                               with the handle until it is destroyed (batches on the handle may read it). */
-    int tail_units;        /* level-synchronous sweeps with the face stream: > 0 runs the last slots that
-                              each hold fewer than this many work units as one persistent launch (the
-                              tail: warps take units in slot order, per-direction completion counters and
-                              bounded waits replace the launch boundaries) instead of one launch per
-                              slot; 0 (default) = no tail.  Results are bit-identical.  Measured slower
-                              than per-slot launches on every workload tried; kept as an option. */
+    int tail_units;        /* level-synchronous sweeps with the face stream and JSWEEP_PRIO_LEVEL: > 0 runs
+                              the last slots that each hold fewer than this many work units in one launch
+                              of one block per direction (the tail), each block sweeping its direction's
+                              remaining layers in order with a block barrier between layers, instead of
+                              one launch per slot; 0 (default) = no tail.  Results are bit-identical. */
     int reserved[1];
 } jsweep_options;
 

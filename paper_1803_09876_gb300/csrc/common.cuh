@@ -196,9 +196,9 @@ struct Dags {
         const void *dirs = nullptr;
         bool failed = false;             // allocation refused: sweeps read the cell geometry
     } coef[2];
-    // tail of the level-synchronous sweep (persistent launch of the last, small slots)
-    DevBuf tail_pre;         // int32 [M]: units of each direction that run before the tail
-    int64_t tail_t0 = -1;    // first tail unit of the captured graph (-1: no tail)
+    // tail of the level-synchronous sweep (the last, small slots: one block per direction)
+    DevBuf tail_lpoff;       // int64 [M+1]: device copy of sp_off
+    DevBuf tail_nlev;        // int32 [M]: device copy of slayers
     UnitTable ut;
     std::unique_ptr<PatchSched> ps;  // lazily built (patch programs)
     // CUDA graph of the level-synchronous sweep

@@ -15,8 +15,8 @@
 //     coefficients (Omega.A per face slot and the upwind ids) from a stream
 //     laid out in sweep order (k_coef_fill, once per handle); k_sweep_level
 //     computes them from the cell geometry instead (no_face_stream).  With
-//     tail_units, the last small slots run as one persistent launch
-//     (k_sweep_tail) with per-direction completion counters.
+//     tail_units, the last small slots run in one launch of one block per
+//     direction (k_sweep_tail), layer after layer.
 //   data-driven (persistent): one launch of resident warps; unit t of the
 //     slot-ordered table goes to warp t mod W, and each cell waits (bounded
 //     spin, acquire) for its own upwind cells' epoch flags, then releases its
@@ -83,69 +83,34 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
 }
 
-// The tail of a level-synchronous sweep: the last slots, too small to fill the
-// GPU, run in one persistent launch instead of one launch each.  Warps take
-// tail units in slot order from a shared counter (*next), each taking its next
-// unit before it solves the current one.  done[m] counts the finished tail
-// units of direction m; a unit of direction m needs the units of m's earlier
-// layers: u.w of them in all, pre[m] of which ran before the tail (before this
-// launch), so it waits until done[m] >= u.w - pre[m].  A unit only finishes
-// after its own wait, so once done[m] reaches that count every earlier layer
-// is complete.  Every unit a warp holds has its producers at smaller indices,
-// taken earlier by running warps, so the smallest unfinished unit can always
-// proceed: the launch cannot deadlock even when only part of the grid is
-// resident.  Waits are bounded (timeout in clock cycles, error flag *err).
+// The tail of a level-synchronous sweep, one block per direction: the last
+// slots, each too small to fill the GPU, are swept by block m for direction m,
+// layer after layer with a block barrier between layers, instead of by one
+// launch per slot.  A layer depends only on earlier layers of its own
+// direction (the per-direction dependency graph), so the blocks never wait for
+// one another; the layers before first_layer were swept by the slot launches
+// that precede this one.
 template <class T, int R, int SPLIT, int MAXF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_sweep_tail(SweepArgs<T> a, int64_t t0, int64_t nt, const unsigned char *coef, const int *pre,
-                 int *done, int *next, int *err, long long timeout, int debug_extra) {
+    k_sweep_tail(SweepArgs<T> a, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, int first_layer,
+                 const unsigned char *coef) {
     constexpr int RB = coef_record_bytes<T, MAXF>();
-    const int lane = threadIdx.x & 31;
-    const int cell = lane / SPLIT, sub = lane % SPLIT;
+    constexpr int per_pass = kWarpsPerBlock * 32 / SPLIT;  // cells of a layer solved at once
+    const int m = blockIdx.x;
+    const int cell = threadIdx.x / SPLIT, sub = threadIdx.x % SPLIT;
     const uint64_t pol_stream = l2_evict_first();
-    int t = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 1) : 0, 0);
-    while (t < nt) {
-        const int t_next = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 1) : 0, 0);
-        const int4 u = ldg_hint(a.units + t0 + t, pol_stream);
-        // debug_extra (test hook): one more finished unit than can exist, so every wait runs out
-        const int need = u.w - __ldg(pre + u.x) + debug_extra;
-        const int *cnt = done + u.x;
-        bool ok = true;
-        if (cell < u.z) {
-            const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
-            ok = solve_cell_coef<T, R, SPLIT, MAXF>(
-                a, u.x, ldg_hint(a.order + idx, pol_stream), ldg_hint(a.mask + idx, pol_stream), sub,
-                coef + idx * RB, pol_stream, [&]() -> bool {
-                    pdl_wait_prev();  // the level-synchronous slots before the tail
-                    if (ld_acquire(cnt) >= need) return true;
-                    const long long c0 = clock64();
-                    int ns = 32;
-                    while (ld_acquire(cnt) < need) {
-                        if (ld_volatile(err) != 0) return false;
-                        if (clock64() - c0 > timeout) {
-                            atomicCAS(err, 0, 1);
-                            return false;
-                        }
-                        __nanosleep(ns);
-                        ns = ns < 128 ? 2 * ns : 128;
-                    }
-                    return true;
-                });
+    const int L = nlev[m];
+    const int32_t *lpm = lp + lp_off[m];
+    pdl_wait_prev();  // the slot launches before the tail are complete
+    for (int l = first_layer; l < L; ++l) {
+        const int p1 = lpm[l + 1];
+        for (int p = lpm[l] + cell; p < p1; p += per_pass) {
+            const int64_t idx = (int64_t)m * a.N + p;
+            solve_cell_coef<T, R, SPLIT, MAXF>(a, m, ldg_hint(a.order + idx, pol_stream),
+                                               ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB,
+                                               pol_stream, [] { return true; });
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
-        // the warp's psi stores are ordered before the first lane's release
-        __syncwarp();
-        if (lane == 0) red_release_add(done + u.x, 1);
-        t = t_next;
-    }
-}
-
-// pre[m] = the smallest wait target among direction m's tail units (the units
-// of m that ran before the tail); pre is filled with INT_MAX first.
-__global__ void k_tail_pre(const int4 *units, int64_t nt, int *pre) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
-        const int4 u = units[i];
-        atomicMin(pre + u.x, u.w);
+        __syncthreads();  // this layer's psi is stored before the next layer reads it
     }
 }
 
@@ -820,40 +785,26 @@ template <class T, int R> int64_t patch_warps(const Dags *d, int mode) {
     return (mode == JSWEEP_MODE_PERSISTENT && d->opt.priority == JSWEEP_PRIO_PATCH) ? dd_resident_warps<T, R>(d) : 0;
 }
 
-// Blocks of the tail kernel that can be resident at once.
-template <class T, int R, int SPLIT, int MAXF> int64_t tail_resident_blocks() {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sweep_tail<T, R, SPLIT, MAXF>, kWarpsPerBlock * 32,
-                                                      0) != cudaSuccess)
-        occ = 1;
-    return (int64_t)device_sm_count() * std::max(occ, 1);
-}
-
 // First slot of the tail: the slots from it to the end each hold fewer than
-// tail_units units.  Returns the number of slots when there is no tail.
+// tail_units units.  Returns the number of slots when there is no tail.  Only
+// when slot t is layer t of every direction (JSWEEP_PRIO_LEVEL).
 int64_t tail_slot(const Dags *d) {
     const auto &sp = d->ut.slot_ptr;
     const int64_t Tn = (int64_t)sp.size() - 1;
-    if (d->opt.tail_units <= 0 || Tn <= 0) return std::max<int64_t>(Tn, 0);
+    if (d->opt.tail_units <= 0 || Tn <= 0 || d->ut.priority != JSWEEP_PRIO_LEVEL) return std::max<int64_t>(Tn, 0);
     const int64_t thr = d->opt.tail_units;
     int64_t S = Tn;
     while (S > 0 && sp[S] - sp[S - 1] < thr) --S;
-    while (S < Tn && sp[Tn] - sp[S] > INT32_MAX / 2) ++S;  // the tail's unit counter is 32-bit
     return S;
 }
 
-long long spin_timeout_cycles(const Dags *d) {
-    const int khz = device_clock_khz();
-    return (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
-}
-
 // Records the sweep's launches on the capture stream: one launch per slot
-// before the tail slot S, then (S < number of slots) the persistent tail.
+// before the tail slot S, then (S < number of slots) the tail, one block per
+// direction.
 template <class T, int R, int SPLIT, int MAXF>
 void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsigned char *coef, int64_t S) {
     const auto &sp = d->ut.slot_ptr;
     const int64_t Tn = (int64_t)sp.size() - 1;
-    if (S < Tn) cudaMemsetAsync(d->counters.p, 0, (size_t)(d->M + 8) * 4, cs);  // error flag and done[]
     bool first = true;
     for (int64_t l = 0; l < std::min(S, Tn); ++l) {
         const int64_t nu = sp[l + 1] - sp[l];
@@ -876,11 +827,8 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         else cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
     }
     if (S < Tn) {
-        const int64_t t0 = sp[S], nt = sp[Tn] - sp[S];
-        const int64_t blocks = std::min(tail_resident_blocks<T, R, SPLIT, MAXF>(),
-                                        (nt + kWarpsPerBlock - 1) / kWarpsPerBlock);
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)std::max<int64_t>(blocks, 1));
+        cfg.gridDim = dim3((unsigned)d->M);
         cfg.blockDim = dim3(kWarpsPerBlock * 32);
         cfg.stream = cs;
         cudaLaunchAttribute at[1];
@@ -888,11 +836,9 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = first ? 0 : 1;
-        // counters: [0] error flag, [1] next unit, [8, 8 + M) finished units per direction
-        int *err = reinterpret_cast<int *>(d->counters.p);
-        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF>, a, t0, nt, coef,
-                           (const int *)d->tail_pre.as<int>(), err + 8, err + 1, err, spin_timeout_cycles(d),
-                           d->opt.debug_block_waits ? 1 : 0);
+        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF>, a, (const int32_t *)d->s_lp,
+                           (const int64_t *)d->tail_lpoff.as<int64_t>(), (const int32_t *)d->tail_nlev.as<int32_t>(),
+                           (int)S, coef);
     }
 }
 
@@ -939,26 +885,27 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         const int64_t Tn = (int64_t)d->ut.slot_ptr.size() - 1;
         const int64_t S = coef ? tail_slot(d) : Tn;  // the tail runs on the face stream
         char key[512];
-        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld/%p/%lld/%d", (int)sizeof(T), R,
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld", (int)sizeof(T), R,
                  (const void *)a.srcv, (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
                  (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units, (const void *)coef,
-                 (long long)S, d->counters.p, spin_timeout_cycles(d), d->opt.debug_block_waits);
+                 (long long)S);
         if (!d->graph || d->graph_key != key) {
             if (d->graph) {
                 cudaGraphExecDestroy(d->graph);
                 d->graph = nullptr;
             }
             if (!d->capture_stream) JS_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
-            d->tail_t0 = -1;
             if (S < Tn) {
-                // units of each direction that run before the tail
-                const int64_t t0 = d->ut.slot_ptr[S], nt = d->ut.slot_ptr[Tn] - t0;
-                JS_TRY(d->tail_pre.ensure((size_t)d->M * 4, s));
-                JS_CUDA(cudaMemsetAsync(d->tail_pre.p, 0x7f, (size_t)d->M * 4, s));
-                k_tail_pre<<<grid_for(nt, 256, 152 * 8), 256, 0, s>>>(d->ut.units.as<int4>() + t0, nt,
-                                                                      d->tail_pre.as<int>());
-                JS_LAUNCH_CHECK();
-                d->tail_t0 = t0;
+                // the tail kernel reads each direction's layer pointers and layer count
+                const int64_t M = d->M;
+                std::vector<int32_t> nl32(M);
+                for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)d->slayers[m];
+                JS_TRY(d->tail_lpoff.ensure((size_t)(M + 1) * 8, s));
+                JS_TRY(d->tail_nlev.ensure((size_t)M * 4, s));
+                JS_CUDA(cudaMemcpyAsync(d->tail_lpoff.p, d->sp_off.data(), (size_t)(M + 1) * 8,
+                                        cudaMemcpyHostToDevice, s));
+                JS_CUDA(cudaMemcpyAsync(d->tail_nlev.p, nl32.data(), (size_t)M * 4, cudaMemcpyHostToDevice, s));
+                JS_CUDA(cudaStreamSynchronize(s));
             }
             cudaStream_t cs = d->capture_stream;
             JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -994,16 +941,6 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
 }
 
 int check_sweep_error(Dags *d, cudaStream_t s, int mode) {
-    if (mode == JSWEEP_MODE_LEVEL_SYNC && d->tail_t0 >= 0) {
-        int err = 0;
-        JS_CUDA(cudaMemcpyAsync(&err, d->counters.p, 4, cudaMemcpyDeviceToHost, s));
-        JS_CUDA(cudaStreamSynchronize(s));
-        if (err) {
-            set_error("level-synchronous sweep tail: a dependency wait exceeded %.3g s", d->opt.spin_timeout_s);
-            return JSWEEP_ERR_DEVICE_TIMEOUT;
-        }
-        return JSWEEP_OK;
-    }
     if (mode != JSWEEP_MODE_PERSISTENT && mode != JSWEEP_MODE_PATCH) return JSWEEP_OK;
     if (mode == JSWEEP_MODE_PATCH) JS_TRY(patch_counts(d, s));
     int err = 0;

@@ -177,10 +177,6 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void red_release_add(int *p, int v) {
-    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Per-cell geometry and bookkeeping shared by the sweep kernels.
 template <class T, int MAXF> struct CellGeo {
     typename V4<T>::type g[MAXF];

@@ -236,15 +236,13 @@ def test_workload3_full_size_sampled_psi_and_phi_reduction():
     assert rel_err(phi.double().cpu().numpy(), acc.cpu().numpy()) < 1e-6
 
 
-@pytest.mark.parametrize("mode", [2, 3, 1], ids=["persistent", "patch_programs", "level_sync_tail"])
+@pytest.mark.parametrize("mode", [2, 3], ids=["persistent", "patch_programs"])
 def test_bounded_wait_times_out_and_context_survives(mode):
     torch = _torch()
     js = J()
     mesh = hex_grid(6, 0.15, 1)
     dirs, w = oracle.product_quadrature(1, 3)
-    # level-synchronous: every slot in the persistent tail, whose waits are bounded
-    g = build(mesh, dirs, w, sweep_mode=mode, debug_block_waits=1, spin_timeout_s=0.05, patch_cells=32,
-              tail_units=1 << 30)
+    g = build(mesh, dirs, w, sweep_mode=mode, debug_block_waits=1, spin_timeout_s=0.05, patch_cells=32)
     N = mesh["n_cells"]
     sig = tensor(np.ones(N), torch.float32)
     src = tensor(np.ones((1, N)), torch.float32)
