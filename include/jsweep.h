@@ -277,6 +277,20 @@ JSWEEP_API int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision
                           int max_iters, void *phi_out, int *iters_out, double *resid_out,
                           void *stream);
 
+/* ---- bounds-checked builds ----------------------------------------------------
+ * A build with the flag JSWEEP_BOUNDS_CHECK (libjsweep_bounds.so, see the
+ * package's build script) checks every gather index of the sweep kernels: cell
+ * ids read from the orders, upwind cells, boundary faces, order positions and
+ * directions.  The first index out of range on a device is recorded and its
+ * access skipped (no trap).  Patch programs are not covered.
+ *   jsweep_bounds_checked: 1 in such a build, 0 otherwise (no device work).
+ *   jsweep_bounds_error: waits for the current device, then returns the
+ *   recorded word in *word and clears it: 0 = none, else (code << 56) | index
+ *   with code 1 cell id, 2 upwind cell, 3 boundary face, 4 order position,
+ *   5 direction.  Always 0 in other builds. */
+JSWEEP_API int jsweep_bounds_checked(void);
+JSWEEP_API int jsweep_bounds_error(uint64_t *word);
+
 /* ---- multigroup source iteration (the appendix's transport equation over
  * energy groups g and its source-iteration algorithm) -------------------------
  * phi^0 = 0, lagged values 0; repeat { S_g = (sum_h sigma_s[h][g] phi_h + q_g)

@@ -4,6 +4,11 @@ Each ``csrc/*.cu`` translation unit is compiled in parallel to an object for
 ``sm_103a`` only, then linked into ``paper_1803_09876_gb300/libjsweep.so``
 (static CUDA runtime).  Rebuilds only when a source or header is newer than
 the library.
+
+``build(bounds_check=True)`` builds ``libjsweep_bounds.so`` instead, with the
+flag JSWEEP_BOUNDS_CHECK: every gather index of the sweep kernels is checked,
+and the first one out of range is recorded (jsweep_bounds_error) and skipped.
+It is built on demand, for the debug tests only.
 """
 
 from __future__ import annotations
@@ -21,6 +26,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjsweep.so")
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libjsweep_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", f"-I{INCLUDE}",
@@ -42,23 +49,26 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    if not force and not needs_build():
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, bounds_check: bool = False) -> str:
+    lib_path = LIB_BOUNDS if bounds_check else LIB
+    build_dir = BUILD_BOUNDS if bounds_check else BUILD
+    flags = NVCC_FLAGS + (["-DJSWEEP_BOUNDS_CHECK"] if bounds_check else [])
+    if not force and not needs_build(lib_path):
+        return lib_path
     nvcc = nvcc_path()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
+        cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
         if ptxas_v:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -73,14 +83,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             if log.strip():
                 print(log, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv,
+                bounds_check="--bounds" in sys.argv))

@@ -88,6 +88,30 @@ int device_sm_count() {
     return n > 0 ? n : 1;
 }
 
+// Error word of the bounds-checked build on the current device (8 bytes, zeroed,
+// allocated once per device and kept for the process); nullptr in other builds.
+unsigned long long *bounds_word() {
+#ifdef JSWEEP_BOUNDS_CHECK
+    static std::mutex mu;
+    static unsigned long long *words[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!words[dev]) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, 8) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemset(p, 0, 8);
+        words[dev] = static_cast<unsigned long long *>(p);
+    }
+    return words[dev];
+#else
+    return nullptr;
+#endif
+}
+
 // SM clock (kHz) of the current device, queried once per device: the query is
 // slow enough to show between the events of a short sweep.
 int device_clock_khz() {
@@ -744,6 +768,31 @@ int jsweep_source_iterate(jsweep_dags_t dags, int nrhs, int precision, const voi
                                   max_iters, phi_out, iters_out, resid_out, (cudaStream_t)stream);
     impl(dags)->timing.call_launches = g_kernel_launches.load() - l0;
     return rc;
+}
+
+int jsweep_bounds_checked(void) {
+#ifdef JSWEEP_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int jsweep_bounds_error(uint64_t *word) {
+    clear_error();
+    if (!word) {
+        set_error("jsweep_bounds_error: NULL argument");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    *word = 0;
+    unsigned long long *w = bounds_word();
+    if (!w) return JSWEEP_OK;
+    unsigned long long v = 0;
+    JS_CUDA(cudaDeviceSynchronize());
+    JS_CUDA(cudaMemcpy(&v, w, 8, cudaMemcpyDeviceToHost));
+    JS_CUDA(cudaMemset(w, 0, 8));
+    *word = v;
+    return JSWEEP_OK;
 }
 
 int jsweep_source_iterate_mg(jsweep_dags_t dags, int n_groups, int precision, const void *sigma_t,

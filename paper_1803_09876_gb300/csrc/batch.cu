@@ -101,13 +101,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         if (t < n_units) {
             u = units[t];
             p = uprob[t];
-            if (cell < u.z && S[p].active) {
+            if (cell < u.z && S[p].active && JS_IN_RANGE(P[p].a, u.x, P[p].a.M, 5) &&
+                JS_IN_RANGE(P[p].a, (int64_t)u.y + cell, P[p].a.N, 4)) {
                 const ProbArgs<T> &pp = P[p];
                 epoch = S[p].epoch;
                 const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
                 c = __ldg(pp.a.order + idx);
-                ok = solve_cell<T, R, SPLIT, MAXF, true>(pp.a, u.x, c, __ldg(pp.a.mask + idx), sub, pp.flags,
-                                                         pp.dbg ? epoch + 1 : epoch, err, timeout);
+                if (JS_IN_RANGE(pp.a, c, pp.a.N, 1))
+                    ok = solve_cell<T, R, SPLIT, MAXF, true>(pp.a, u.x, c, __ldg(pp.a.mask + idx), sub, pp.flags,
+                                                             pp.dbg ? epoch + 1 : epoch, err, timeout);
+                else
+                    c = -1;  // bounds-checked builds: a bad cell id is neither solved nor released
             }
         }
         if constexpr (SPLIT == 1) {
@@ -139,7 +143,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         const uint64_t pol_stream = l2_evict_first();
         const int4 u = ldg_hint(units + u0 + t, pol_stream);
         const int p = ldg_hint(uprob + u0 + t, pol_stream);
-        if (cell < u.z && S[p].active) {
+        if (cell < u.z && S[p].active && JS_IN_RANGE(P[p].a, u.x, P[p].a.M, 5) &&
+            JS_IN_RANGE(P[p].a, (int64_t)u.y + cell, P[p].a.N, 4)) {
             const ProbArgs<T> &pp = P[p];
             const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
             solve_cell_coef<T, R, SPLIT, MAXF>(pp.a, u.x, ldg_hint(pp.a.order + idx, pol_stream),
@@ -152,7 +157,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     } else {
         const int4 u = units[u0 + t];
         const int p = uprob[u0 + t];
-        if (cell < u.z && S[p].active) {
+        if (cell < u.z && S[p].active && JS_IN_RANGE(P[p].a, u.x, P[p].a.M, 5) &&
+            JS_IN_RANGE(P[p].a, (int64_t)u.y + cell, P[p].a.N, 4)) {
             const ProbArgs<T> &pp = P[p];
             const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
             solve_cell<T, R, SPLIT, MAXF, false, true>(pp.a, u.x, __ldg(pp.a.order + idx), __ldg(pp.a.mask + idx),
@@ -451,6 +457,7 @@ template <class T> ProbArgs<T> prob_args(const Batch *b, BatchProb &p) {
     a.lag_face = d->lag_face.as<int32_t>();
     a.sface = d->mesh->sface.as<int32_t>();
     a.units = nullptr;
+    a.bounds_err = bounds_word();
     pa.flags = p.flags.as<int>();
     pa.sig = static_cast<const T *>(p.sig);
     pa.cr = static_cast<const T *>(p.cr);

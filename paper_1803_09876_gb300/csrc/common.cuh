@@ -250,6 +250,7 @@ inline int grid_for(int64_t n, int block, int64_t cap = 1 << 20) {
 
 int device_sm_count();
 int device_clock_khz();  // SM clock of the current device (cached)
+unsigned long long *bounds_word();  // error word of the bounds-checked build (nullptr otherwise)
 int check_options(const jsweep_options *opt, jsweep_options *o);
 
 }  // namespace js

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T
     if (t >= nu) return;
     const int4 u = a.units[u0 + t];
     const int cell = lane / SPLIT, sub = lane % SPLIT;
-    if (cell < u.z) {
+    if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
         const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
         solve_cell<T, R, SPLIT, MAXF, false, true>(a, u.x, __ldg(a.order + idx), __ldg(a.mask + idx), sub, nullptr,
                                                    0, nullptr, 0);
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const uint64_t pol_stream = l2_evict_first();
     const int4 u = ldg_hint(a.units + u0 + t, pol_stream);
     const int cell = lane / SPLIT, sub = lane % SPLIT;
-    if (cell < u.z) {
+    if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
         const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
         solve_cell_coef<T, R, SPLIT, MAXF>(a, u.x, ldg_hint(a.order + idx, pol_stream),
                                            ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB, pol_stream, [] {
@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     for (int l = first_layer; l < L; ++l) {
         const int p1 = lpm[l + 1];
         for (int p = lpm[l] + cell; p < p1; p += per_pass) {
+            if (!JS_IN_RANGE(a, p, a.N, 4)) continue;
             const int64_t idx = (int64_t)m * a.N + p;
             solve_cell_coef<T, R, SPLIT, MAXF>(a, m, ldg_hint(a.order + idx, pol_stream),
                                                ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB,
@@ -169,10 +170,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         const int4 u = a.units[t];
         bool ok = true;
         int c = -1;
-        if (cell < u.z) {
+        if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
             const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
             c = __ldg(a.order + idx);
-            ok = solve_cell<T, R, SPLIT, MAXF, true>(a, u.x, c, __ldg(a.mask + idx), sub, flags, want, err, timeout);
+            if (JS_IN_RANGE(a, c, a.N, 1))
+                ok = solve_cell<T, R, SPLIT, MAXF, true>(a, u.x, c, __ldg(a.mask + idx), sub, flags, want, err,
+                                                         timeout);
+            else
+                c = -1;  // bounds-checked builds: a bad cell id is neither solved nor released
         }
         if constexpr (SPLIT == 1) {
             if (c >= 0 && ok) st_release(flags + (int64_t)c * a.M + u.x, epoch);
@@ -686,6 +691,7 @@ template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
     a.lag_face = d->lag_face.as<int32_t>();
     a.sface = d->mesh->sface.as<int32_t>();
     a.units = d->ut.units.as<int4>();
+    a.bounds_err = bounds_word();
     (void)Rp;
     return a;
 }
@@ -1289,6 +1295,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int32_t wid = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int32_t stride = gridDim.x * kWarpsPerBlock * CPW;
     for (int32_t pos = p0 + wid * CPW + cell; pos < p1; pos += stride) {
+        if (!JS_IN_RANGE(a, pos, a.N, 4)) continue;
         const int64_t idx = m * a.N + pos;
         solve_cell<T, R, SPLIT, MAXF, false>(a, (int)m, __ldg(a.order + idx), __ldg(a.mask + idx), sub, nullptr, 0,
                                              nullptr, 0);
@@ -1413,6 +1420,7 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
     a.lag_face = d->lag_face.as<int32_t>();
     a.sface = d->mesh->sface.as<int32_t>();
     a.units = nullptr;
+    a.bounds_err = bounds_word();
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
                                   : reinterpret_cast<const T *>(d->mesh->vol32.p);
     const T *w = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->quad->w64.p)

@@ -34,7 +34,24 @@ template <class T> struct SweepArgs {
     const T *psi_lag; // [Tl][R]
     const int32_t *lag_ptr, *lag_face, *sface;
     const int4 *units;
+    unsigned long long *bounds_err;  // bounds-checked builds: first bad index (else unused)
 };
+
+// Bounds-checked builds (JSWEEP_BOUNDS_CHECK): every gather index of the
+// sweeps is checked; the first one out of range is recorded in *bounds_err as
+// (check code << 56) | index and its access is skipped.  Codes: 1 cell id,
+// 2 upwind cell, 3 boundary face, 4 order position, 5 direction.  In other
+// builds JS_IN_RANGE is the constant true and the checks compile away.
+__device__ __forceinline__ bool in_range(unsigned long long *w, int64_t i, int64_t n, int code) {
+    if (i >= 0 && i < n) return true;
+    if (w) atomicCAS(w, 0ull, ((unsigned long long)code << 56) | ((unsigned long long)i & 0xffffffffffffffull));
+    return false;
+}
+#ifdef JSWEEP_BOUNDS_CHECK
+#define JS_IN_RANGE(args, i, n, code) ::js::dev::in_range((args).bounds_err, (int64_t)(i), (int64_t)(n), (code))
+#else
+#define JS_IN_RANGE(args, i, n, code) true
+#endif
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -201,6 +218,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
                                            const int *flags, int want, int *err, long long timeout) {
     using V = typename V4<T>::type;
     constexpr int RH = R / SPLIT;
+    if (!JS_IN_RANGE(a, c, a.N, 1)) return true;  // bounds-checked builds: skip a bad cell id
     const T ox = a.dirs[4 * m], oy = a.dirs[4 * m + 1], oz = a.dirs[4 * m + 2];
     const V *g = a.geo + (int64_t)c * a.GS;
     V gk[MAXF];
@@ -235,7 +253,7 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
 #pragma unroll
         for (int k = 0; k < MAXF; ++k) {
             const int nb = nbr_bits<T>(gk[k]);
-            if (((msk >> k) & 1u) && !((lagk >> k) & 1u) && nb >= 0) {
+            if (((msk >> k) & 1u) && !((lagk >> k) & 1u) && nb >= 0 && JS_IN_RANGE(a, nb, a.N, 2)) {
                 const int *fp = flags + (int64_t)nb * a.M + m;
                 if (ld_acquire(fp) != want) {
                     const long long t0 = clock64();
@@ -263,14 +281,18 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
             if (nb >= 0) {
                 if ((lagk >> k) & 1u) {
                     load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
-                } else {
+                } else if (JS_IN_RANGE(a, nb, a.N, 2)) {
                     load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RH; ++r) up[r] = T(0);
                 }
             } else {
                 const int b = -nb - 1;
+                const bool inb = JS_IN_RANGE(a, b, a.Fb, 3);
 #pragma unroll
                 for (int r = 0; r < RH; ++r)
-                    up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
+                    up[r] = (a.inflow && inb) ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
             }
 #pragma unroll
             for (int r = 0; r < RH; ++r) num[r] = fma_rn(wf, up[r], num[r]);
@@ -305,6 +327,7 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
                                                 Ready upwind_ready) {
     constexpr int RH = R / SPLIT;
     constexpr int RB = coef_record_bytes<T, MAXF>();
+    if (!JS_IN_RANGE(a, c, a.N, 1)) return true;  // bounds-checked builds: skip a bad cell id
     T dk[MAXF];
     int nbk[MAXF];
     {
@@ -343,14 +366,18 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
             if (nb >= 0) {
                 if ((lagk >> k) & 1u) {
                     load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
-                } else {
+                } else if (JS_IN_RANGE(a, nb, a.N, 2)) {
                     load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RH; ++r) up[r] = T(0);
                 }
             } else {
                 const int b = -nb - 1;
+                const bool inb = JS_IN_RANGE(a, b, a.Fb, 3);
 #pragma unroll
                 for (int r = 0; r < RH; ++r)
-                    up[r] = a.inflow ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
+                    up[r] = (a.inflow && inb) ? a.inflow[(int64_t)(sub * RH + r) * a.Fb + b] : T(0);
             }
 #pragma unroll
             for (int r = 0; r < RH; ++r) num[r] = fma_rn(wf, up[r], num[r]);

@@ -56,7 +56,7 @@ EXPORTED = [
     "jsweep_build_dags", "jsweep_dags_destroy", "jsweep_dags_info", "jsweep_dags_nlevels",
     "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
     "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
-    "jsweep_source_iterate_noalloc", "jsweep_source_iterate_mg",
+    "jsweep_source_iterate_noalloc", "jsweep_source_iterate_mg", "jsweep_bounds_checked", "jsweep_bounds_error",
     "jsweep_batch_create", "jsweep_batch_problem_bytes", "jsweep_batch_add", "jsweep_batch_step",
     "jsweep_batch_launch", "jsweep_batch_poll",
     "jsweep_batch_query", "jsweep_batch_remove", "jsweep_batch_clear", "jsweep_batch_size",
@@ -173,6 +173,8 @@ def load(path: str = LIB_PATH):
             "jsweep_dags_timing": (I, [P, P]),
             "jsweep_source_iterate_noalloc": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
             "jsweep_source_iterate_mg": (I, [P, I, I, P, P, P, P, ctypes.c_double, I, P, P, P, P]),
+            "jsweep_bounds_checked": (I, []),
+            "jsweep_bounds_error": (I, [P]),
             "jsweep_batch_create": (I, [I, I, P, P]),
             "jsweep_batch_problem_bytes": (I, [P, P, I, P]),
             "jsweep_batch_add": (I, [P, P, P, P, P, P, P, ctypes.c_double, I, P, P]),
@@ -479,6 +481,19 @@ def jsweep_source_iterate_mg(dags: Dags, sigma_t, sigma_s, q, inflow=None, tol=1
         return phi_out, it.value, res.value, False
     _check(rc, "jsweep_source_iterate_mg")
     return phi_out, it.value, res.value, True
+
+
+def jsweep_bounds_checked() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(lib().jsweep_bounds_checked())
+
+
+def jsweep_bounds_error() -> int:
+    """The first out-of-range index recorded by a bounds-checked build on the
+    current device ((code << 56) | index, 0 = none); clears it."""
+    w = ctypes.c_uint64(0)
+    _check(lib().jsweep_bounds_error(ctypes.byref(w)), "jsweep_bounds_error")
+    return int(w.value)
 
 
 JSWEEP_PROBLEM_ACTIVE = 0

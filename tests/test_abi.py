@@ -42,6 +42,21 @@ def test_exports_nothing_else(lib):
     assert exported == set(header_symbols())
 
 
+def test_bounds_checked_build_exports_the_same_symbols(lib):
+    # the bounds-checked library (debug build) has the same ABI and says what it is
+    import subprocess
+    path = libbuild.build(bounds_check=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert exported == set(header_symbols())
+    checked = ctypes.CDLL(path)
+    assert checked.jsweep_bounds_checked() == 1
+    assert lib.jsweep_bounds_checked() == 0
+    assert lib.jsweep_bounds_error(None) == J.JSWEEP_ERR_INVALID_ARG
+    w = ctypes.c_uint64(7)
+    assert lib.jsweep_bounds_error(ctypes.byref(w)) == J.JSWEEP_OK and w.value == 0  # no device work
+
+
 def test_version_and_options(lib):
     assert J.jsweep_version() >= 100
     o = J.jsweep_options_default()
