@@ -42,6 +42,11 @@
  *     repeat { S = (c sigma_t phi + q) / (4 pi); sweep all directions;
  *     update lagged values; err = max_c |phi_new - phi| / max_c |phi_new| }
  *     until err < tol for every right-hand side.
+ *   - Multigroup source iteration (the appendix's transport equation over
+ *     energy groups g, same algorithm): every group's source from the
+ *     previous iterate of all groups, S_g = (sum_h sigma_s[h][g] phi_h + q_g)
+ *     / (4 pi), then one sweep per group with its own sigma_t and lagged
+ *     values; err is the largest over the groups.
  */
 #include <math.h>
 #include <stdint.h>
