@@ -236,6 +236,14 @@ JSWEEP_API int jsweep_dags_nlevels(jsweep_dags_t dags, int64_t m, int64_t *nleve
 JSWEEP_API int jsweep_dags_levels(jsweep_dags_t dags, int64_t m, int32_t *level_of_cell);
 /* order [n_cells], level_ptr [nlevels+1] (host). */
 JSWEEP_API int jsweep_dags_order(jsweep_dags_t dags, int64_t m, int32_t *order, int32_t *level_ptr);
+/* The schedule the sweeps of direction m run: its layers (the octant-aligned
+ * layers by default, the levels with JSWEEP_LAYERS_LEVEL; every active upwind
+ * cell of a cell is in an earlier layer), as the number of layers in
+ * *n_layers, the cells in layer-major order in order [n_cells] (host) and the
+ * layer pointers in layer_ptr [n_layers+1] (host).  order and layer_ptr may be
+ * NULL (then only the count is returned). */
+JSWEEP_API int jsweep_dags_schedule(jsweep_dags_t dags, int64_t m, int64_t *n_layers, int32_t *order,
+                                    int32_t *layer_ptr);
 /* Lagged faces of direction m sorted by face id, rows (face, upwind cell,
  * downwind cell) into rows [*n][3] (host; may be NULL to query *n only). */
 JSWEEP_API int jsweep_dags_lagged(jsweep_dags_t dags, int64_t m, int64_t *rows, int64_t *n);

@@ -667,6 +667,22 @@ int jsweep_dags_order(jsweep_dags_t dags, int64_t m, int32_t *order, int32_t *le
     return JSWEEP_OK;
 }
 
+int jsweep_dags_schedule(jsweep_dags_t dags, int64_t m, int64_t *n_layers, int32_t *order, int32_t *layer_ptr) {
+    if (!dags || !n_layers) {
+        set_error("jsweep_dags_schedule: NULL");
+        return JSWEEP_ERR_INVALID_ARG;
+    }
+    Dags *d = impl(dags);
+    JS_TRY(check_dir(d, m));
+    *n_layers = d->slayers[m];
+    if (!order && !layer_ptr) return JSWEEP_OK;
+    JS_CUDA(cudaDeviceSynchronize());
+    if (order) JS_CUDA(cudaMemcpy(order, d->s_order + m * d->N, d->N * 4, cudaMemcpyDeviceToHost));
+    if (layer_ptr)
+        JS_CUDA(cudaMemcpy(layer_ptr, d->s_lp + d->sp_off[m], (d->slayers[m] + 1) * 4, cudaMemcpyDeviceToHost));
+    return JSWEEP_OK;
+}
+
 int jsweep_dags_lagged(jsweep_dags_t dags, int64_t m, int64_t *rows, int64_t *n) {
     if (!dags || !n) {
         set_error("jsweep_dags_lagged: NULL");

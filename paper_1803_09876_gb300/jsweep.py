@@ -54,7 +54,7 @@ EXPORTED = [
     "jsweep_mesh_create", "jsweep_mesh_destroy", "jsweep_mesh_info",
     "jsweep_quadrature_product", "jsweep_quadrature_create", "jsweep_quadrature_destroy",
     "jsweep_build_dags", "jsweep_dags_destroy", "jsweep_dags_info", "jsweep_dags_nlevels",
-    "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
+    "jsweep_dags_levels", "jsweep_dags_order", "jsweep_dags_schedule", "jsweep_dags_lagged", "jsweep_dags_reset_lag",
     "jsweep_dags_set_options", "jsweep_sweep", "jsweep_source_iterate", "jsweep_dags_timing",
     "jsweep_source_iterate_noalloc", "jsweep_source_iterate_mg", "jsweep_bounds_checked", "jsweep_bounds_error",
     "jsweep_batch_create", "jsweep_batch_problem_bytes", "jsweep_batch_add", "jsweep_batch_step",
@@ -165,6 +165,7 @@ def load(path: str = LIB_PATH):
             "jsweep_dags_nlevels": (I, [P, I64, P]),
             "jsweep_dags_levels": (I, [P, I64, P]),
             "jsweep_dags_order": (I, [P, I64, P, P]),
+            "jsweep_dags_schedule": (I, [P, I64, P, P, P]),
             "jsweep_dags_lagged": (I, [P, I64, P, P]),
             "jsweep_dags_reset_lag": (I, [P]),
             "jsweep_dags_set_options": (I, [P, P]),
@@ -340,6 +341,15 @@ class Dags:
         order = np.empty(self.n_cells, dtype=np.int32)
         ptr = np.empty(self.nlevels(m) + 1, dtype=np.int32)
         _check(lib().jsweep_dags_order(self._h, int(m), _ptr(order), _ptr(ptr)))
+        return order, ptr
+
+    def schedule(self, m: int):
+        """(order [n_cells], layer_ptr [n_layers + 1]) of the layers the sweeps of direction m run."""
+        n = ctypes.c_int64()
+        _check(lib().jsweep_dags_schedule(self._h, int(m), ctypes.byref(n), None, None))
+        order = np.empty(self.n_cells, dtype=np.int32)
+        ptr = np.empty(n.value + 1, dtype=np.int32)
+        _check(lib().jsweep_dags_schedule(self._h, int(m), ctypes.byref(n), _ptr(order), _ptr(ptr)))
         return order, ptr
 
     def lagged(self, m: int) -> np.ndarray:

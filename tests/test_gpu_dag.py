@@ -135,3 +135,28 @@ def test_eager_search_cap_does_not_change_the_graphs(eager):
     dirs, w = oracle.product_quadrature(6, 6)
     _, n_lag = compare_all(mesh, dirs, w, eager_search_max=eager, cycle_search_max=max(256, eager))
     assert n_lag > 100
+
+
+@pytest.mark.parametrize("layering", [0, 1], ids=["octant_layers", "levels"])
+def test_schedule_layers_follow_every_active_dependency(layering):
+    # the paper's progress argument, checked on the layers the sweeps run: a
+    # cell is scheduled after every active (not lagged) upwind cell
+    from _bruteforce import edges
+    for mesh, quad in ((hex_grid(5, 0.3, 11), (6, 6)), (kuhn_tets(4, 0.2, 8), (4, 4))):
+        dirs, w = oracle.product_quadrature(*quad)
+        g = build(mesh, dirs, w, layering=layering)
+        N = mesh["n_cells"]
+        for m in range(len(dirs)):
+            order, ptr = g.schedule(m)
+            assert np.array_equal(np.sort(order), np.arange(N))
+            assert ptr[0] == 0 and ptr[-1] == N and np.all(np.diff(ptr) >= 0)  # octant layers may be empty
+            if layering == 1:  # the level schedule is the level-major order
+                lo, lp = g.order(m)
+                assert np.array_equal(order, lo) and np.array_equal(ptr, lp)
+            layer = np.empty(N, dtype=np.int64)
+            for k in range(len(ptr) - 1):
+                layer[order[ptr[k]:ptr[k + 1]]] = k
+            lagged = {int(f) for f in g.lagged(m)[:, 0]}
+            for f, u, v in edges(mesh, dirs[m]):
+                if f not in lagged:
+                    assert layer[u] < layer[v], (m, f, u, v)
