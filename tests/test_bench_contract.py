@@ -31,3 +31,12 @@ def test_reference_arm_line_has_the_contract_keys():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_multigroup_reference_line():
+    d = _run("--workload", "mg")
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["unit"] == "cell-angle-group updates/s"
+    assert d["config"]["workload"] == "tet48x6_128dirs_4groups_fp32_si_tol1e-6"
+    assert d["cpu_baseline"]["kind"] == "oracle" and "4-group iteration" in d["cpu_baseline"]["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
