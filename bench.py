@@ -41,16 +41,23 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "cell-angle updates/s"
-# DRAM bytes (read + write) of one sweep of the dominant kernel, from the full-sweep ncu capture
-# summarised in profiles/k_sweep_level_coef_hex128_full_sweep_dram.md; keyed by
-# (hex edge, sweep mode, priority, cluster cells, layering, face stream); valid while the kernel is
-# unchanged
-SWEEP_TRAFFIC_BYTES = {(128, 1, 0, 32, 0, 1): 1.582e11}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell-direction of the
+# level-synchronous sweep kernel, from one ncu capture of three consecutive mid-sweep slot
+# launches on the 64^3 jittered hex with the benchmark's directions, right-hand sides and
+# options (a smaller case than the timed 128^3 one, scaled by the cell-directions a launch
+# processes).  The figure belongs to the kernel sources it was taken on (SHA-256 of the files
+# below, first 16 hex digits); when they differ the line reports no traffic.
+SWEEP_TRAFFIC = None  # {"sources_sha16": ..., "bytes_per_cell_dir": ..., "capture": ...}
+SWEEP_SOURCES = ("paper_1803_09876_gb300/csrc/sweep.cu", "paper_1803_09876_gb300/csrc/sweep_cell.cuh")
+# source-iteration sweeps of one benchmark step (128^3, tol 1e-6): the count the GPU arm
+# measures (every schedule gives the same bits, so the same count); the reference arm uses it
+# to weigh its sampled DAG build against its sampled sweeps the way one step does
+SI_SWEEPS_PER_STEP = 22
 UNIT = "cell-angle-rhs updates/s"
 WORKLOAD = "hex128_jitter0.15_288dirs_8rhs_fp32_si_tol1e-6"
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
@@ -82,7 +89,27 @@ def parse():
                    help="serve: Poisson arrival rates (requests/s), comma-separated; the line's headline is the last")
     p.add_argument("--meshes", type=int, default=24, help="serve: meshes in the catalog")
     p.add_argument("--budget-gb", type=float, default=60.0, help="serve: device-memory budget")
-    return p.parse_args()
+    p.add_argument("--no-sweep-order-psi", action="store_true",
+                   help="level-synchronous sweeps read upwind values from the cell-major psi instead of the "
+                        "sweep-order copy")
+    return p.parse_args(argv)
+
+
+def sweep_options(args) -> dict:
+    """jsweep_options fields of the timed configuration (also used by the
+    full-size parity test, so that it checks exactly what is timed)."""
+    return dict(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster, layering=args.layering,
+                no_face_stream=int(args.no_face_stream), tail_units=args.tail_units,
+                no_sweep_order_psi=int(args.no_sweep_order_psi))
+
+
+def sources_sha16(paths=SWEEP_SOURCES) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ---- multi-process plumbing (replicas: every rank runs its own full problem) ----
@@ -167,8 +194,9 @@ def measured_peaks():
 
 # ---- the reference arm: FP64 CPU oracle on a bounded sample -----------------------
 def oracle_sample(wl, dirs, w, n_dirs_sample, nthreads):
-    """Oracle DAG build + one sweep of n_dirs_sample directions of the workload;
-    returns (cell-angle-rhs updates, seconds)."""
+    """Oracle DAG build, then one sweep, of n_dirs_sample evenly spaced
+    directions of the workload (all right-hand sides); returns (cell-angle-rhs
+    updates of the sweep, build seconds, sweep seconds)."""
     import numpy as np
 
     import oracle
@@ -177,9 +205,40 @@ def oracle_sample(wl, dirs, w, n_dirs_sample, nthreads):
     src = wl["q"] / (4 * math.pi)
     t0 = time.perf_counter()
     o = oracle.build_dags(wl, dirs[sample])
+    t1 = time.perf_counter()
     o.sweep(wl["sigma_t"], src, w[sample], nthreads=nthreads)
-    dt = time.perf_counter() - t0
-    return float(n_dirs_sample) * wl["n_cells"] * wl["q"].shape[0], dt
+    t2 = time.perf_counter()
+    return float(n_dirs_sample) * wl["n_cells"] * wl["q"].shape[0], t1 - t0, t2 - t1
+
+
+def step_rate(updates, build_s, sweep_s, sweeps_per_step):
+    """Cell-angle-rhs updates per second of a step shaped like the GPU arm's:
+    one DAG build, then sweeps_per_step sweeps (one sweep timed, the others
+    counted at its time)."""
+    return sweeps_per_step * updates / (build_s + sweeps_per_step * sweep_s)
+
+
+def oracle_baseline(wl, dirs, w, sweeps_per_step, reps=1):
+    """The oracle on the host cores: all threads on a sample of 2 x threads
+    directions, and one thread on 2 of them; returns the cpu_baseline object."""
+    import oracle
+
+    nt = oracle.max_threads()
+    nd = max(2, 2 * nt)
+    u = b = sw = 0.0
+    for _ in range(reps):
+        u_, b_, s_ = oracle_sample(wl, dirs, w, nd, nt)
+        u, b, sw = u + u_, b + b_, sw + s_
+    u1, b1, s1 = oracle_sample(wl, dirs, w, 2, 1)
+    value = step_rate(u, b, sw, sweeps_per_step)
+    return {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": (f"oracle on {nd} evenly spaced of {len(dirs)} directions, all {wl['q'].shape[0]} right-hand "
+                       f"sides, full {wl['n_cells']}-cell mesh, {nt} OpenMP threads: DAG build {b / reps:.2f} s, one "
+                       f"sweep {sw / reps:.2f} s; a step is counted as the build plus {sweeps_per_step} sweeps (the "
+                       f"source-iteration sweeps of one GPU step), each at the timed sweep's time"),
+            "sweep_only_rate": u / sw, "build_s": b / reps, "sweep_s": sw / reps, "sweeps_per_step": sweeps_per_step,
+            "one_thread": {"value": step_rate(u1, b1, s1, sweeps_per_step), "sweep_only_rate": u1 / s1,
+                           "cores": 1, "sample": "the same on 2 of the directions, 1 thread"}}
 
 
 def run_reference(args):
@@ -192,23 +251,27 @@ def run_reference(args):
     wl = make_workload(3, n=args.n)
     dirs, w = oracle.product_quadrature(*wl["spec"]["quad"])
     nt = oracle.max_threads()
-    nd = max(2, min(len(dirs), 4 * nt if args.n >= 128 else len(dirs)))
+    nd = max(2, 2 * nt)  # the same sample as the GPU line's cpu_baseline
     for _ in range(args.warmup):
         oracle_sample(wl, dirs, w, nd, nt)
-    tot_u, tot_s = 0.0, 0.0
+    tot_u = tot_b = tot_s = 0.0
     for _ in range(args.steps):
-        u, s = oracle_sample(wl, dirs, w, nd, nt)
-        tot_u += u
-        tot_s += s
-    value = tot_u / tot_s
+        u, b, s = oracle_sample(wl, dirs, w, nd, nt)
+        tot_u, tot_b, tot_s = tot_u + u, tot_b + b, tot_s + s
+    K = SI_SWEEPS_PER_STEP
+    value = step_rate(tot_u, tot_b, tot_s, K)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (tot_b + K * tot_s) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.n == 128 else f"hex{args.n}_288dirs_8rhs"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
-                         "sample": f"per step: oracle DAG build + one sweep of {nd} of 288 directions, "
-                                   f"all 8 right-hand sides, full {wl['n_cells']}-cell mesh, {nt} OpenMP threads"},
+                         "sample": f"per step: oracle DAG build and one sweep of {nd} evenly spaced of 288 "
+                                   f"directions, all 8 right-hand sides, full {wl['n_cells']}-cell mesh, {nt} OpenMP "
+                                   f"threads; the step counted as the build plus {K} sweeps (the source-iteration "
+                                   f"sweeps of one GPU step) at the timed sweep's time",
+                         "build_s": tot_b / args.steps, "sweep_s": tot_s / args.steps,
+                         "sweep_only_rate": tot_u / tot_s},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -238,9 +301,7 @@ def run_gpu(args):
     M = len(dirs)
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
-    opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
-                                   layering=args.layering, no_face_stream=int(args.no_face_stream),
-                                   tail_units=args.tail_units)
+    opt = J.jsweep_options_default(**sweep_options(args))
     dev = torch.device("cuda", local)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device=dev)
     cr = torch.as_tensor(wl["c_ratio"], dtype=torch.float32, device=dev)
@@ -308,11 +369,16 @@ def run_gpu(args):
     achieved = alg_bytes / ((sw_ms + ph_ms) / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic = SWEEP_TRAFFIC_BYTES.get((args.n, args.mode, args.priority, args.cluster, args.layering,
-                                       int(not args.no_face_stream)))
+    sha = sources_sha16()
+    traffic, traffic_src = None, None
+    if (SWEEP_TRAFFIC and SWEEP_TRAFFIC["sources_sha16"] == sha and args.mode == 1
+            and sweep_options(args) == sweep_options(parse([]))):
+        traffic = SWEEP_TRAFFIC["bytes_per_cell_dir"] * N * M
+        traffic_src = SWEEP_TRAFFIC["capture"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
             "traffic_unit": "bytes per sweep (one launch sequence of the CUDA graph)",
+            "traffic_source": traffic_src, "kernel_sources_sha16": sha,
             "kernel": (("sweep (level-synchronous CUDA graph, "
                         + ("geometry reads)" if args.no_face_stream else "face-coefficient stream)"))
                        if args.mode == 1 else "sweep (data-driven persistent)")
@@ -353,12 +419,7 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         d64, w64 = oracle.product_quadrature(npol, naz)
-        nt = oracle.max_threads()
-        nd = max(2, 2 * nt)
-        u, s = oracle_sample(wl, d64, w64, nd, nt)
-        cpu = {"value": u / s, "unit": UNIT, "cores": nt, "kind": "oracle",
-               "sample": f"oracle DAG build + one sweep of {nd} of {M} directions, all {R} right-hand sides, "
-                         f"full {N}-cell mesh, {nt} OpenMP threads ({s:.1f} s)"}
+        cpu = oracle_baseline(wl, d64, w64, max(1, round(iters / args.steps)))
 
     if rank == 0:
         line = {
@@ -949,7 +1010,7 @@ def run_reference_mg(args):
 
 def run_sweeps(args):
     """Build the graphs of the workload once, then args.sweeps plain sweeps
-    (the launch sequence the per-kernel ncu captures in profiles/ skip into)."""
+    (the launch sequence that per-kernel ncu captures skip into)."""
     import torch
 
     from inputs import make_workload
@@ -963,9 +1024,7 @@ def run_sweeps(args):
     N, R = wl["n_cells"], wl["q"].shape[0]
     dirs, w = J.jsweep_quadrature_product(*wl["spec"]["quad"])
     M = len(dirs)
-    opt = J.jsweep_options_default(sweep_mode=args.mode, priority=args.priority, cluster_cells=args.cluster,
-                                   layering=args.layering, no_face_stream=int(args.no_face_stream),
-                                   tail_units=args.tail_units)
+    opt = J.jsweep_options_default(**sweep_options(args))
     dags = J.jsweep_build_dags(J.mesh_from_dict(wl), J.jsweep_quadrature_create(dirs, w), opt)
     sig = torch.as_tensor(wl["sigma_t"], dtype=torch.float32, device="cuda")
     src = torch.as_tensor(wl["q"] / (4 * math.pi), dtype=torch.float32, device="cuda").contiguous()

@@ -145,7 +145,14 @@ typedef struct {
                               of one block per direction (the tail), each block sweeping its direction's
                               remaining layers in order with a block barrier between layers, instead of
                               one launch per slot; 0 (default) = no tail.  Results are bit-identical. */
-    int reserved[1];
+    int no_sweep_order_psi; /* level-synchronous sweeps with the face stream: 0 (default) keeps a second copy
+                              of psi in each direction's sweep order ([M][N][R], N x M x R x element bytes;
+                              built at the first such sweep, kept with the handle) beside the cell-major
+                              psi.  A slot then writes its cell-directions as one contiguous run and reads
+                              its upwind values from the runs of the layers just before it, which stay in
+                              L2; the face stream holds upwind positions in that order instead of cell
+                              ids.  Nonzero reads upwind values from the cell-major psi.  Results are
+                              bit-identical either way. */
 } jsweep_options;
 
 /* Fill *opt with defaults. */
@@ -431,8 +438,15 @@ JSWEEP_API int jsweep_batch_destroy(jsweep_batch_t batch);
  *     JSWEEP_ERR_INVALID_ARG (the message gives the bytes needed): roughly
  *     directions x cells x padded right-hand sides x element size must stay
  *     below 64 MiB (e.g. 4,096 cells x 96 directions x 1 rhs in FP64 fits).
- *   - The first call on a device looks up the array's device address with that
- *     device current; make that first call before any stream capture.
+ *   - The array belongs to the library's device code: the first use of the
+ *     library on a device loads that code and commits the array there (64 MiB),
+ *     and the first call of this function on a device looks up the array's
+ *     address with that device current.  A caller that budgets all of the
+ *     device's memory should make one small call (any built handle) before it
+ *     takes its budget.
+ *   - The function synchronises `stream` at every iteration (it reads the
+ *     residual on the host to decide whether to stop), so it cannot be called
+ *     while the stream is being captured into a CUDA graph.
  *   - All calls share the one array and it keeps the last call's contents (each
  *     call zeroes what must start at zero), so calls that overlap on the GPU
  *     (different streams or threads) race: serialise them.

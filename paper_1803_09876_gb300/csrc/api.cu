@@ -536,6 +536,7 @@ int check_options(const jsweep_options *opt, jsweep_options *o) {
     if (opt->eager_search_max > 0) o->eager_search_max = opt->eager_search_max;
     o->no_face_stream = opt->no_face_stream ? 1 : 0;
     o->tail_units = opt->tail_units;
+    o->no_sweep_order_psi = opt->no_sweep_order_psi ? 1 : 0;
     if (opt->angles_per_warp != 0 && opt->angles_per_warp != 1 && opt->angles_per_warp != 2 &&
         opt->angles_per_warp != 4) {
         set_error("jsweep_options.angles_per_warp=%d (1, 2 or 4)", opt->angles_per_warp);

@@ -452,6 +452,7 @@ template <class T> ProbArgs<T> prob_args(const Batch *b, BatchProb &p) {
     a.srcv = p.srcv.as<T>();
     a.inflow = p.has_inflow ? p.inflow.as<T>() : nullptr;
     a.psi = p.psi.as<T>();
+    a.psi_seq = nullptr;
     a.psi_lag = p.psi_lag.as<T>();
     a.lag_ptr = d->lag_ptr.as<int32_t>();
     a.lag_face = d->lag_face.as<int32_t>();

@@ -124,6 +124,8 @@ struct UnitTable {
     DevBuf units;                  // int4 [n_units]: (m, pos0, ncells, wait target)
     int64_t n_units = 0;
     std::vector<int64_t> slot_ptr; // level-sync: units of level l are [slot_ptr[l], slot_ptr[l+1])
+    bool dirmajor = false;         // persistent queues: units direction by direction, each in layer order
+    DevBuf dir_ptr;                // int64 [M+1]: units of direction m are [dir_ptr[m], dir_ptr[m+1])
 };
 
 // Patch-program schedule of a handle (JSWEEP_MODE_PATCH).
@@ -183,6 +185,7 @@ struct Dags {
     DevBuf phi_a, phi_b;  // [R][N] (SI ping-pong)
     DevBuf red;      // residual accumulators / flags
     DevBuf counters; // persistent schedule: error word
+    DevBuf qstate;   // persistent queues: per-direction cursor and finished-unit counter
     DevBuf flags;    // int32 [N][M]: sweep epoch at which (cell, direction) was last written
     int epoch = 0;
     DevBuf dirs4_64; // double [M][4]: directions padded for aligned loads (FP64 sweeps)
@@ -195,7 +198,11 @@ struct Dags {
         const int32_t *order = nullptr;  // the order and directions it was built for
         const void *dirs = nullptr;
         bool failed = false;             // allocation refused: sweeps read the cell geometry
-    } coef[2];
+    } coef[2], pcoef[2];                 // pcoef: interior neighbours as positions in the sweep order
+    // psi in each direction's sweep order ([M][N][R], level-synchronous sweeps with
+    // pcoef); prec/R of its contents, failed when its allocation was refused
+    DevBuf psi_seq;
+    bool psi_seq_failed = false;
     // tail of the level-synchronous sweep (the last, small slots: one block per direction)
     DevBuf tail_lpoff;       // int64 [M+1]: device copy of sp_off
     DevBuf tail_nlev;        // int32 [M]: device copy of slayers
@@ -221,7 +228,10 @@ int build_dags(Dags *d, cudaStream_t s);
 Dags *build_diagonals(Dags *d, cudaStream_t s);
 
 // unit schedules and sweeps (sweep.cu)
-int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps = 0);
+// dirmajor: the persistent queues' direction-major table (single problems);
+// otherwise the slot-ordered table (level-synchronous sweeps, batches, patch tasks)
+int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps = 0,
+                 bool dirmajor = false);
 int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s);  // FP64 directions as [M][4]
 // Face-coefficient stream of a handle (level-synchronous sweeps), built on
 // first use; nullptr when the option is off or its allocation was refused.

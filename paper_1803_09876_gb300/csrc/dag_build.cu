@@ -99,6 +99,30 @@ __device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, i
     }
 }
 
+// push() for the lanes of a warp at once: the active lanes that want to push
+// to the same list reserve their slots with one atomic (list order is not
+// significant: levels are maxima over upwind cells and the lag rule picks the
+// smallest face of a component, whatever order cells were found in).  Every
+// active lane must call it.
+__device__ __forceinline__ void push_warp(int32_t *list, int32_t *count, int32_t v, bool want, int64_t cap,
+                                          int32_t *status) {
+    const unsigned act = __activemask();
+    const unsigned wanted = __ballot_sync(act, want);
+    if (!want) return;
+    const unsigned peers = __match_any_sync(wanted, (unsigned long long)(uintptr_t)count);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const int32_t i = base + __popc(peers & ((1u << lane) - 1u));
+    if (i < cap) {
+        list[i] = v;
+    } else {
+        atomicCAS(&status[0], 0, JSWEEP_ERR_OOM);
+    }
+}
+
 __device__ __forceinline__ void load_nbr8(const BuildCtx &c, int32_t v, int32_t (&nb)[8]) {
     const int4 a = __ldg(c.nbr8 + 2 * (int64_t)v), b = __ldg(c.nbr8 + 2 * (int64_t)v + 1);
     nb[0] = a.x; nb[1] = a.y; nb[2] = a.z; nb[3] = a.w;
@@ -140,12 +164,9 @@ __global__ void k_classify(BuildCtx c) {
         c.inm[idx] = (uint8_t)in;
         c.outm[idx] = (uint8_t)out;
         c.cnt[idx] = count;
-        if (count == 0) {
-            push(c.front + m * c.N, c.nfront + m, v, c.N, c.status);
-        } else if (bin) {
-            c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
-            push(c.cand + m * c.N, c.ncand + m, v, c.N, c.status);
-        }
+        if (count != 0 && bin) c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
+        push_warp(c.front + m * c.N, c.nfront + m, v, count == 0, c.N, c.status);
+        push_warp(c.cand + m * c.N, c.ncand + m, v, count != 0 && bin, c.N, c.status);
     }
 }
 
@@ -185,13 +206,12 @@ __global__ void k_peel(BuildCtx c, int cur) {
         for (int k = 0; k < 8; ++k) old[k] = ((ob >> k) & 1u) ? atomicSub(&c.cnt[base + nb[k]], 1) : 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (!((ob >> k) & 1u)) continue;
+            const bool o = ((ob >> k) & 1u) != 0;
             const int32_t w = nb[k];
-            if (old[k] == 1) {
-                push(fn, nfn, w, c.N, c.status);
-            } else if (cyclic && atomicExch(&c.stamp[base + w], ep) != ep) {
-                push(cl, ncl, w, c.N, c.status);
-            }
+            const bool ready = o && old[k] == 1;
+            const bool cand = o && !ready && cyclic && atomicExch(&c.stamp[base + w], ep) != ep;
+            push_warp(fn, nfn, w, ready, c.N, c.status);
+            push_warp(cl, ncl, w, cand, c.N, c.status);
         }
         ++processed;
     }
@@ -588,30 +608,37 @@ __global__ void k_lag_ptr(const int32_t *lm, int32_t T, int64_t M, int32_t *lag_
     }
 }
 
-// Octant-aligned schedule layers, one launch per level l (blockIdx.y = direction):
+// Octant-aligned schedule layers (blockIdx.x = direction m):
 // kappa(c) = max(floor(rho_o * lambda_o(c)), 1 + max kappa(active upwind cell)).
-// Upwind cells have smaller levels, so their kappa is final when c's level runs.
-__global__ void k_kappa_level(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
-                              const uint8_t *inm, const uint8_t *lagm, const int4 *nbr8, int64_t N,
-                              const int32_t *oct, const float *rho, const int32_t *lam, int32_t l, int32_t *kap) {
-    const int64_t m = blockIdx.y;
-    if (l >= nlev[m]) return;
-    const int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
+// Upwind cells have smaller levels, so their kappa is final when c's level runs;
+// one block sweeps its direction level after level with a block barrier in
+// between (a direction's levels need no other direction).
+__global__ void __launch_bounds__(1024)
+    k_kappa_dir(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
+                const uint8_t *inm, const uint8_t *lagm, const int4 *nbr8, int64_t N, const int32_t *oct,
+                const float *rho, const int32_t *lam, int32_t *kap) {
+    const int64_t m = blockIdx.x;
     const int o = oct[m];
     const float r = rho[o];
     const int64_t base = m * N;
-    for (int32_t pos = p0 + blockIdx.x * blockDim.x + threadIdx.x; pos < p1; pos += gridDim.x * blockDim.x) {
-        const int32_t c = order[base + pos];
-        int32_t k = (int32_t)(r * (float)lam[(int64_t)o * N + c]);
-        const unsigned act = (unsigned)inm[base + c] & ~(unsigned)lagm[base + c];
-        const int4 a = __ldg(nbr8 + 2 * (int64_t)c), b = __ldg(nbr8 + 2 * (int64_t)c + 1);
-        const int32_t nb[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        int32_t kk[8];
+    const int L = nlev[m];
+    const int32_t *lpm = lp + lp_off[m];
+    for (int l = 0; l < L; ++l) {
+        const int32_t p0 = lpm[l], p1 = lpm[l + 1];
+        for (int32_t pos = p0 + threadIdx.x; pos < p1; pos += blockDim.x) {
+            const int32_t c = order[base + pos];
+            int32_t k = (int32_t)(r * (float)lam[(int64_t)o * N + c]);
+            const unsigned act = (unsigned)inm[base + c] & ~(unsigned)lagm[base + c];
+            const int4 a = __ldg(nbr8 + 2 * (int64_t)c), b = __ldg(nbr8 + 2 * (int64_t)c + 1);
+            const int32_t nb[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            int32_t kk[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) kk[q] = (((act >> q) & 1u) && nb[q] >= 0) ? kap[base + nb[q]] + 1 : k;
+            for (int q = 0; q < 8; ++q) kk[q] = (((act >> q) & 1u) && nb[q] >= 0) ? __ldcg(kap + base + nb[q]) + 1 : k;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) k = max(k, kk[q]);
-        kap[base + c] = k;
+            for (int q = 0; q < 8; ++q) k = max(k, kk[q]);
+            kap[base + c] = k;
+        }
+        __syncthreads();  // this level's layers are stored before the next level reads them
     }
 }
 
@@ -851,15 +878,10 @@ static int octant_layers(Dags *d, const Dags *dg, const std::vector<int32_t> &oc
     JS_TRY(kap.alloc(N * M * 4, s));
     JS_CUDA(cudaMemcpyAsync(oct_d.p, oct.data(), M * 4, cudaMemcpyHostToDevice, s));
     JS_CUDA(cudaMemcpyAsync(rho_d.p, rho.data(), 8 * 4, cudaMemcpyHostToDevice, s));
-    const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (256 * 64)), 8);
-    for (int64_t l = 0; l < d->Lmax; ++l) {
-        k_kappa_level<<<dim3(gx, (unsigned)M), 256, 0, s>>>(d->order.as<int32_t>(), d->lp.as<int32_t>(), lpoff_dev,
-                                                           nlev_dev, inm, lagm, d->mesh->nbr8.as<int4>(), N,
-                                                           oct_d.as<int32_t>(), rho_d.as<float>(),
-                                                           dg->level.as<int32_t>(), (int32_t)l, kap.as<int32_t>());
-        note_launches(1);
-    }
-    JS_CUDA(cudaGetLastError());
+    k_kappa_dir<<<(unsigned)M, 1024, 0, s>>>(d->order.as<int32_t>(), d->lp.as<int32_t>(), lpoff_dev, nlev_dev, inm,
+                                             lagm, d->mesh->nbr8.as<int4>(), N, oct_d.as<int32_t>(),
+                                             rho_d.as<float>(), dg->level.as<int32_t>(), kap.as<int32_t>());
+    JS_LAUNCH_CHECK();
     // layer counts, sort by (layer, cell id), layer pointers, mask in layer order
     JS_TRY(kmax.alloc(M * 4, s));
     JS_CUDA(cudaMemsetAsync(kmax.p, 0xff, M * 4, s));
@@ -1046,14 +1068,26 @@ int build_dags(Dags *d, cudaStream_t s) {
         pev.push_back(e);
         (void)k;
     };
+    // Cycles are searched for every kSearchEvery steps (the candidates of the
+    // steps in between accumulate): the lags found do not depend on when a
+    // component is found, only how long the cells behind it wait.
+    constexpr int kSearchEvery = 4;
     while (true) {
         int cur = (int)(step & 1);
+        const bool search = step % kSearchEvery == kSearchEvery - 1;
         prof_mark(0);
         k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
         prof_mark(1);
-        k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
+        if (search) {
+            k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
+            note_launches(1);
+        }
         prof_mark(2);
-        k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B, d->eager_cap > 0 ? d->eager_cap : B);
+        if (search) {
+            k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B,
+                                                                     d->eager_cap > 0 ? d->eager_cap : B);
+            note_launches(1);
+        }
         prof_mark(3);
         k_commit<<<64, 256, 0, s>>>(c, cur ^ 1, cur);
         prof_mark(4);
@@ -1068,7 +1102,7 @@ int build_dags(Dags *d, cudaStream_t s) {
             for (auto e : pev) cudaEventDestroy(e);
             pev.clear();
         }
-        note_launches(3);  // peel, walk, resolve; the check below counts commit
+        note_launches(1);  // peel (walk and resolve counted above); the check below counts commit
         JS_LAUNCH_CHECK();
         ++step;
         if (step % check_every == 0) {

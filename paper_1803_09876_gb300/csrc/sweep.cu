@@ -61,8 +61,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T
     }
 }
 
-// Level-synchronous sweep reading the precomputed face coefficients.
-template <class T, int R, int SPLIT, int MAXF>
+// Level-synchronous sweep reading the precomputed face coefficients (SEQ: the
+// records hold upwind positions and psi has a sweep-order copy, see
+// solve_cell_coef).
+template <class T, int R, int SPLIT, int MAXF, bool SEQ>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sweep_level_coef(SweepArgs<T> a, int64_t u0, int64_t nu, const unsigned char *coef) {
     pdl_launch_next();
@@ -75,11 +77,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int cell = lane / SPLIT, sub = lane % SPLIT;
     if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
         const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
-        solve_cell_coef<T, R, SPLIT, MAXF>(a, u.x, ldg_hint(a.order + idx, pol_stream),
-                                           ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB, pol_stream, [] {
-                                               pdl_wait_prev();  // upwind values come from earlier slots
-                                               return true;
-                                           });
+        solve_cell_coef<T, R, SPLIT, MAXF, SEQ>(a, u.x, ldg_hint(a.order + idx, pol_stream),
+                                                ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB, pol_stream,
+                                                [] {
+                                                    pdl_wait_prev();  // upwind values come from earlier slots
+                                                    return true;
+                                                },
+                                                idx);
     }
 }
 
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // direction (the per-direction dependency graph), so the blocks never wait for
 // one another; the layers before first_layer were swept by the slot launches
 // that precede this one.
-template <class T, int R, int SPLIT, int MAXF>
+template <class T, int R, int SPLIT, int MAXF, bool SEQ>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sweep_tail(SweepArgs<T> a, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, int first_layer,
                  const unsigned char *coef) {
@@ -107,18 +111,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         for (int p = lpm[l] + cell; p < p1; p += per_pass) {
             if (!JS_IN_RANGE(a, p, a.N, 4)) continue;
             const int64_t idx = (int64_t)m * a.N + p;
-            solve_cell_coef<T, R, SPLIT, MAXF>(a, m, ldg_hint(a.order + idx, pol_stream),
-                                               ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB,
-                                               pol_stream, [] { return true; });
+            solve_cell_coef<T, R, SPLIT, MAXF, SEQ>(a, m, ldg_hint(a.order + idx, pol_stream),
+                                                    ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB,
+                                                    pol_stream, [] { return true; }, idx);
         }
         __syncthreads();  // this layer's psi is stored before the next layer reads it
     }
 }
 
+// Position of every cell in each direction's sweep order: pos[m][order[m][p]] = p.
+__global__ void k_sweep_positions(const int32_t *order, int64_t N, int64_t M, int32_t *pos) {
+    const int64_t total = N * M;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i / N;
+        pos[m * N + order[i]] = (int32_t)(i - m * N);
+    }
+}
+
 // Face-coefficient records of every (direction, position) of the sweep order.
+// With pos (not null) an interior neighbour is recorded as its position in the
+// direction's sweep order instead of its cell id.
 template <class T, int MAXF>
 __global__ void k_coef_fill(const int32_t *order, const typename V4<T>::type *geo, const T *dirs, int64_t N,
-                            int64_t M, int FS, int GS, unsigned char *coef) {
+                            int64_t M, int FS, int GS, const int32_t *pos, unsigned char *coef) {
     constexpr int RB = coef_record_bytes<T, MAXF>();
     const int64_t total = N * M;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -134,6 +149,7 @@ __global__ void k_coef_fill(const int32_t *order, const typename V4<T>::type *ge
                 const typename V4<T>::type g = geo[(int64_t)c * GS + k];
                 dk[k] = face_dot(ox, oy, oz, g.x, g.y, g.z);
                 nbk[k] = nbr_bits<T>(g);
+                if (pos && nbk[k] >= 0) nbk[k] = pos[m * N + nbk[k]];
             } else {
                 dk[k] = T(0);
                 nbk[k] = INT32_MIN;
@@ -189,6 +205,80 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             if (c >= 0 && ok && sub == 0) st_release(flags + (int64_t)c * a.M + u.x, epoch);
         }
         if (__any_sync(0xffffffffu, !ok)) return;
+    }
+}
+
+// Data-driven persistent sweep with ready queues and dependency counters
+// (Listing 1: the counts, the queue Q and its dequeue; vertex clustering,
+// Sec. V-C; priority, Sec. V-D).  The work units (up to 32 / SPLIT cells of
+// one layer of one direction) of direction m sit in the table in depth order
+// (layer by layer, dir_ptr[m] .. dir_ptr[m+1]); cursor[m] is m's queue head
+// and done[m] counts m's finished units.  A warp dequeues one unit of its
+// direction (one atomic on m's own cursor; every direction's cursor and
+// counter have a 128-byte line to themselves, since same-address atomics
+// serialise); a unit of layer l needs every unit of m's layers before l (its
+// wait target u.w), so its cells wait (bounded, acquire) until done[m] reaches
+// it, then read their upwind values, solve and store, and the warp adds one
+// to done[m] after a fence.  Warps start on direction (warp mod M) and move to
+// the next direction when theirs has no units left; they return when a whole
+// round of directions had none.  Within a direction units are dequeued in
+// order and wait only for earlier units, so the first unfinished unit of a
+// direction is either running or not yet dequeued by anyone: some warp can
+// always progress, whether or not every block is resident.  The face records
+// hold upwind positions and psi has its sweep-order copy (solve_cell_coef,
+// SEQ).
+constexpr int kQueueStride = 32;  // ints between two directions' cursors / counters (128 bytes)
+
+template <class T, int R, int SPLIT, int MAXF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sweep_queue(SweepArgs<T> a, const int64_t *dir_ptr, const unsigned char *coef, unsigned *cursor, int *done,
+                  int extra, int *err, long long timeout) {
+    constexpr int RB = coef_record_bytes<T, MAXF>();
+    const int lane = threadIdx.x & 31;
+    const int cell = lane / SPLIT, sub = lane % SPLIT;
+    const uint64_t pol = l2_evict_first();
+    int m = (int)(((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) % a.M);
+    int empty = 0;  // directions in a row found without units
+    while (empty < a.M) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(cursor + (int64_t)m * kQueueStride, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        const int64_t u0 = dir_ptr[m], nm = dir_ptr[m + 1] - u0;
+        if ((int64_t)t >= nm) {
+            m = m + 1 == a.M ? 0 : m + 1;
+            ++empty;
+            continue;
+        }
+        empty = 0;
+        const int4 u = ldg_hint(a.units + u0 + t, pol);
+        int *dm = done + (int64_t)m * kQueueStride;
+        bool ok = true;
+        if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
+            const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
+            const int want = u.w + extra;
+            ok = solve_cell_coef<T, R, SPLIT, MAXF, true>(
+                a, u.x, ldg_hint(a.order + idx, pol), ldg_hint(a.mask + idx, pol), sub, coef + idx * RB, pol,
+                [&] {
+                    if (ld_acquire(dm) >= want) return true;
+                    const long long t0 = clock64();
+                    int ns = 32;
+                    while (ld_acquire(dm) < want) {
+                        if (ld_volatile(err) != 0) return false;
+                        if (clock64() - t0 > timeout) {
+                            atomicCAS(err, 0, 1);
+                            return false;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 256 ? 2 * ns : 256;
+                    }
+                    return true;
+                },
+                idx);
+        }
+        // the warp's stores are visible device-wide before its unit counts as done
+        __threadfence();
+        if (__any_sync(0xffffffffu, !ok)) return;
+        if (lane == 0) atomicAdd(dm, 1);
     }
 }
 
@@ -252,6 +342,24 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
             }
             int32_t s = p0 + (int32_t)(j * U);
             units[pos] = make_int4((int)m, s, min(U, p1 - s), wait);
+        }
+    }
+}
+
+// Direction-major unit table: the units of (m, l) start at wscan[m * Lmax + l]
+// (the exclusive scan of the unit counts in direction-then-layer order), and
+// each waits for the units of m's layers before l.
+__global__ void k_unit_fill_dir(const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, const int64_t *ucnt,
+                                const int64_t *wscan, int64_t M, int64_t Lmax, int U, int4 *units) {
+    const int64_t total = M * Lmax;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i / Lmax, l = i - m * Lmax;
+        if (l >= nlev[m]) continue;
+        const int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
+        const int32_t wait = (int32_t)(wscan[i] - wscan[m * Lmax]);
+        for (int64_t j = 0; j < ucnt[i]; ++j) {
+            const int32_t s = p0 + (int32_t)(j * U);
+            units[wscan[i] + j] = make_int4((int)m, s, min(U, p1 - s), wait);
         }
     }
 }
@@ -526,6 +634,7 @@ static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream
     ut.n_units = n_units;
     ut.warps = W;
     ut.slot_ptr.assign({0, n_units});
+    ut.dirmajor = false;
     ut.mode = JSWEEP_MODE_PERSISTENT;
     ut.priority = JSWEEP_PRIO_PATCH;
     ut.cluster = U;
@@ -539,17 +648,74 @@ static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream
     return JSWEEP_OK;
 }
 
-int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps) {
+// Direction-major table of the persistent schedule (see k_sweep_queue): every
+// direction's units in layer order, with the direction boundaries.  Any
+// priority other than patch tasks uses it (the order across directions is the
+// warps' choice at run time; within a direction it is the depth order).
+static int ensure_units_dir(Dags *d, int U, cudaStream_t s) {
+    UnitTable &ut = d->ut;
+    if (ut.dirmajor && ut.mode == JSWEEP_MODE_PERSISTENT && ut.cluster == U) return JSWEEP_OK;
+    const int64_t M = d->M, Lmax = d->Smax;
+    DevBuf ucnt, wscan, lpoff_d, nlev_d;
+    JS_TRY(ucnt.alloc(M * Lmax * 8, s));
+    JS_TRY(wscan.alloc(M * Lmax * 8, s));
+    JS_TRY(lpoff_d.alloc((M + 1) * 8, s));
+    JS_TRY(nlev_d.alloc(M * 4, s));
+    std::vector<int32_t> nl32(M);
+    for (int64_t m = 0; m < M; ++m) nl32[m] = (int32_t)d->slayers[m];
+    JS_CUDA(cudaMemcpyAsync(lpoff_d.p, d->sp_off.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(nlev_d.p, nl32.data(), M * 4, cudaMemcpyHostToDevice, s));
+    k_unit_counts<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
+                                                                nlev_d.as<int32_t>(), M, Lmax, U, ucnt.as<int64_t>());
+    JS_LAUNCH_CHECK();
+    JS_TRY(scan_exclusive_i64(ucnt.as<int64_t>(), wscan.as<int64_t>(), M * Lmax, s));
+    std::vector<int64_t> ws(M * Lmax), uc(1);
+    JS_CUDA(cudaMemcpyAsync(ws.data(), wscan.p, M * Lmax * 8, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaMemcpyAsync(uc.data(), ucnt.as<int64_t>() + M * Lmax - 1, 8, cudaMemcpyDeviceToHost, s));
+    JS_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_units = ws[M * Lmax - 1] + uc[0];
+    std::vector<int64_t> dp(M + 1);
+    for (int64_t m = 0; m < M; ++m) dp[m] = ws[m * Lmax];
+    dp[M] = n_units;
+    JS_TRY(ut.units.alloc(std::max<int64_t>(n_units, 1) * 16, s));
+    JS_TRY(ut.dir_ptr.alloc((M + 1) * 8, s));
+    JS_CUDA(cudaMemcpyAsync(ut.dir_ptr.p, dp.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
+    k_unit_fill_dir<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
+                                                                  nlev_d.as<int32_t>(), ucnt.as<int64_t>(),
+                                                                  wscan.as<int64_t>(), M, Lmax, U,
+                                                                  ut.units.as<int4>());
+    JS_LAUNCH_CHECK();
+    JS_CUDA(cudaStreamSynchronize(s));
+    ut.n_units = n_units;
+    ut.warps = 0;
+    ut.slot_ptr.assign({0, n_units});
+    ut.dirmajor = true;
+    ut.mode = JSWEEP_MODE_PERSISTENT;
+    ut.priority = d->opt.priority;
+    ut.cluster = U;
+    ut.stagger = 0;
+    ut.order = d->opt.unit_order;
+    if (d->graph) {
+        cudaGraphExecDestroy(d->graph);
+        d->graph = nullptr;
+        d->graph_key.clear();
+    }
+    return JSWEEP_OK;
+}
+
+int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resident_warps, bool dirmajor) {
     if (mode == JSWEEP_MODE_PATCH) return JSWEEP_OK;  // patch programs have their own schedule
     const int U = std::max(1, std::min(d->opt.cluster_cells, max_cells));
     int prio = d->opt.priority;
     if (prio == JSWEEP_PRIO_PATCH && mode != JSWEEP_MODE_PERSISTENT) prio = JSWEEP_PRIO_LEVEL;
     if (prio == JSWEEP_PRIO_PATCH) return ensure_units_patch(d, U, resident_warps, s);
+    if (dirmajor) return ensure_units_dir(d, U, s);
     int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Smax / 4);
     if (prio != JSWEEP_PRIO_OCTANT) stagger = 0;
     const int order = d->opt.unit_order;
     UnitTable &ut = d->ut;
-    if (ut.mode == mode && ut.priority == prio && ut.cluster == U && ut.stagger == stagger && ut.order == order)
+    if (!ut.dirmajor && ut.mode == mode && ut.priority == prio && ut.cluster == U && ut.stagger == stagger &&
+        ut.order == order)
         return JSWEEP_OK;
     // schedule layers (levels or octant-aligned layers) play the part of levels here
     const int64_t M = d->M, Lmax = d->Smax;
@@ -631,6 +797,7 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resid
     JS_CUDA(cudaStreamSynchronize(s));
     ut.n_units = n_units;
     ut.warps = 0;
+    ut.dirmajor = false;
     ut.mode = mode;
     ut.priority = prio;
     ut.cluster = U;
@@ -667,6 +834,14 @@ int resolve_mode(const Dags *d) {
     return mode;
 }
 
+// The persistent schedule of a single problem runs on the ready queues
+// (k_sweep_queue) unless the face stream or the sweep-order psi is switched
+// off or was refused, or the priority is patch tasks.
+bool use_queues(const Dags *d, int mode) {
+    return mode == JSWEEP_MODE_PERSISTENT && d->opt.priority != JSWEEP_PRIO_PATCH && !d->opt.no_face_stream &&
+           !d->opt.no_sweep_order_psi && !d->psi_seq_failed;
+}
+
 template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
     SweepArgs<T> a;
     a.N = d->N;
@@ -686,6 +861,7 @@ template <class T> SweepArgs<T> make_args(Dags *d, int Rp, bool has_inflow) {
     a.srcv = d->srcv.as<T>();
     a.inflow = has_inflow ? d->inflow.as<T>() : nullptr;
     a.psi = d->psi.as<T>();
+    a.psi_seq = nullptr;  // set by the level-synchronous sweep when it uses the sweep-order copy
     a.psi_lag = d->psi_lag.as<T>();
     a.lag_ptr = d->lag_ptr.as<int32_t>();
     a.lag_face = d->lag_face.as<int32_t>();
@@ -726,6 +902,36 @@ int ensure_workspace(Dags *d, int prec, int Rp, int nrhs, cudaStream_t s) {
 
 template <class T, int R> constexpr int split_of() {
     return (int)(sizeof(T) * R / 16) > 1 ? (int)(sizeof(T) * R / 16) : 1;
+}
+
+template <class T, int R, int SPLIT, int MAXF>
+int launch_queue(Dags *d, const SweepArgs<T> &a, const unsigned char *coef, cudaStream_t s) {
+    auto kern = k_sweep_queue<T, R, SPLIT, MAXF>;
+    int occ = 0;
+    JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarpsPerBlock * 32, 0));
+    if (occ < 1) occ = 1;
+    int bps = d->opt.blocks_per_sm;
+    if (bps <= 0 || bps > occ) bps = occ;
+    const int khz = device_clock_khz();
+    const long long timeout = (long long)(d->opt.spin_timeout_s * (double)khz * 1000.0);
+    int64_t grid = (int64_t)device_sm_count() * bps;
+    const int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > maxg) grid = std::max<int64_t>(1, maxg);
+    // state: [0, 8) error word (read by check_sweep_error), then per direction a
+    // cursor line and a counter line
+    const size_t words = 8 + (size_t)2 * d->M * kQueueStride;
+    JS_TRY(d->qstate.ensure(words * 4, s));
+    int *st = d->qstate.as<int>();
+    JS_CUDA(cudaMemsetAsync(st, 0, words * 4, s));
+    JS_CUDA(cudaMemsetAsync(d->counters.p, 0, 8, s));
+    unsigned *cursor = reinterpret_cast<unsigned *>(st + 8);
+    int *done = st + 8 + (size_t)d->M * kQueueStride;
+    int *err = reinterpret_cast<int *>(d->counters.p);
+    kern<<<(unsigned)grid, kWarpsPerBlock * 32, 0, s>>>(a, d->ut.dir_ptr.as<int64_t>(), coef, cursor, done,
+                                                         d->opt.debug_block_waits ? 1 : 0, err, timeout);
+    JS_LAUNCH_CHECK();
+    d->timing.sweep_launches = 1;
+    return JSWEEP_OK;
 }
 
 template <class T, int R, int SPLIT, int MAXF>
@@ -807,7 +1013,7 @@ int64_t tail_slot(const Dags *d) {
 // Records the sweep's launches on the capture stream: one launch per slot
 // before the tail slot S, then (S < number of slots) the tail, one block per
 // direction.
-template <class T, int R, int SPLIT, int MAXF>
+template <class T, int R, int SPLIT, int MAXF, bool SEQ>
 void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsigned char *coef, int64_t S) {
     const auto &sp = d->ut.slot_ptr;
     const int64_t Tn = (int64_t)sp.size() - 1;
@@ -829,7 +1035,7 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         cfg.numAttrs = first ? 0 : 1;
         first = false;
         int64_t u0 = sp[l];
-        if (coef) cudaLaunchKernelEx(&cfg, k_sweep_level_coef<T, R, SPLIT, MAXF>, a, u0, nu, coef);
+        if (coef) cudaLaunchKernelEx(&cfg, k_sweep_level_coef<T, R, SPLIT, MAXF, SEQ>, a, u0, nu, coef);
         else cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
     }
     if (S < Tn) {
@@ -842,7 +1048,7 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = first ? 0 : 1;
-        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF>, a, (const int32_t *)d->s_lp,
+        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF, SEQ>, a, (const int32_t *)d->s_lp,
                            (const int64_t *)d->tail_lpoff.as<int64_t>(), (const int32_t *)d->tail_nlev.as<int32_t>(),
                            (int)S, coef);
     }
@@ -853,8 +1059,12 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
 // allocation was refused (the sweep then reads the cell geometry).  It is
 // built for the handle's sweep order and directions, which do not change
 // after the build, so its address stays valid for the handle's life.
-template <class T> const unsigned char *ensure_coef(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
-    Dags::FaceStream &fs = d->coef[sizeof(T) == 8 ? 1 : 0];
+// positions: the variant whose interior neighbours are positions in the sweep
+// order (read with the sweep-order copy of psi); it needs a temporary [M][N]
+// int32 table of positions while it is filled.
+template <class T>
+const unsigned char *ensure_coef(Dags *d, const SweepArgs<T> &a, cudaStream_t s, bool positions = false) {
+    Dags::FaceStream &fs = (positions ? d->pcoef : d->coef)[sizeof(T) == 8 ? 1 : 0];
     if (fs.failed) return nullptr;
     const int maxf = a.FS <= 4 ? 4 : a.FS <= 6 ? 6 : 7;
     if (fs.buf.p && fs.maxf == maxf && fs.order == d->s_order && fs.dirs == (const void *)a.dirs)
@@ -868,14 +1078,28 @@ template <class T> const unsigned char *ensure_coef(Dags *d, const SweepArgs<T> 
     }
     unsigned char *out = fs.buf.as<unsigned char>();
     const int grid = grid_for(d->N * d->M, 256, 152 * 64);
-    if (maxf == 4) k_coef_fill<T, 4><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, out);
-    else if (maxf == 6) k_coef_fill<T, 6><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, out);
-    else k_coef_fill<T, 7><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, out);
+    DevBuf posbuf;
+    const int32_t *pos = nullptr;
+    if (positions) {
+        if (posbuf.alloc((size_t)d->N * d->M * 4, s) != JSWEEP_OK) {
+            clear_error();
+            fs.buf.release();
+            fs.failed = true;
+            return nullptr;
+        }
+        k_sweep_positions<<<grid, 256, 0, s>>>(d->s_order, d->N, d->M, posbuf.as<int32_t>());
+        note_launches(1);
+        pos = posbuf.as<int32_t>();
+    }
+    if (maxf == 4) k_coef_fill<T, 4><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, pos, out);
+    else if (maxf == 6) k_coef_fill<T, 6><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, pos, out);
+    else k_coef_fill<T, 7><<<grid, 256, 0, s>>>(d->s_order, a.geo, a.dirs, d->N, d->M, a.FS, a.GS, pos, out);
     if (cudaGetLastError() != cudaSuccess) {
         fs.buf.release();
         fs.failed = true;
         return nullptr;
     }
+    if (positions) cudaStreamSynchronize(s);  // the position table is released on return
     note_launches(1);
     fs.maxf = maxf;
     fs.order = d->s_order;
@@ -887,14 +1111,28 @@ template <class T, int R>
 int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
     constexpr int SPLIT = split_of<T, R>();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
-        const unsigned char *coef = d->opt.no_face_stream ? nullptr : ensure_coef<T>(d, a, s);
+        // default: the face stream with upwind positions and the sweep-order copy of
+        // psi; else the face stream with upwind cell ids; else the cell geometry
+        const unsigned char *coef = nullptr;
+        if (!d->opt.no_face_stream && !d->opt.no_sweep_order_psi && !d->psi_seq_failed) {
+            const size_t bytes = (size_t)d->M * d->N * R * sizeof(T);
+            if (d->psi_seq.ensure(bytes, s) == JSWEEP_OK) {
+                coef = ensure_coef<T>(d, a, s, true);
+                if (coef) a.psi_seq = d->psi_seq.as<T>();
+            } else {
+                clear_error();
+                d->psi_seq_failed = true;
+            }
+        }
+        if (!coef && !d->opt.no_face_stream) coef = ensure_coef<T>(d, a, s);
+        const bool seq = a.psi_seq != nullptr;
         const int64_t Tn = (int64_t)d->ut.slot_ptr.size() - 1;
         const int64_t S = coef ? tail_slot(d) : Tn;  // the tail runs on the face stream
         char key[512];
-        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld", (int)sizeof(T), R,
+        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld/%p", (int)sizeof(T), R,
                  (const void *)a.srcv, (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
                  (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units, (const void *)coef,
-                 (long long)S);
+                 (long long)S, (const void *)a.psi_seq);
         if (!d->graph || d->graph_key != key) {
             if (d->graph) {
                 cudaGraphExecDestroy(d->graph);
@@ -915,9 +1153,15 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
             }
             cudaStream_t cs = d->capture_stream;
             JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            if (a.FS <= 4) capture_levels<T, R, SPLIT, 4>(d, a, cs, coef, S);
-            else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6>(d, a, cs, coef, S);
-            else capture_levels<T, R, SPLIT, 7>(d, a, cs, coef, S);
+            if (seq) {
+                if (a.FS <= 4) capture_levels<T, R, SPLIT, 4, true>(d, a, cs, coef, S);
+                else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6, true>(d, a, cs, coef, S);
+                else capture_levels<T, R, SPLIT, 7, true>(d, a, cs, coef, S);
+            } else {
+                if (a.FS <= 4) capture_levels<T, R, SPLIT, 4, false>(d, a, cs, coef, S);
+                else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6, false>(d, a, cs, coef, S);
+                else capture_levels<T, R, SPLIT, 7, false>(d, a, cs, coef, S);
+            }
             cudaGraph_t g;
             cudaError_t e = cudaStreamEndCapture(cs, &g);
             if (e != cudaSuccess) {
@@ -941,6 +1185,25 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         return JSWEEP_OK;
     }
     if (mode == JSWEEP_MODE_PATCH) return launch_patch<T, R>(d, a, s);
+    // persistent: the queue-driven kernel on the face stream with upwind positions
+    // and the sweep-order copy of psi; per-cell epoch flags otherwise (and for
+    // patch tasks, whose table is laid out for a fixed warp count)
+    if (d->ut.dirmajor && use_queues(d, mode)) {
+        const unsigned char *coef = nullptr;
+        const size_t bytes = (size_t)d->M * d->N * R * sizeof(T);
+        if (d->psi_seq.ensure(bytes, s) == JSWEEP_OK) {
+            coef = ensure_coef<T>(d, a, s, true);
+        } else {
+            clear_error();
+            d->psi_seq_failed = true;
+        }
+        if (coef) {
+            a.psi_seq = d->psi_seq.as<T>();
+            if (a.FS <= 4) return launch_queue<T, R, SPLIT, 4>(d, a, coef, s);
+            if (a.FS <= 6) return launch_queue<T, R, SPLIT, 6>(d, a, coef, s);
+            return launch_queue<T, R, SPLIT, 7>(d, a, coef, s);
+        }
+    }
     if (a.FS <= 4) return launch_dd<T, R, SPLIT, 4>(d, a, s);
     if (a.FS <= 6) return launch_dd<T, R, SPLIT, 6>(d, a, s);
     return launch_dd<T, R, SPLIT, 7>(d, a, s);
@@ -1024,7 +1287,7 @@ template <class T, int R>
 static int run_sweep_t(Dags *d, int nrhs, const void *sigma_t, const void *ang_source, const void *inflow,
                        void *phi_out, void *psi_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, patch_warps<T, R>(d, mode)));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, patch_warps<T, R>(d, mode), use_queues(d, mode)));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
                                   : reinterpret_cast<const T *>(d->mesh->vol32.p);
@@ -1061,7 +1324,7 @@ template <class T, int R>
 static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, const void *q, const void *inflow,
                     double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, patch_warps<T, R>(d, mode)));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, patch_warps<T, R>(d, mode), use_queues(d, mode)));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, nrhs, s));
     JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
     const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
@@ -1134,7 +1397,7 @@ template <class T>
 static int run_si_mg_t(Dags *d, int G, const void *sigma_t, const void *sigma_s, const void *q, const void *inflow,
                        double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
-    JS_TRY(ensure_units(d, mode, 32 / split_of<T, 1>(), s, patch_warps<T, 1>(d, mode)));
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, 1>(), s, patch_warps<T, 1>(d, mode), use_queues(d, mode)));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, 1, 1, s));
     const int64_t N = d->N, Fb = d->mesh->Fb, Tl = d->T;
     const size_t es = sizeof(T);
@@ -1415,6 +1678,7 @@ int si_noalloc_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio, co
     a.srcv = srcv;
     a.inflow = inflow ? infl : nullptr;
     a.psi = psi;
+    a.psi_seq = nullptr;
     a.psi_lag = lag;
     a.lag_ptr = d->lag_ptr.as<int32_t>();
     a.lag_face = d->lag_face.as<int32_t>();

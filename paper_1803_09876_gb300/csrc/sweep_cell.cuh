@@ -31,6 +31,7 @@ template <class T> struct SweepArgs {
     const T *srcv;  // [N][RS]: S V of each rhs at [0, R), sigma_t V at [R]
     const T *inflow;  // [R][Fb] or null
     T *psi;           // [N][M][R]
+    T *psi_seq;       // [M][N][R] in each direction's sweep order, or null (see solve_cell_coef)
     const T *psi_lag; // [Tl][R]
     const int32_t *lag_ptr, *lag_face, *sface;
     const int4 *units;
@@ -119,6 +120,25 @@ template <class T, int R> __device__ __forceinline__ void store_cg(T *p, const T
     } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) __stcg(p + r, v[r]);
+    }
+}
+
+// R contiguous values stored with an L2 eviction policy (16-byte pieces; other
+// sizes are plain stores through L2).
+template <class T, int R> __device__ __forceinline__ void store_hint(T *p, const T (&v)[R], uint64_t pol) {
+    if constexpr (sizeof(T) * R % 16 == 0) {
+        constexpr int n16 = sizeof(T) * R / 16;
+#pragma unroll
+        for (int i = 0; i < n16; ++i) {
+            float4 x;
+            memcpy(&x, reinterpret_cast<const char *>(v) + 16 * i, 16);
+            asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(
+                             reinterpret_cast<float4 *>(p) + i),
+                         "f"(x.x), "f"(x.y), "f"(x.z), "f"(x.w), "l"(pol)
+                         : "memory");
+        }
+    } else {
+        store_cg<T, R>(p, v);
     }
 }
 
@@ -321,10 +341,19 @@ template <class T, int MAXF> constexpr int coef_record_bytes() {
 // `upwind_ready()` is called after every load that does not depend on other
 // cells and before the upwind psi reads; it returns false to abandon the cell
 // (a bounded wait that gave up).
-template <class T, int R, int SPLIT, int MAXF, class Ready>
+// SEQ: the record's neighbour entries of interior faces are positions in
+// direction m's sweep order, not cell ids; upwind values are read from the
+// sweep-order copy psi_seq[m][pos][R], and the result is stored at position
+// `idx` (= m N + pos) of that copy as well as in the cell-major psi (with an
+// evict-first hint: its next reader is the phi reduction after the sweep).
+// A slot's cells then write one contiguous run, and the upwind values come
+// from the runs the slots just before wrote, which are still in L2; in the
+// cell-major layout each 32-byte piece sits in a 128-byte line whose other
+// pieces (the cell's other directions) are written at other times.
+template <class T, int R, int SPLIT, int MAXF, bool SEQ = false, class Ready>
 __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
                                                 const unsigned char *rec, uint64_t pol_stream,
-                                                Ready upwind_ready) {
+                                                Ready upwind_ready, int64_t idx = 0) {
     constexpr int RH = R / SPLIT;
     constexpr int RB = coef_record_bytes<T, MAXF>();
     if (!JS_IN_RANGE(a, c, a.N, 1)) return true;  // bounds-checked builds: skip a bad cell id
@@ -367,7 +396,8 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
                 if ((lagk >> k) & 1u) {
                     load_ro<T, RH>(a.psi_lag + (int64_t)lagj[k] * R + sub * RH, up);
                 } else if (JS_IN_RANGE(a, nb, a.N, 2)) {
-                    load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
+                    if constexpr (SEQ) load_cg<T, RH>(a.psi_seq + ((int64_t)m * a.N + nb) * R + sub * RH, up);
+                    else load_cg<T, RH>(a.psi + ((int64_t)nb * a.M + m) * R + sub * RH, up);
                 } else {
 #pragma unroll
                     for (int r = 0; r < RH; ++r) up[r] = T(0);
@@ -388,7 +418,12 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
     T out[RH];
 #pragma unroll
     for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
-    store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
+    if constexpr (SEQ) {
+        store_cg<T, RH>(a.psi_seq + idx * R + sub * RH, out);
+        store_hint<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out, pol_stream);
+    } else {
+        store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
+    }
     return true;
 }
 

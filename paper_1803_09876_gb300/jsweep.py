@@ -89,7 +89,7 @@ class jsweep_options(ctypes.Structure):
         ("eager_search_max", ctypes.c_int),
         ("no_face_stream", ctypes.c_int),
         ("tail_units", ctypes.c_int),
-        ("reserved", ctypes.c_int * 1),
+        ("no_sweep_order_psi", ctypes.c_int),
     ]
 
 

@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 MODES = [dict(sweep_mode=1), dict(sweep_mode=2), dict(sweep_mode=2, priority=1, cluster_cells=7),
          dict(sweep_mode=2, priority=2, cluster_cells=1), dict(sweep_mode=1, cluster_cells=5),
          dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=3, cluster_cells=3),
-         dict(sweep_mode=3), dict(sweep_mode=3, patch_cells=64), dict(sweep_mode=1, tail_units=64)]
+         dict(sweep_mode=3), dict(sweep_mode=3, patch_cells=64), dict(sweep_mode=1, tail_units=64),
+         dict(sweep_mode=1, no_sweep_order_psi=1)]
 
 
 def _torch():
@@ -212,28 +213,88 @@ def test_workload2_full_size_fp32_sweep_and_two_iterations():
     assert rel_err(phi.cpu().numpy(), phi_ref) < TOL_F32
 
 
-def test_workload3_full_size_sampled_psi_and_phi_reduction():
-    # 128^3, 288 directions, 8 right-hand sides, FP32, persistent schedule as
-    # timed by the benchmark: psi of sampled directions against the oracle;
-    # phi against an FP64 sum of the GPU's own psi (checks the reduction).
+def _bench_options(**override):
+    """jsweep_options fields of the benchmark's default line (bench.py)."""
+    import bench
+    opts = bench.sweep_options(bench.parse([]))
+    opts.update(override)
+    return opts
+
+
+def _oracle_phi_all_directions(wl, dirs, w, src, chunk=36):
+    """phi of one oracle sweep over every direction, built and swept chunk by
+    chunk of directions (bounded host memory); FP64 sums."""
+    nt = oracle.max_threads()
+    phi = None
+    for m0 in range(0, len(dirs), chunk):
+        o = oracle.build_dags(wl, dirs[m0:m0 + chunk])
+        p, _, _ = o.sweep(wl["sigma_t"], src, w[m0:m0 + chunk], nthreads=nt)
+        phi = p if phi is None else phi + p
+        del o
+    return phi
+
+
+def test_workload3_full_size_benchmark_configuration_against_oracle():
+    # 128^3, 288 directions, 8 right-hand sides, FP32, with the options the
+    # benchmark times (bench.sweep_options of its default arguments): the full
+    # phi of one sweep against the oracle's phi over all 288 directions, and
+    # psi of sampled directions against the oracle's psi.  This reaches what
+    # only the full size reaches: 64-bit psi and face-record offsets, grid
+    # sizes, 1,859 schedule slots.  The persistent queue-driven schedule must
+    # give the same bits.
     torch = _torch()
     wl = make_workload(3)
     dirs, w = oracle.product_quadrature(*wl["spec"]["quad"])
-    g = build(wl, dirs, w, sweep_mode=2, priority=2)
+    g = build(wl, dirs, w, **_bench_options())
     N, M, R = wl["n_cells"], len(dirs), 8
     src = wl["q"] / (4 * math.pi)
     psi = torch.empty((R, M, N), dtype=torch.float32, device="cuda")
-    phi = J().jsweep_sweep(g, tensor(wl["sigma_t"], torch.float32), tensor(src, torch.float32), psi_out=psi)
+    sig_t, src_t = tensor(wl["sigma_t"], torch.float32), tensor(src, torch.float32)
+    phi = J().jsweep_sweep(g, sig_t, src_t, psi_out=psi)
     sample = [0, 37, 100, 143, 200, 287]
+    psi_s = psi[:, sample, :].cpu().numpy()
+    del psi
+    phi_np = phi.cpu().numpy()
+    # the same sweep again (lagged values back to zero) on the persistent schedule
+    g.reset_lag()
+    set_opts(g, **_bench_options(sweep_mode=2))
+    phi_q = J().jsweep_sweep(g, sig_t, src_t)
+    same_bits = torch.equal(phi_q.cpu(), phi.cpu())
+    del g
+    torch.cuda.empty_cache()
     o = oracle.build_dags(wl, dirs[sample])
     _, psi_ref, _ = o.sweep(wl["sigma_t"], src, w[sample], want_psi=True, nthreads=oracle.max_threads())
-    psi_s = psi[:, sample, :].cpu().numpy()
     for i in range(len(sample)):
         assert rel_err(psi_s[:, i, :], psi_ref[:, i, :]) < TOL_F32
-    acc = torch.zeros((R, N), dtype=torch.float64, device="cuda")
-    for m in range(M):
-        acc += float(w[m]) * psi[:, m, :].double()
-    assert rel_err(phi.double().cpu().numpy(), acc.cpu().numpy()) < 1e-6
+    del o, psi_ref
+    phi_ref = _oracle_phi_all_directions(wl, dirs, w, src)
+    assert rel_err(phi_np, phi_ref) < TOL_F32
+    assert same_bits
+
+
+def test_workload3_downscaled_converged_fp32_source_iteration():
+    # workload 3 at 32^3 (c = 0.8, 8 right-hand sides, 288 directions): FP32
+    # source iteration converged to 1e-6 against the oracle converged to the
+    # same tolerance (the truncation error tol c / (1 - c) = 4e-6 stays inside
+    # the FP32 tolerance), with the benchmark's options and the persistent one
+    torch = _torch()
+    wl = make_workload(3, n=32)
+    dirs, w = oracle.product_quadrature(*wl["spec"]["quad"])
+    o = oracle.build_dags(wl, dirs)
+    assert o.n_lag_total > 0
+    phi_ref, it_ref, _, conv, _ = o.source_iterate(wl["sigma_t"], wl["c_ratio"], wl["q"], w, 1e-6, 1000,
+                                                   nthreads=oracle.max_threads())
+    assert conv
+    args = (tensor(wl["sigma_t"], torch.float32), tensor(wl["c_ratio"], torch.float32),
+            tensor(wl["q"], torch.float32))
+    outs = []
+    for opts in (_bench_options(), _bench_options(sweep_mode=2)):
+        g = build(wl, dirs, w, **opts)
+        phi, it, res, ok = J().jsweep_source_iterate(g, *args, tol=1e-6, max_iters=1000)
+        assert ok and res < 1e-6 and abs(it - it_ref) <= 2
+        assert rel_err(phi.cpu().numpy(), phi_ref) < TOL_F32
+        outs.append(phi.cpu())
+    assert torch.equal(outs[0], outs[1])
 
 
 @pytest.mark.parametrize("mode", [2, 3], ids=["persistent", "patch_programs"])
@@ -325,7 +386,9 @@ def test_face_stream_and_every_schedule_give_the_same_bits(prec):
         srcs = [rng.uniform(0.0, 1.0, (R, N)) for _ in range(2)]
         outs = []
         for opts in (dict(sweep_mode=1), dict(sweep_mode=1, no_face_stream=1),
+                     dict(sweep_mode=1, no_sweep_order_psi=1),
                      dict(sweep_mode=1, tail_units=1 << 30), dict(sweep_mode=1, tail_units=40),
+                     dict(sweep_mode=1, tail_units=40, no_sweep_order_psi=1),
                      dict(sweep_mode=2), dict(sweep_mode=3, patch_cells=64)):
             g = build(mesh, dirs, w, **opts)
             outs.append([J().jsweep_sweep(g, tensor(sig, dt), tensor(s, dt)).cpu() for s in srcs])

@@ -4,11 +4,14 @@ jsweep_source_iterate_noalloc exists for callers that cannot allocate device
 memory while they run (a host application that owns the device's memory
 budget, or a loop that cannot afford the device-wide synchronisation of
 cudaMalloc/cudaFree).  These checks call both entry points through the C ABI on
-the same inputs, twice in a row, and require the same results within the
-parity tolerances used everywhere else; they also check that the calls make no
-allocation through the installed (torch) allocator and that a problem larger
-than the fixed scratch array is refused.  This file is collected last so that a
-run stopping at its first failure has run everything else first.
+the same inputs, twice in a row.  Both run the same per-cell solve, emission,
+phi reduction and residual kernels, so they must agree bit for bit (same
+iteration count, same residual, same phi); each result is also checked against
+the FP64 oracle's converged solution within the parity tolerance of its
+precision.  The checks also require that the calls make no allocation through
+the installed (torch) allocator and that a problem larger than the fixed
+scratch array is refused.  This file is collected last so that a run stopping
+at its first failure has run everything else first.
 """
 
 import numpy as np
@@ -32,11 +35,14 @@ def _compare(mesh, dirs, w, sig, c, q, dtype, tol, rel_tol, inflow=None):
     args = (tensor(sig, dtype), tensor(c, dtype), tensor(q, dtype))
     infl = None if inflow is None else tensor(inflow, dtype)
     R, N = q.shape
+    ref_phi, _, _, conv, _ = oracle.build_dags(mesh, dirs).source_iterate(
+        sig, c, q, w, tol, 2000, inflow=inflow, nthreads=oracle.max_threads())
+    assert conv
     outs = []
     for _ in range(2):
         phi, it, res, ok = js.jsweep_source_iterate(g, *args, inflow=infl, tol=tol, max_iters=2000)
         assert ok
-        outs.append((phi.cpu().numpy(), it))
+        outs.append((phi.cpu().numpy(), it, res))
     phi_na = torch.empty((R, N), dtype=dtype, device="cuda")
     torch.cuda.synchronize()
     before = _alloc_count(torch)
@@ -45,12 +51,13 @@ def _compare(mesh, dirs, w, sig, c, q, dtype, tol, rel_tol, inflow=None):
         phi, it, res, ok = js.jsweep_source_iterate_noalloc(g, *args, phi_na, inflow=infl, tol=tol,
                                                              max_iters=2000)
         assert ok and res < tol
-        na.append((phi.cpu().numpy(), it))
+        na.append((phi.cpu().numpy(), it, res))
     torch.cuda.synchronize()
     assert _alloc_count(torch) == before  # nothing was allocated through the installed allocator
-    for (ref, it_ref), (got, it_got) in zip(outs, na):
-        assert it_got == it_ref
-        assert rel_err(got, ref) < rel_tol
+    for (ref, it_ref, res_ref), (got, it_got, res_got) in zip(outs, na):
+        assert it_got == it_ref and res_got == res_ref
+        assert np.array_equal(got, ref)  # same kernels: the same bits
+        assert rel_err(got, ref_phi) < rel_tol  # and the oracle's fixed point
     return g
 
 
