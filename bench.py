@@ -47,7 +47,14 @@ METRIC = "cell-angle updates/s"
 # options (a smaller case than the timed 128^3 one, scaled by the cell-directions a launch
 # processes).  The figure belongs to the kernel sources it was taken on (SHA-256 of the files
 # below, first 16 hex digits); when they differ the line reports no traffic.
-SWEEP_TRAFFIC = None  # {"sources_sha16": ..., "bytes_per_cell_dir": ..., "capture": ...}
+SWEEP_TRAFFIC = {
+    "sources_sha16": "e0caa9f8539a06f3",
+    "bytes_per_cell_dir": 177.2,
+    "capture": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none -k "
+                "regex:k_sweep_level_coef -s 440 -c 3 on bench.py --n 64 --sweeps 1: 111.0 MB over the 626,420 "
+                "cell-directions of slots 440-442 (102.8 B read + 74.4 B written per cell-direction), scaled to "
+                "the 128^3 sweep; the smaller mesh keeps more of a slot in L2, so this is a lower bound"),
+}
 SWEEP_SOURCES = ("paper_1803_09876_gb300/csrc/sweep.cu", "paper_1803_09876_gb300/csrc/sweep_cell.cuh")
 # source-iteration sweeps of one benchmark step (128^3, tol 1e-6): the count the GPU arm
 # measures (every schedule gives the same bits, so the same count); the reference arm uses it
@@ -66,7 +73,9 @@ def parse(argv=None):
     p.add_argument("--n", type=int, default=128, help="hex edge (128 = the benchmark workload)")
     p.add_argument("--mode", type=int, default=1, help="1 level-synchronous (CUDA graph), 2 data-driven persistent")
     p.add_argument("--priority", type=int, default=0)
-    p.add_argument("--layering", type=int, default=0, help="0 octant-aligned layers, 1 longest-path levels")
+    p.add_argument("--layering", type=int, default=1,
+                   help="1 longest-path levels (default: the octant-aligned layers of 0 cost more to build than "
+                        "the 22 sweeps of a step win back)")
     p.add_argument("--cluster", type=int, default=32)
     p.add_argument("--no-face-stream", action="store_true",
                    help="level-synchronous sweeps read the cell geometry instead of the precomputed face stream")
@@ -961,7 +970,8 @@ def run_mg(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": MG_WORKLOAD, "cells": N, "directions": M,
                        "groups": G, "sweep_mode": args.mode, "si_iterations_per_step": iters / args.steps,
-                       "groups_swept": "one after the other, each a single-rhs sweep"},
+                       "groups_swept": ("one after the other, each a single-rhs sweep" if args.no_face_stream
+                                        else "together, riding the right-hand-side dimension of one sweep")},
             "phases_ms": {"dag_build_mean": build_ms / args.steps,
                           "source_iteration_mean": ms / args.steps - build_ms / args.steps}}
     print(json.dumps(line), flush=True)
@@ -1011,6 +1021,7 @@ def run_reference_mg(args):
 def run_sweeps(args):
     """Build the graphs of the workload once, then args.sweeps plain sweeps
     (the launch sequence that per-kernel ncu captures skip into)."""
+    import numpy as np
     import torch
 
     from inputs import make_workload
@@ -1034,8 +1045,17 @@ def run_sweeps(args):
         J.jsweep_sweep(dags, sig, src, phi_out=phi)
         tm = dags.timing()
         out.append({"sweep_ms": tm["sweep_ms"], "phi_ms": tm["phi_ms"], "launches": tm["sweep_launches"]})
+    # cell-directions of each level-synchronous launch (non-empty schedule slots in
+    # launch order): what a capture of some of the slot kernel's launches covers
+    slot = {}
+    for m in range(M):
+        _, ptr = dags.schedule(m)
+        for t, k in enumerate(np.diff(ptr)):
+            slot[t] = slot.get(t, 0) + int(k)
+    per_launch = [slot[t] for t in sorted(slot) if slot[t] > 0]
     print(json.dumps({"workload": f"hex{args.n}_{M}dirs_{R}rhs", "mode": args.mode, "cells": N, "directions": M,
-                      "build_ms": dags.timing()["build_ms"], "sweeps": out}), flush=True)
+                      "build_ms": dags.timing()["build_ms"], "sweeps": out,
+                      "slot_cell_dirs": per_launch if args.mode == 1 else None}), flush=True)
 
 
 def main():

@@ -129,45 +129,121 @@ __device__ __forceinline__ void load_nbr8(const BuildCtx &c, int32_t v, int32_t 
     nb[4] = b.x; nb[5] = b.y; nb[6] = b.z; nb[7] = b.w;
 }
 
-__global__ void k_classify(BuildCtx c) {
-    const int64_t total = c.N * c.M;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t m = idx / c.N;
-        int32_t v = (int32_t)(idx - m * c.N);
-        const double *o = c.dirs + 3 * m;
+// Face classification, cell by cell (one thread per cell v, a loop over the
+// directions; block b starts at direction b mod M so that the blocks' list
+// counters are spread over the directions).  The cell's faces, neighbours and
+// normals are read once for all directions.
+// Sign of the FP64 expression ((n_x O_x) + (n_y O_y)) + (n_z O_z): the FP32
+// evaluation of the same expression on the rounded inputs differs from the
+// exact dot product by at most about 6 * 2^-24 * sum |n_i O_i| <= 4e-7 for unit
+// vectors, so when its magnitude exceeds 1e-6 its sign is the exact sign, and
+// so the sign of the FP64 evaluation (whose error is below 1e-15); otherwise the
+// FP64 expression itself decides.  The signs are those of the FP64 evaluation
+// in every case.
+// Per-block lists: the pushes of a block for a direction reserve their slots
+// with one atomic (list order carries no meaning; see push_warp).
+constexpr int kClassifyThreads = 256;
+
+__global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const float *dirs32) {
+    extern __shared__ unsigned char cls_smem[];
+    uint8_t *sh_cyc = cls_smem;  // [M]: a back edge of the certificate seen in this block
+    __shared__ int wcnt[2][2][kClassifyThreads / 32];
+    __shared__ int gbase[2][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) sh_cyc[m] = 0;
+    const int64_t v64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = v64 < c.N;
+    const int32_t v = live ? (int32_t)v64 : 0;
+    // the cell's faces: FP32 normals oriented out of v, neighbours, face slots
+    // (a cell's face slots are filled from slot 0 on; empty slots hold -1)
+    float nx[kMaxFaces], ny[kMaxFaces], nz[kMaxFaces];
+    int32_t nb[kMaxFaces], sf[kMaxFaces];
+#pragma unroll
+    for (int k = 0; k < kMaxFaces; ++k) {
+        const int32_t q = (live && k < c.FS) ? c.sface[(int64_t)v * c.FS + k] : -1;
+        sf[k] = q;
+        nb[k] = q >= 0 ? c.nbr[(int64_t)v * c.FS + k] : -1;
+        const double *n = c.normal + 3 * (int64_t)(q >= 0 ? q >> 1 : 0);
+        nx[k] = q >= 0 ? (float)n[0] : 0.f;
+        ny[k] = q >= 0 ? (float)n[1] : 0.f;
+        nz[k] = q >= 0 ? (float)n[2] : 0.f;
+    }
+    // certificate back edges: bit 8 o + k when lam_o(v) <= lam_o(neighbour k)
+    unsigned long long back = 0;
+    if (c.lam && live) {
+        for (int o = 0; o < 8; ++o) {
+            const int32_t lv = c.lam[(int64_t)o * c.N + v];
+#pragma unroll
+            for (int k = 0; k < kMaxFaces; ++k)
+                if (sf[k] >= 0 && nb[k] >= 0 && lv <= c.lam[(int64_t)o * c.N + nb[k]]) back |= 1ull << (8 * o + k);
+        }
+    }
+    __syncthreads();
+    const int64_t m0 = blockIdx.x % c.M;
+    for (int64_t i = 0; i < c.M; ++i) {
+        const int64_t m = m0 + i < c.M ? m0 + i : m0 + i - c.M;
+        const float ox = __ldg(dirs32 + 3 * m), oy = __ldg(dirs32 + 3 * m + 1), oz = __ldg(dirs32 + 3 * m + 2);
         unsigned in = 0, out = 0;
         int count = 0;
         bool bin = false;
-        for (int k = 0; k < c.FS; ++k) {
-            int32_t sf = c.sface[(int64_t)v * c.FS + k];
-            if (sf < 0) break;
-            int32_t f = sf >> 1;
-            double d = dot_rn(c.normal + 3 * (int64_t)f, o);
-            double s = (sf & 1) ? -d : d;  // outward from v
-            int32_t nb = c.nbr[(int64_t)v * c.FS + k];
-            if (s < 0.0) {
+#pragma unroll
+        for (int k = 0; k < kMaxFaces; ++k) {
+            if (sf[k] < 0) continue;
+            float d32 = __fadd_rn(__fadd_rn(__fmul_rn(nx[k], ox), __fmul_rn(ny[k], oy)), __fmul_rn(nz[k], oz));
+            int sg;  // sign of the FP64 expression, outward from the face's cell0
+            if (fabsf(d32) > 1e-6f) {
+                sg = d32 > 0.f ? 1 : -1;
+            } else {
+                const double d = dot_rn(c.normal + 3 * (int64_t)(sf[k] >> 1), c.dirs + 3 * m);
+                sg = d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+            }
+            if (sf[k] & 1) sg = -sg;  // outward from v
+            if (sg < 0) {
                 in |= 1u << k;
-                if (nb >= 0) {
-                    ++count;
-                    if (c.lam) {
-                        const int64_t lo = (int64_t)c.oct[m] * c.N;
-                        if (c.lam[lo + v] <= c.lam[lo + nb]) c.cyc[m] = 1;  // back edge: not certified
-                    }
-                } else {
-                    bin = true;
-                }
-            } else if (s > 0.0 && nb >= 0) {
+                if (nb[k] >= 0) ++count;
+                else bin = true;
+            } else if (sg > 0 && nb[k] >= 0) {
                 out |= 1u << k;
             }
         }
-        c.inm[idx] = (uint8_t)in;
-        c.outm[idx] = (uint8_t)out;
-        c.cnt[idx] = count;
-        if (count != 0 && bin) c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
-        push_warp(c.front + m * c.N, c.nfront + m, v, count == 0, c.N, c.status);
-        push_warp(c.cand + m * c.N, c.ncand + m, v, count != 0 && bin, c.N, c.status);
+        const int64_t idx = m * c.N + v;
+        if (live) {
+            c.inm[idx] = (uint8_t)in;
+            c.outm[idx] = (uint8_t)out;
+            c.cnt[idx] = count;
+            if (count != 0 && bin) c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
+            const unsigned interior_in = in & (unsigned)(back >> (8 * (c.lam ? c.oct[m] : 0))) & 0xffu;
+            if (interior_in) sh_cyc[m] = 1;  // an active edge against the diagonal's levels
+        }
+        // block-wide slots for the frontier (sources) and candidate lists
+        const bool pf = live && count == 0, pc = live && count != 0 && bin;
+        const unsigned bf = __ballot_sync(0xffffffffu, pf), bc = __ballot_sync(0xffffffffu, pc);
+        const int par = (int)(i & 1);
+        if (lane == 0) {
+            wcnt[par][0][warp] = __popc(bf);
+            wcnt[par][1][warp] = __popc(bc);
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            int tot = 0;
+            for (int w = 0; w < kClassifyThreads / 32; ++w) tot += wcnt[par][threadIdx.x][w];
+            int32_t *cnt = threadIdx.x == 0 ? c.nfront + m : c.ncand + m;
+            gbase[par][threadIdx.x] = tot ? atomicAdd(cnt, tot) : 0;
+        }
+        __syncthreads();
+        if (pf || pc) {
+            const int t = pf ? 0 : 1;
+            int off = gbase[par][t];
+            for (int w = 0; w < warp; ++w) off += wcnt[par][t][w];
+            off += __popc((pf ? bf : bc) & lanemask_lt());
+            int32_t *list = (pf ? c.front : c.cand) + m * c.N;
+            if (off < c.N) list[off] = v;
+            else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+        }
     }
+    __syncthreads();
+    for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x)
+        if (sh_cyc[m]) c.cyc[m] = 1;
 }
 
 // One frontier step for every direction: blockIdx.y = direction.
@@ -1036,8 +1112,20 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.oct = oct_d.as<int32_t>();
     c.cyc = cyc_d.as<int32_t>();
     if (dg) JS_CUDA(cudaMemsetAsync(c.cyc, 0, M * 4, s));
-    k_classify<<<grid_for(MN, 256, 152 * 64), 256, 0, s>>>(c);
-    JS_LAUNCH_CHECK();
+    {
+        std::vector<float> d32(3 * M);
+        for (int64_t i = 0; i < 3 * M; ++i) d32[i] = (float)d->quad->dirs[i];
+        DevBuf dirs32;
+        JS_TRY(dirs32.alloc(3 * M * 4, s));
+        JS_CUDA(cudaMemcpyAsync(dirs32.p, d32.data(), 3 * M * 4, cudaMemcpyHostToDevice, s));
+        const size_t shm = (size_t)M;
+        if (shm > 48 * 1024)
+            JS_CUDA(cudaFuncSetAttribute(k_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        k_classify<<<(unsigned)((N + kClassifyThreads - 1) / kClassifyThreads), kClassifyThreads, shm, s>>>(
+            c, dirs32.as<float>());
+        JS_LAUNCH_CHECK();
+        JS_CUDA(cudaStreamSynchronize(s));  // dirs32 is released on return
+    }
     JS_CUDA(cudaEventRecord(pe[2], s));
 
     // ---- frontier loop with stall resolution
@@ -1072,39 +1160,66 @@ int build_dags(Dags *d, cudaStream_t s) {
     // steps in between accumulate): the lags found do not depend on when a
     // component is found, only how long the cells behind it wait.
     constexpr int kSearchEvery = 4;
+    static_assert(check_every % kSearchEvery == 0 && check_every % 2 == 0, "a check period repeats the steps");
+    const int Beager = d->eager_cap > 0 ? d->eager_cap : B;
+    auto launch_step = [&](cudaStream_t st, int64_t stp, bool marks) {
+        const int cur = (int)(stp & 1);
+        const bool search = stp % kSearchEvery == kSearchEvery - 1;
+        if (marks) prof_mark(0);
+        k_peel<<<dim3(gx, (unsigned)M), 256, 0, st>>>(c, cur);
+        if (marks) prof_mark(1);
+        if (search) k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, st>>>(c, cur ^ 1, walk_max);
+        if (marks) prof_mark(2);
+        if (search) k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, st>>>(c, cur ^ 1, B, Beager);
+        if (marks) prof_mark(3);
+        k_commit<<<64, 256, 0, st>>>(c, cur ^ 1, cur);
+        if (marks) prof_mark(4);
+        return search ? 4 : 2;
+    };
+    // One check period (check_every steps) is captured once into a CUDA graph and
+    // replayed: the steps of a period are the same launches every time (the
+    // step parity and the search steps repeat), and the host then issues one
+    // graph launch per period instead of a few launches per step.
+    struct PeriodGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cap = nullptr;
+        ~PeriodGraph() {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (cap) cudaStreamDestroy(cap);
+        }
+    } period;
+    int period_launches = 0;
+    if (!prof && cudaStreamCreateWithFlags(&period.cap, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaStreamBeginCapture(period.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        for (int k = 0; k < check_every; ++k) period_launches += launch_step(period.cap, k, false);
+        cudaGraph_t g = nullptr;
+        if (cudaStreamEndCapture(period.cap, &g) == cudaSuccess && g) {
+            if (cudaGraphInstantiate(&period.exec, g, 0) != cudaSuccess) period.exec = nullptr;
+            cudaGraphDestroy(g);
+        }
+        cudaGetLastError();  // a failed capture falls back to launches step by step
+    }
     while (true) {
-        int cur = (int)(step & 1);
-        const bool search = step % kSearchEvery == kSearchEvery - 1;
-        prof_mark(0);
-        k_peel<<<dim3(gx, (unsigned)M), 256, 0, s>>>(c, cur);
-        prof_mark(1);
-        if (search) {
-            k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, s>>>(c, cur ^ 1, walk_max);
-            note_launches(1);
+        if (period.exec) {
+            JS_CUDA(cudaGraphLaunch(period.exec, s));
+            note_launches(period_launches);
+            step += check_every;
+        } else {
+            note_launches(launch_step(s, step, prof));
+            if (prof && pev.size() >= 500) {  // fold the events of a few steps into the totals
+                cudaStreamSynchronize(s);
+                for (size_t i = 0; i + 4 < pev.size(); i += 5)
+                    for (int k = 0; k < 4; ++k) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, pev[i + k], pev[i + k + 1]);
+                        kms[k] += ms;
+                    }
+                for (auto e : pev) cudaEventDestroy(e);
+                pev.clear();
+            }
+            JS_CUDA(cudaGetLastError());
+            ++step;
         }
-        prof_mark(2);
-        if (search) {
-            k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, s>>>(c, cur ^ 1, B,
-                                                                     d->eager_cap > 0 ? d->eager_cap : B);
-            note_launches(1);
-        }
-        prof_mark(3);
-        k_commit<<<64, 256, 0, s>>>(c, cur ^ 1, cur);
-        prof_mark(4);
-        if (prof && pev.size() >= 500) {  // fold the events of a few steps into the totals
-            cudaStreamSynchronize(s);
-            for (size_t i = 0; i + 4 < pev.size(); i += 5)
-                for (int k = 0; k < 4; ++k) {
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, pev[i + k], pev[i + k + 1]);
-                    kms[k] += ms;
-                }
-            for (auto e : pev) cudaEventDestroy(e);
-            pev.clear();
-        }
-        note_launches(1);  // peel (walk and resolve counted above); the check below counts commit
-        JS_LAUNCH_CHECK();
-        ++step;
         if (step % check_every == 0) {
             JS_CUDA(cudaMemcpyAsync(status, c.status, 32, cudaMemcpyDeviceToHost, s));
             JS_CUDA(cudaStreamSynchronize(s));

@@ -1,8 +1,11 @@
 // Patch programs (JSWEEP_MODE_PATCH): the patch-centric data-driven sweep of
 // Sec. V-A / V-B on one GPU.
 //
-// The cells are grouped into compact patches (recursive breadth-first
-// bisection of the face graph; the ABI carries no coordinates).  A program is
+// The cells are grouped into compact patches: a k-d split of pseudo-coordinates
+// taken from the levels of the eight octant diagonals (x ~ level(+,+,+) -
+// level(-,+,+), ...; the ABI carries no coordinates), or, when the diagonals'
+// graphs cannot be built, a recursive breadth-first bisection of the face
+// graph.  A program is
 // a (patch, octant) pair.  One block runs a program: it stages the patch's
 // geometry records and source records in shared memory once, then its warps
 // take the octant's directions one after another and sweep each across the

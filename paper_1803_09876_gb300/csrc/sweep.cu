@@ -64,8 +64,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T
 // Level-synchronous sweep reading the precomputed face coefficients (SEQ: the
 // records hold upwind positions and psi has a sweep-order copy, see
 // solve_cell_coef).
-template <class T, int R, int SPLIT, int MAXF, bool SEQ>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// The kernel is bound by how many warps have memory requests in flight: it
+// is compiled for 6 resident blocks of 8 warps per SM (40 registers), which
+// measured faster than 5 (48 registers) or 8 (32 registers, with spills).
+template <class T, int R, int SPLIT, int MAXF, bool SEQ, bool MG>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 6)
     k_sweep_level_coef(SweepArgs<T> a, int64_t u0, int64_t nu, const unsigned char *coef) {
     pdl_launch_next();
     constexpr int RB = coef_record_bytes<T, MAXF>();
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int cell = lane / SPLIT, sub = lane % SPLIT;
     if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
         const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
-        solve_cell_coef<T, R, SPLIT, MAXF, SEQ>(a, u.x, ldg_hint(a.order + idx, pol_stream),
+        solve_cell_coef<T, R, SPLIT, MAXF, SEQ, MG>(a, u.x, ldg_hint(a.order + idx, pol_stream),
                                                 ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB, pol_stream,
                                                 [] {
                                                     pdl_wait_prev();  // upwind values come from earlier slots
@@ -94,7 +97,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // direction (the per-direction dependency graph), so the blocks never wait for
 // one another; the layers before first_layer were swept by the slot launches
 // that precede this one.
-template <class T, int R, int SPLIT, int MAXF, bool SEQ>
+template <class T, int R, int SPLIT, int MAXF, bool SEQ, bool MG>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sweep_tail(SweepArgs<T> a, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, int first_layer,
                  const unsigned char *coef) {
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         for (int p = lpm[l] + cell; p < p1; p += per_pass) {
             if (!JS_IN_RANGE(a, p, a.N, 4)) continue;
             const int64_t idx = (int64_t)m * a.N + p;
-            solve_cell_coef<T, R, SPLIT, MAXF, SEQ>(a, m, ldg_hint(a.order + idx, pol_stream),
+            solve_cell_coef<T, R, SPLIT, MAXF, SEQ, MG>(a, m, ldg_hint(a.order + idx, pol_stream),
                                                     ldg_hint(a.mask + idx, pol_stream), sub, coef + idx * RB,
                                                     pol_stream, [] { return true; }, idx);
         }
@@ -229,8 +232,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // SEQ).
 constexpr int kQueueStride = 32;  // ints between two directions' cursors / counters (128 bytes)
 
-template <class T, int R, int SPLIT, int MAXF>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+template <class T, int R, int SPLIT, int MAXF, bool MG>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 6)
     k_sweep_queue(SweepArgs<T> a, const int64_t *dir_ptr, const unsigned char *coef, unsigned *cursor, int *done,
                   int extra, int *err, long long timeout) {
     constexpr int RB = coef_record_bytes<T, MAXF>();
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         if (cell < u.z && JS_IN_RANGE(a, u.x, a.M, 5) && JS_IN_RANGE(a, (int64_t)u.y + cell, a.N, 4)) {
             const int64_t idx = (int64_t)u.x * a.N + u.y + cell;
             const int want = u.w + extra;
-            ok = solve_cell_coef<T, R, SPLIT, MAXF, true>(
+            ok = solve_cell_coef<T, R, SPLIT, MAXF, true, MG>(
                 a, u.x, ldg_hint(a.order + idx, pol), ldg_hint(a.mask + idx, pol), sub, coef + idx * RB, pol,
                 [&] {
                     if (ld_acquire(dm) >= want) return true;
@@ -496,6 +499,29 @@ __global__ void k_source_prep(const T *sig, const T *src, const T *vol, int64_t 
 #pragma unroll
         for (int r = 0; r < R; ++r) out[r] = r < nrhs ? src[(int64_t)r * N + c] * V : T(0);
         out[R] = sig[c] * V;
+#pragma unroll
+        for (int r = 0; r < RS; ++r) srcv[c * RS + r] = out[r];
+    }
+}
+
+// Source records of G groups riding the right-hand-side dimension: S_g V at
+// [g], sigma_t,g V at [R + g] (src and sig [G][N]; the same products as
+// k_source_prep of each group alone).
+template <class T, int R>
+__global__ void k_source_prep_mg(const T *sig, const T *src, const T *vol, int64_t N, int G, T *srcv) {
+    constexpr int RS = src_stride<R>();
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        const T V = vol[c];
+        T out[RS];
+#pragma unroll
+        for (int r = 0; r < RS; ++r) out[r] = T(0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r < G) {
+                out[r] = src[(int64_t)r * N + c] * V;
+                out[R + r] = sig[(int64_t)r * N + c] * V;
+            }
+        }
 #pragma unroll
         for (int r = 0; r < RS; ++r) srcv[c * RS + r] = out[r];
     }
@@ -904,9 +930,9 @@ template <class T, int R> constexpr int split_of() {
     return (int)(sizeof(T) * R / 16) > 1 ? (int)(sizeof(T) * R / 16) : 1;
 }
 
-template <class T, int R, int SPLIT, int MAXF>
+template <class T, int R, int SPLIT, int MAXF, bool MG>
 int launch_queue(Dags *d, const SweepArgs<T> &a, const unsigned char *coef, cudaStream_t s) {
-    auto kern = k_sweep_queue<T, R, SPLIT, MAXF>;
+    auto kern = k_sweep_queue<T, R, SPLIT, MAXF, MG>;
     int occ = 0;
     JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarpsPerBlock * 32, 0));
     if (occ < 1) occ = 1;
@@ -1013,7 +1039,7 @@ int64_t tail_slot(const Dags *d) {
 // Records the sweep's launches on the capture stream: one launch per slot
 // before the tail slot S, then (S < number of slots) the tail, one block per
 // direction.
-template <class T, int R, int SPLIT, int MAXF, bool SEQ>
+template <class T, int R, int SPLIT, int MAXF, bool SEQ, bool MG>
 void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsigned char *coef, int64_t S) {
     const auto &sp = d->ut.slot_ptr;
     const int64_t Tn = (int64_t)sp.size() - 1;
@@ -1035,7 +1061,7 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         cfg.numAttrs = first ? 0 : 1;
         first = false;
         int64_t u0 = sp[l];
-        if (coef) cudaLaunchKernelEx(&cfg, k_sweep_level_coef<T, R, SPLIT, MAXF, SEQ>, a, u0, nu, coef);
+        if (coef) cudaLaunchKernelEx(&cfg, k_sweep_level_coef<T, R, SPLIT, MAXF, SEQ, MG>, a, u0, nu, coef);
         else cudaLaunchKernelEx(&cfg, k_sweep_level<T, R, SPLIT, MAXF>, a, u0, nu);
     }
     if (S < Tn) {
@@ -1048,7 +1074,7 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = first ? 0 : 1;
-        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF, SEQ>, a, (const int32_t *)d->s_lp,
+        cudaLaunchKernelEx(&cfg, k_sweep_tail<T, R, SPLIT, MAXF, SEQ, MG>, a, (const int32_t *)d->s_lp,
                            (const int64_t *)d->tail_lpoff.as<int64_t>(), (const int32_t *)d->tail_nlev.as<int32_t>(),
                            (int)S, coef);
     }
@@ -1107,7 +1133,9 @@ const unsigned char *ensure_coef(Dags *d, const SweepArgs<T> &a, cudaStream_t s,
     return out;
 }
 
-template <class T, int R>
+// MG: every right-hand side has its own sigma_t (see solve_cell_coef); only the
+// face-stream schedules (level-synchronous, persistent queues) have it.
+template <class T, int R, bool MG = false>
 int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
     constexpr int SPLIT = split_of<T, R>();
     if (mode == JSWEEP_MODE_LEVEL_SYNC) {
@@ -1126,10 +1154,14 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         }
         if (!coef && !d->opt.no_face_stream) coef = ensure_coef<T>(d, a, s);
         const bool seq = a.psi_seq != nullptr;
+        if (MG && !coef) {
+            set_error("per-group cross sections need the face stream");
+            return JSWEEP_ERR_UNIMPLEMENTED;
+        }
         const int64_t Tn = (int64_t)d->ut.slot_ptr.size() - 1;
         const int64_t S = coef ? tail_slot(d) : Tn;  // the tail runs on the face stream
         char key[512];
-        snprintf(key, sizeof(key), "%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld/%p", (int)sizeof(T), R,
+        snprintf(key, sizeof(key), "%d/%d/%d/%p/%p/%p/%p/%p/%p/%lld/%p/%lld/%p", (int)sizeof(T), R, (int)MG,
                  (const void *)a.srcv, (const void *)a.inflow, (const void *)a.psi, (const void *)a.psi_lag,
                  (const void *)a.units, (const void *)a.dirs, (long long)d->ut.n_units, (const void *)coef,
                  (long long)S, (const void *)a.psi_seq);
@@ -1154,13 +1186,13 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
             cudaStream_t cs = d->capture_stream;
             JS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             if (seq) {
-                if (a.FS <= 4) capture_levels<T, R, SPLIT, 4, true>(d, a, cs, coef, S);
-                else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6, true>(d, a, cs, coef, S);
-                else capture_levels<T, R, SPLIT, 7, true>(d, a, cs, coef, S);
+                if (a.FS <= 4) capture_levels<T, R, SPLIT, 4, true, MG>(d, a, cs, coef, S);
+                else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6, true, MG>(d, a, cs, coef, S);
+                else capture_levels<T, R, SPLIT, 7, true, MG>(d, a, cs, coef, S);
             } else {
-                if (a.FS <= 4) capture_levels<T, R, SPLIT, 4, false>(d, a, cs, coef, S);
-                else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6, false>(d, a, cs, coef, S);
-                else capture_levels<T, R, SPLIT, 7, false>(d, a, cs, coef, S);
+                if (a.FS <= 4) capture_levels<T, R, SPLIT, 4, false, MG>(d, a, cs, coef, S);
+                else if (a.FS <= 6) capture_levels<T, R, SPLIT, 6, false, MG>(d, a, cs, coef, S);
+                else capture_levels<T, R, SPLIT, 7, false, MG>(d, a, cs, coef, S);
             }
             cudaGraph_t g;
             cudaError_t e = cudaStreamEndCapture(cs, &g);
@@ -1184,7 +1216,7 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         d->timing.sweep_launches = nodes;
         return JSWEEP_OK;
     }
-    if (mode == JSWEEP_MODE_PATCH) return launch_patch<T, R>(d, a, s);
+    if (mode == JSWEEP_MODE_PATCH && !MG) return launch_patch<T, R>(d, a, s);
     // persistent: the queue-driven kernel on the face stream with upwind positions
     // and the sweep-order copy of psi; per-cell epoch flags otherwise (and for
     // patch tasks, whose table is laid out for a fixed warp count)
@@ -1199,10 +1231,14 @@ int sweep_core(Dags *d, SweepArgs<T> a, int mode, cudaStream_t s) {
         }
         if (coef) {
             a.psi_seq = d->psi_seq.as<T>();
-            if (a.FS <= 4) return launch_queue<T, R, SPLIT, 4>(d, a, coef, s);
-            if (a.FS <= 6) return launch_queue<T, R, SPLIT, 6>(d, a, coef, s);
-            return launch_queue<T, R, SPLIT, 7>(d, a, coef, s);
+            if (a.FS <= 4) return launch_queue<T, R, SPLIT, 4, MG>(d, a, coef, s);
+            if (a.FS <= 6) return launch_queue<T, R, SPLIT, 6, MG>(d, a, coef, s);
+            return launch_queue<T, R, SPLIT, 7, MG>(d, a, coef, s);
         }
+    }
+    if (MG) {
+        set_error("per-group cross sections need the face stream");
+        return JSWEEP_ERR_UNIMPLEMENTED;
     }
     if (a.FS <= 4) return launch_dd<T, R, SPLIT, 4>(d, a, s);
     if (a.FS <= 6) return launch_dd<T, R, SPLIT, 6>(d, a, s);
@@ -1230,13 +1266,13 @@ int check_sweep_error(Dags *d, cudaStream_t s, int mode) {
     return JSWEEP_OK;
 }
 
-template <class T, int R>
+template <class T, int R, bool MG = false>
 int one_sweep(Dags *d, int mode, bool has_inflow, const T *wts, T *phi_dst, int nrhs, cudaStream_t s,
               const T *dirs_override) {
     SweepArgs<T> a = make_args<T>(d, R, has_inflow);
     if (dirs_override) a.dirs = dirs_override;
     JS_CUDA(cudaEventRecord(d->ev[0], s));
-    JS_TRY((sweep_core<T, R>(d, a, mode, s)));
+    JS_TRY((sweep_core<T, R, MG>(d, a, mode, s)));
     JS_CUDA(cudaEventRecord(d->ev[1], s));
     if (d->T > 0) {
         k_lag_update<T, R><<<grid_for(d->T, 256), 256, 0, s>>>(d->psi.as<T>(), d->lag_m.as<int32_t>(),
@@ -1393,10 +1429,109 @@ static int run_si_t(Dags *d, int nrhs, const void *sigma_t, const void *c_ratio,
 // captured level-synchronous graph serves all of them): a group's inflow and
 // lagged values are copied in before its sweep and its lagged values copied
 // out after it.
+// The same iteration with the G <= 8 groups riding the right-hand-side
+// dimension: one sweep per iteration carries every group (per-group sigma_t in
+// the source records, per-group lagged values and inflow rows), on the
+// schedules that read the face stream.  Each group is solved by the same
+// operations as in a one-rhs sweep, so the results are those of the
+// group-by-group iteration, bit for bit.
+template <class T, int R>
+static int run_si_mg_groups_t(Dags *d, int G, const void *sigma_t, const void *sigma_s, const void *q,
+                              const void *inflow, double tol, int max_iters, void *phi_out, int *iters_out,
+                              double *resid_out, cudaStream_t s) {
+    const int mode = resolve_mode(d);
+    JS_TRY(ensure_units(d, mode, 32 / split_of<T, R>(), s, 0, use_queues(d, mode)));
+    JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, R, G, s));
+    JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
+    const int64_t N = d->N, Fb = d->mesh->Fb;
+    const size_t es = sizeof(T);
+    const T *vol = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->mesh->vol64.p)
+                                  : reinterpret_cast<const T *>(d->mesh->vol32.p);
+    const T *w = sizeof(T) == 8 ? reinterpret_cast<const T *>(d->quad->w64.p)
+                                : reinterpret_cast<const T *>(d->quad->w32.p);
+    const double *d64 = nullptr;
+    if (sizeof(T) == 8) JS_TRY(dirs64x4(d, s, &d64));
+    const bool has_inflow = inflow != nullptr;
+    if (has_inflow) {
+        JS_CUDA(cudaMemsetAsync(d->inflow.p, 0, d->inflow.bytes, s));
+        JS_CUDA(cudaMemcpyAsync(d->inflow.p, inflow, (size_t)G * Fb * es, cudaMemcpyDeviceToDevice, s));
+    }
+    DevBuf src_d;
+    const int rc = [&]() -> int {
+        JS_TRY(src_d.alloc((size_t)G * N * es, s));
+        T *bufs[2] = {d->phi_a.as<T>(), d->phi_b.as<T>()};
+        T *phi_old = nullptr;  // phi^0 = 0
+        T *phi_new = bufs[0];
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(d->red.p);
+        double *resid_d = reinterpret_cast<double *>(acc + 32);
+        double resid_h[9] = {0};
+        int it = 0;
+        bool conv = false;
+        for (it = 1; it <= max_iters; ++it) {
+            phi_new = bufs[(it - 1) & 1];
+            k_emission_mg<T><<<grid_for((int64_t)G * N, 256, 152 * 16), 256, 0, s>>>(
+                (const T *)sigma_s, (const T *)q, phi_old, N, G, src_d.as<T>());
+            JS_LAUNCH_CHECK();
+            k_source_prep_mg<T, R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>((const T *)sigma_t, src_d.as<T>(), vol,
+                                                                             N, G, d->srcv.as<T>());
+            JS_LAUNCH_CHECK();
+            JS_TRY((one_sweep<T, R, true>(d, mode, has_inflow, w, phi_new, G, s, (const T *)d64)));
+            JS_CUDA(cudaMemsetAsync(acc, 0, 2 * 8 * 8, s));
+            k_resid<T><<<dim3(grid_for(N, 256, 152 * 4), G), 256, 0, s>>>(phi_new, phi_old, N, acc);
+            JS_LAUNCH_CHECK();
+            k_resid_final<<<1, 32, 0, s>>>(acc, G, resid_d);
+            JS_LAUNCH_CHECK();
+            JS_CUDA(cudaMemcpyAsync(resid_h, resid_d, (size_t)(G + 1) * 8, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaStreamSynchronize(s));
+            JS_TRY(check_sweep_error(d, s, mode));
+            phi_old = phi_new;
+            if (resid_h[G] < tol) {
+                conv = true;
+                break;
+            }
+        }
+        if (it > max_iters) it = max_iters;
+        JS_CUDA(cudaMemcpyAsync(phi_out, phi_new, (size_t)G * N * es, cudaMemcpyDeviceToDevice, s));
+        // the handle's lagged values belong to the groups: start later sweeps from 0
+        JS_CUDA(cudaMemsetAsync(d->psi_lag.p, 0, d->psi_lag.bytes, s));
+        JS_CUDA(cudaStreamSynchronize(s));
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, d->ev[0], d->ev[1]);
+        cudaEventElapsedTime(&b, d->ev[2], d->ev[3]);
+        d->timing.sweep_ms = a;
+        d->timing.phi_ms = b;
+        if (iters_out) *iters_out = it;
+        if (resid_out) *resid_out = resid_h[G];
+        if (!conv) {
+            set_error("multigroup source iteration did not reach tol %g in %d iterations (residual %g)", tol,
+                      max_iters, resid_h[G]);
+            return JSWEEP_ERR_NOT_CONVERGED;
+        }
+        return JSWEEP_OK;
+    }();
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
 template <class T>
 static int run_si_mg_t(Dags *d, int G, const void *sigma_t, const void *sigma_s, const void *q, const void *inflow,
                        double tol, int max_iters, void *phi_out, int *iters_out, double *resid_out, cudaStream_t s) {
     const int mode = resolve_mode(d);
+    // groups ride the right-hand sides where the schedule reads the face stream
+    const bool fast = G <= 8 && !d->opt.no_face_stream &&
+                      (mode == JSWEEP_MODE_LEVEL_SYNC || use_queues(d, mode));
+    if (fast) {
+        switch (pad_rhs(G)) {
+            case 1: return run_si_mg_groups_t<T, 1>(d, G, sigma_t, sigma_s, q, inflow, tol, max_iters, phi_out,
+                                                     iters_out, resid_out, s);
+            case 2: return run_si_mg_groups_t<T, 2>(d, G, sigma_t, sigma_s, q, inflow, tol, max_iters, phi_out,
+                                                     iters_out, resid_out, s);
+            case 4: return run_si_mg_groups_t<T, 4>(d, G, sigma_t, sigma_s, q, inflow, tol, max_iters, phi_out,
+                                                     iters_out, resid_out, s);
+            default: return run_si_mg_groups_t<T, 8>(d, G, sigma_t, sigma_s, q, inflow, tol, max_iters, phi_out,
+                                                      iters_out, resid_out, s);
+        }
+    }
     JS_TRY(ensure_units(d, mode, 32 / split_of<T, 1>(), s, patch_warps<T, 1>(d, mode), use_queues(d, mode)));
     JS_TRY(ensure_workspace(d, sizeof(T) == 8 ? JSWEEP_F64 : JSWEEP_F32, 1, 1, s));
     const int64_t N = d->N, Fb = d->mesh->Fb, Tl = d->T;

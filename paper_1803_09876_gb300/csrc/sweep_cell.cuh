@@ -350,11 +350,15 @@ template <class T, int MAXF> constexpr int coef_record_bytes() {
 // from the runs the slots just before wrote, which are still in L2; in the
 // cell-major layout each 32-byte piece sits in a 128-byte line whose other
 // pieces (the cell's other directions) are written at other times.
-template <class T, int R, int SPLIT, int MAXF, bool SEQ = false, class Ready>
+// MG: every right-hand side has its own sigma_t (energy groups riding the
+// right-hand-side dimension): the record holds sigma_t V of each rhs after
+// the S V values, and each rhs has its own denominator, accumulated in the
+// same order as the single one, so a group gives the bits of a one-rhs sweep
+// with its own sigma_t.
+template <class T, int R, int SPLIT, int MAXF, bool SEQ = false, bool MG = false, class Ready>
 __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, int c, unsigned msk, int sub,
                                                 const unsigned char *rec, uint64_t pol_stream,
                                                 Ready upwind_ready, int64_t idx = 0) {
-    constexpr int RH = R / SPLIT;
     constexpr int RB = coef_record_bytes<T, MAXF>();
     if (!JS_IN_RANGE(a, c, a.N, 1)) return true;  // bounds-checked builds: skip a bad cell id
     T dk[MAXF];
@@ -368,9 +372,12 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
         memcpy(nbk, b + MAXF * sizeof(T), MAXF * 4);
     }
     constexpr int RS = src_stride<R>();
-    T num[RH];
-    load_ro<T, RH>(a.srcv + (int64_t)c * RS + sub * RH, num);
-    T den = __ldg(a.srcv + (int64_t)c * RS + R);
+    T num[R / SPLIT], den[MG ? R / SPLIT : 1];
+    load_ro<T, R / SPLIT>(a.srcv + (int64_t)c * RS + sub * (R / SPLIT), num);
+    if constexpr (MG) load_ro<T, R / SPLIT>(a.srcv + (int64_t)c * RS + R + sub * (R / SPLIT), den);
+    else den[0] = __ldg(a.srcv + (int64_t)c * RS + R);
+    constexpr int RH = R / SPLIT;
+    constexpr int ND = MG ? RH : 1;
     unsigned lagk = 0;
     int lagj[MAXF];
     if (msk & 0x80u) {
@@ -412,12 +419,14 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
 #pragma unroll
             for (int r = 0; r < RH; ++r) num[r] = fma_rn(wf, up[r], num[r]);
         } else {
-            den += d > T(0) ? d : T(0);
+            const T dp = d > T(0) ? d : T(0);
+#pragma unroll
+            for (int r = 0; r < ND; ++r) den[r] += dp;
         }
     }
     T out[RH];
 #pragma unroll
-    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
+    for (int r = 0; r < RH; ++r) out[r] = num[r] / den[MG ? r : 0];
     if constexpr (SEQ) {
         store_cg<T, RH>(a.psi_seq + idx * R + sub * RH, out);
         store_hint<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out, pol_stream);
@@ -426,6 +435,7 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
     }
     return true;
 }
+
 
 // phi[r][c] = sum_m w_m psi[c][m][r]: one warp per cell reads the cell's
 // contiguous [M][R] block (coalesced); lane l sums directions l, l+32, ... in

@@ -290,15 +290,15 @@ def handle_resident_bytes(n_cells: int, n_faces: int, n_dirs: int, n_bfaces: int
     lives: its own unit table (one 16-byte unit per 8 or more (direction,
     cell) pairs, 2 bytes per pair), its face-coefficient stream (one record
     per pair), and, when its requests run through jsweep_source_iterate (the
-    solo lane), that call's sweep state: psi, source records, phi ping-pong,
-    inflow and lagged psi, the residual and counter scratch and 1 MiB of
-    slack."""
+    solo lane), that call's sweep state: psi and its copy in sweep order,
+    source records, phi ping-pong, inflow and lagged psi, the residual and
+    counter scratch and 1 MiB of slack."""
     N, F, M = n_cells, n_faces, n_dirs
     extra = (2 + face_record_bytes(faces_per_cell, elem_bytes)) * M * N
     if solo:
         R = 1 if nrhs <= 1 else 2 if nrhs <= 2 else 4 if nrhs <= 4 else 8
         RS = 2 * R if R >= 4 else (4 if R == 2 else 2)
-        extra += (M * N * R * elem_bytes + N * (RS + 2 * nrhs) * elem_bytes
+        extra += (2 * M * N * R * elem_bytes + N * (RS + 2 * nrhs) * elem_bytes
                   + (max(n_bfaces, 1) + F) * R * elem_bytes + (M + 8) * 8 + (1 << 20))
     return extra
 

@@ -268,9 +268,10 @@ def test_face_record_sizes_and_handle_reservation():
     batched = handle_resident_bytes(N, F, M, Fb, 4, 4, 1, solo=False)
     assert batched == (2 + 32) * M * N  # unit table and FP32 tet stream
     solo = handle_resident_bytes(N, F, M, Fb, 4, 4, 1, solo=True)
-    # plus psi (R = 1), source records (2 values) and two phi rows, inflow and lagged psi, scratch
-    assert solo - batched == M * N * 4 + N * (2 + 2) * 4 + (Fb + F) * 4 + (M + 8) * 8 + (1 << 20)
+    # plus psi and its sweep-order copy (R = 1), source records (2 values) and two phi rows, inflow and
+    # lagged psi, scratch
+    assert solo - batched == 2 * M * N * 4 + N * (2 + 2) * 4 + (Fb + F) * 4 + (M + 8) * 8 + (1 << 20)
     # 3 rhs are padded to 4 for psi and the source records (8 values), phi keeps 3 rows
     s3 = handle_resident_bytes(N, F, M, Fb, 6, 8, 3, solo=True)
     assert s3 - handle_resident_bytes(N, F, M, Fb, 6, 8, 3, solo=False) == (
-        M * N * 4 * 8 + N * (8 + 6) * 8 + (Fb + F) * 4 * 8 + (M + 8) * 8 + (1 << 20))
+        2 * M * N * 4 * 8 + N * (8 + 6) * 8 + (Fb + F) * 4 * 8 + (M + 8) * 8 + (1 << 20))
