@@ -49,11 +49,11 @@ METRIC = "cell-angle updates/s"
 # below, first 16 hex digits); when they differ the line reports no traffic.
 SWEEP_TRAFFIC = {
     "sources_sha16": "e0caa9f8539a06f3",
-    "bytes_per_cell_dir": 177.2,
+    "bytes_per_cell_dir": 164.6,
     "capture": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none -k "
-                "regex:k_sweep_level_coef -s 440 -c 3 on bench.py --n 64 --sweeps 1: 111.0 MB over the 626,420 "
-                "cell-directions of slots 440-442 (102.8 B read + 74.4 B written per cell-direction), scaled to "
-                "the 128^3 sweep; the smaller mesh keeps more of a slot in L2, so this is a lower bound"),
+                "regex:k_sweep_level_coef -s 101 -c 3 on bench.py --n 64 --sweeps 1 (the three largest slots): "
+                "226.5 MB over 1,376,323 cell-directions (93.2 B read + 71.4 B written per cell-direction), scaled "
+                "to the 128^3 sweep; the smaller mesh keeps more of a slot in L2, so this is a lower bound"),
 }
 SWEEP_SOURCES = ("paper_1803_09876_gb300/csrc/sweep.cu", "paper_1803_09876_gb300/csrc/sweep_cell.cuh")
 # source-iteration sweeps of one benchmark step (128^3, tol 1e-6): the count the GPU arm
@@ -614,31 +614,40 @@ def run_batch(args):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
     del b_full
 
-    # one problem at a time through the plain single-problem path
+    # one problem at a time through the plain single-problem path (its default
+    # schedule, sweep-order psi and face stream): every problem on a fresh handle,
+    # one untimed solve to build its stream and graph, then one timed solve; the
+    # handle is released before the next problem, so the single-problem state of
+    # all 256 problems never has to fit beside the batch's
     def solo_pass():
-        u = 0.0
+        u, ms = 0.0, 0.0
         its_solo = []
-        for g, t, ph in zip(handles, tens, phis):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for p, t, ph in zip(probs, tens, phis):
+            dirs, w = J.jsweep_quadrature_product(*p["spec"]["quad"])
+            g = J.jsweep_build_dags(J.mesh_from_dict(p), J.jsweep_quadrature_create(dirs, w))
+            J.jsweep_source_iterate(g, *t, tol=tol, max_iters=max_iters, phi_out=ph)
+            torch.cuda.synchronize()
+            s0.record(stream)
             _, it, _, _ = J.jsweep_source_iterate(g, *t, tol=tol, max_iters=max_iters, phi_out=ph)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            ms += s0.elapsed_time(s1)
             its_solo.append(it)
             u += float(it) * g.n_cells * g.n_dirs
-        return u, its_solo
+            del g
+        return u, its_solo, ms
 
-    solo_pass()  # warm: per-handle unit tables and graphs
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    u_solo, its_solo = solo_pass()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    solo_ms = e0.elapsed_time(e1)
+    u_solo, its_solo, solo_ms = solo_pass()
     solo_value = u_solo / (solo_ms / 1e3)
 
     # end to end through the batch API with host buffers
     h_in = [tuple(torch.as_tensor(x, dtype=torch.float32).contiguous().pin_memory()
                   for x in (p["sigma_t"], p["c_ratio"], p["q"])) for p in probs]
     h_out = [torch.empty((1, g.n_cells), dtype=torch.float32).pin_memory() for g in handles]
-    b.source_iterate()  # the solo pass switched the handles' unit tables: rebuild them untimed
+    b.source_iterate()  # untimed warm-up after the solo pass
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     u_e2e = 0.0
     for _ in range(args.steps):

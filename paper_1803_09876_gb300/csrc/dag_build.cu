@@ -64,7 +64,8 @@ struct BuildCtx {
     const int4 *nbr8;  // [N][2]: neighbour ids padded to 8 slots
     const double *normal, *dirs;
     int32_t *cnt, *lvl, *stamp, *claim;
-    uint8_t *inm, *outm, *lagm;
+    uchar4 *msk;  // [M][N]: x = incoming-face bits, y = outgoing active-edge bits, z = lagged-face bits
+                  // (one 4-byte record, so a cell's three masks cost one scattered access)
     int32_t *front;   // [2][M][N]
     int32_t *nfront;  // [2][M]
     int32_t *cand;    // [2][M][N]
@@ -208,8 +209,7 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const
         }
         const int64_t idx = m * c.N + v;
         if (live) {
-            c.inm[idx] = (uint8_t)in;
-            c.outm[idx] = (uint8_t)out;
+            c.msk[idx] = make_uchar4((uint8_t)in, (uint8_t)out, 0, 0);
             c.cnt[idx] = count;
             if (count != 0 && bin) c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
             const unsigned interior_in = in & (unsigned)(back >> (8 * (c.lam ? c.oct[m] : 0))) & 0xffu;
@@ -264,8 +264,9 @@ __global__ void k_peel(BuildCtx c, int cur) {
     int processed = 0;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int32_t v = fr[i];
-        const unsigned act = (unsigned)c.inm[base + v] & ~(unsigned)c.lagm[base + v];
-        const unsigned ob = c.outm[base + v];
+        const uchar4 mv = c.msk[base + v];
+        const unsigned act = (unsigned)mv.x & ~(unsigned)mv.z;
+        const unsigned ob = mv.y;
         int32_t nb[8];
         load_nbr8(c, v, nb);
         // all upwind levels in flight together
@@ -298,7 +299,8 @@ __global__ void k_peel(BuildCtx c, int cur) {
 
 // First unfinished active upwind cell of x (slots in increasing face id).
 __device__ __forceinline__ int32_t first_open_pred(const BuildCtx &c, int64_t base, int32_t x) {
-    const unsigned act = (unsigned)c.inm[base + x] & ~(unsigned)c.lagm[base + x];
+    const uchar4 mx = c.msk[base + x];
+    const unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
     int32_t nb[8];
     load_nbr8(c, x, nb);
     int lv[8];
@@ -440,7 +442,8 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
             int32_t x = X[head++];
             int32_t u = -1;
             if (lane < c.FS) {
-                unsigned act = (unsigned)c.inm[base + x] & ~(unsigned)c.lagm[base + x];
+                const uchar4 mx = c.msk[base + x];
+                unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
                 if ((act >> lane) & 1u) {
                     int32_t nb = c.nbr[(int64_t)x * c.FS + lane];
                     if (nb >= 0 && c.lvl[base + nb] < 0) u = nb;
@@ -478,7 +481,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
         while (h < ns) {
             int32_t y = X[Sidx[h++]];
             int32_t w = -1;
-            if (lane < c.FS && ((c.outm[base + y] >> lane) & 1u)) w = c.nbr[(int64_t)y * c.FS + lane];
+            if (lane < c.FS && ((c.msk[base + y].y >> lane) & 1u)) w = c.nbr[(int64_t)y * c.FS + lane];
             unsigned todo = __ballot_sync(0xffffffffu, w >= 0);
             while (todo) {
                 int src = __ffs(todo) - 1;
@@ -504,7 +507,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
             int32_t y = X[Sidx[t]];
             smin = min(smin, y);
             int32_t w = -1, f = INT_MAX;
-            if (lane < c.FS && ((c.outm[base + y] >> lane) & 1u)) {
+            if (lane < c.FS && ((c.msk[base + y].y >> lane) & 1u)) {
                 w = c.nbr[(int64_t)y * c.FS + lane];
                 f = c.sface[(int64_t)y * c.FS + lane] >> 1;
             }
@@ -606,8 +609,8 @@ __global__ void k_commit(BuildCtx c, int nxt, int cur) {
             atomicCAS(&c.status[0], 0, JSWEEP_ERR_CYCLE);
             continue;
         }
-        c.lagm[base + dn] |= (uint8_t)(1u << kd);
-        c.outm[base + up] &= (uint8_t)~(1u << ku);
+        c.msk[base + dn].z |= (uint8_t)(1u << kd);
+        c.msk[base + up].y &= (uint8_t)~(1u << ku);
         int32_t old = atomicSub(&c.cnt[base + dn], 1);
         if (old == 1) push(c.front + (int64_t)nxt * c.M * c.N + base, c.nfront + nxt * c.M + m, dn, c.N, c.status);
         int32_t k = atomicAdd(c.nlag, 1);
@@ -641,15 +644,15 @@ __global__ void k_level_ptr(const uint32_t *skeys, int64_t N, int64_t M, const i
     }
 }
 
-__global__ void k_mask_level_order(const uint8_t *inm, const uint8_t *lagm, const int32_t *order,
-                                   int64_t N, int64_t M, uint8_t *mask) {
+__global__ void k_mask_level_order(const uchar4 *msk, const int32_t *order, int64_t N, int64_t M, uint8_t *mask) {
     const int64_t total = N * M;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t m = idx / N;
         int32_t c = order[idx];
         int64_t src = m * N + c;
-        mask[idx] = (uint8_t)(inm[src] | (lagm[src] ? 0x80u : 0u));
+        const uchar4 ms = msk[src];
+        mask[idx] = (uint8_t)(ms.x | (ms.z ? 0x80u : 0u));
     }
 }
 
@@ -691,7 +694,7 @@ __global__ void k_lag_ptr(const int32_t *lm, int32_t T, int64_t M, int32_t *lag_
 // between (a direction's levels need no other direction).
 __global__ void __launch_bounds__(1024)
     k_kappa_dir(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
-                const uint8_t *inm, const uint8_t *lagm, const int4 *nbr8, int64_t N, const int32_t *oct,
+                const uchar4 *msk, const int4 *nbr8, int64_t N, const int32_t *oct,
                 const float *rho, const int32_t *lam, int32_t *kap) {
     const int64_t m = blockIdx.x;
     const int o = oct[m];
@@ -704,7 +707,8 @@ __global__ void __launch_bounds__(1024)
         for (int32_t pos = p0 + threadIdx.x; pos < p1; pos += blockDim.x) {
             const int32_t c = order[base + pos];
             int32_t k = (int32_t)(r * (float)lam[(int64_t)o * N + c]);
-            const unsigned act = (unsigned)inm[base + c] & ~(unsigned)lagm[base + c];
+            const uchar4 mc = msk[base + c];
+            const unsigned act = (unsigned)mc.x & ~(unsigned)mc.z;
             const int4 a = __ldg(nbr8 + 2 * (int64_t)c), b = __ldg(nbr8 + 2 * (int64_t)c + 1);
             const int32_t nb[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
             int32_t kk[8];
@@ -938,8 +942,8 @@ Dags *build_diagonals(Dags *d, cudaStream_t s) {
 
 // Octant-aligned schedule layers (see jsweep_options.layering) from the levels
 // of the octant diagonals.
-static int octant_layers(Dags *d, const Dags *dg, const std::vector<int32_t> &oct, const uint8_t *inm,
-                         const uint8_t *lagm, const int64_t *lpoff_dev, const int32_t *nlev_dev, cudaStream_t s) {
+static int octant_layers(Dags *d, const Dags *dg, const std::vector<int32_t> &oct, const uchar4 *msk,
+                         const int64_t *lpoff_dev, const int32_t *nlev_dev, cudaStream_t s) {
     const int64_t N = d->N, M = d->M;
     std::vector<float> rho(8, 1.0f);
     for (int o = 0; o < 8; ++o) {
@@ -954,8 +958,8 @@ static int octant_layers(Dags *d, const Dags *dg, const std::vector<int32_t> &oc
     JS_TRY(kap.alloc(N * M * 4, s));
     JS_CUDA(cudaMemcpyAsync(oct_d.p, oct.data(), M * 4, cudaMemcpyHostToDevice, s));
     JS_CUDA(cudaMemcpyAsync(rho_d.p, rho.data(), 8 * 4, cudaMemcpyHostToDevice, s));
-    k_kappa_dir<<<(unsigned)M, 1024, 0, s>>>(d->order.as<int32_t>(), d->lp.as<int32_t>(), lpoff_dev, nlev_dev, inm,
-                                             lagm, d->mesh->nbr8.as<int4>(), N, oct_d.as<int32_t>(),
+    k_kappa_dir<<<(unsigned)M, 1024, 0, s>>>(d->order.as<int32_t>(), d->lp.as<int32_t>(), lpoff_dev, nlev_dev, msk,
+                                             d->mesh->nbr8.as<int4>(), N, oct_d.as<int32_t>(),
                                              rho_d.as<float>(), dg->level.as<int32_t>(), kap.as<int32_t>());
     JS_LAUNCH_CHECK();
     // layer counts, sort by (layer, cell id), layer pointers, mask in layer order
@@ -993,7 +997,7 @@ static int octant_layers(Dags *d, const Dags *dg, const std::vector<int32_t> &oc
         skeys.as<uint32_t>(), N, M, off_d.as<int64_t>(), nl_d.as<int32_t>(), d->klp.as<int32_t>());
     JS_LAUNCH_CHECK();
     JS_TRY(d->kmask.alloc(N * M, s));
-    k_mask_level_order<<<grid_for(N * M, 256, 152 * 64), 256, 0, s>>>(inm, lagm, d->korder.as<int32_t>(), N, M,
+    k_mask_level_order<<<grid_for(N * M, 256, 152 * 64), 256, 0, s>>>(msk, d->korder.as<int32_t>(), N, M,
                                                                       d->kmask.as<uint8_t>());
     JS_LAUNCH_CHECK();
     JS_CUDA(cudaStreamSynchronize(s));
@@ -1026,15 +1030,13 @@ int build_dags(Dags *d, cudaStream_t s) {
     for (int i = 0; i < 6; ++i) d->timing.build_phase_ms[i] = 0.0;
 
     // ---- scratch
-    DevBuf cnt, stamp, claim, wclaim, inm, outm, lagm, front, cand, small, pend, lagall;
+    DevBuf cnt, stamp, claim, wclaim, msk, front, cand, small, pend, lagall;
     JS_TRY(d->level.alloc(MN * 4, s));
     JS_TRY(cnt.alloc(MN * 4, s));
     JS_TRY(stamp.alloc(MN * 4, s));
     JS_TRY(claim.alloc(MN * 4, s));
     JS_TRY(wclaim.alloc(MN * 8, s));
-    JS_TRY(inm.alloc(MN, s));
-    JS_TRY(outm.alloc(MN, s));
-    JS_TRY(lagm.alloc(MN, s));
+    JS_TRY(msk.alloc(MN * 4, s));
     JS_TRY(front.alloc(2 * MN * 4, s));
     JS_TRY(cand.alloc(2 * MN * 4, s));
     // small: nfront[2M] ncand[2M] cidx[M] epoch[M] nproc[M] npend nlag status[4]
@@ -1059,9 +1061,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.stamp = stamp.as<int32_t>();
     c.claim = claim.as<int32_t>();
     c.wclaim = wclaim.as<unsigned long long>();
-    c.inm = inm.as<uint8_t>();
-    c.outm = outm.as<uint8_t>();
-    c.lagm = lagm.as<uint8_t>();
+    c.msk = msk.as<uchar4>();
     c.front = front.as<int32_t>();
     c.cand = cand.as<int32_t>();
     int32_t *sm = small.as<int32_t>();
@@ -1082,7 +1082,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     JS_CUDA(cudaMemsetAsync(c.stamp, 0, MN * 4, s));
     JS_CUDA(cudaMemsetAsync(c.claim, 0, MN * 4, s));
     JS_CUDA(cudaMemsetAsync(c.wclaim, 0, MN * 8, s));
-    JS_CUDA(cudaMemsetAsync(c.lagm, 0, MN, s));
+    JS_CUDA(cudaMemsetAsync(c.msk, 0, MN * 4, s));
     JS_CUDA(cudaMemsetAsync(sm, 0, n_small * 4, s));
     {
         std::vector<int32_t> ones(M, 1);
@@ -1301,7 +1301,7 @@ int build_dags(Dags *d, cudaStream_t s) {
         skeys.as<uint32_t>(), N, M, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), d->lp.as<int32_t>());
     JS_LAUNCH_CHECK();
     JS_TRY(d->mask.alloc(MN, s));
-    k_mask_level_order<<<grid_for(MN, 256, 152 * 64), 256, 0, s>>>(c.inm, c.lagm, d->order.as<int32_t>(), N, M,
+    k_mask_level_order<<<grid_for(MN, 256, 152 * 64), 256, 0, s>>>(c.msk, d->order.as<int32_t>(), N, M,
                                                                     d->mask.as<uint8_t>());
     JS_LAUNCH_CHECK();
 
@@ -1353,7 +1353,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     d->sp_off = d->lp_off;
     d->Smax = d->Lmax;
     if (dg) {
-        int rc = octant_layers(d, dg.get(), oct, c.inm, c.lagm, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), s);
+        int rc = octant_layers(d, dg.get(), oct, c.msk, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), s);
         if (rc != JSWEEP_OK) return rc;
     }
     JS_CUDA(cudaEventRecord(pe[6], s));
