@@ -3,8 +3,14 @@
 // init/input/compute readiness), with cycle breaking and the level-major
 // reorder.
 //
-// Data layout: every per-(direction, cell) array is [M][N] with the cell index
-// fastest, so a direction's cells are contiguous.
+// Data layout: the frontier and candidate lists are per direction ([M][N]).
+// The per-(direction, cell) state of the frontier loop (masks, counts, levels,
+// stamps, claims) is [S / 8][N][8] over direction slots: the directions of an
+// octant get consecutive slots (each octant padded to a multiple of 8), so one
+// 32-byte sector holds a cell's state in 8 directions of one octant.  Those
+// directions peel nearly the same cells at nearly the same step, so their
+// scattered accesses share sectors in L2 instead of each missing to DRAM.  The
+// levels and masks are transposed to [M][N] after the loop.
 //
 // Steps:
 //   1. classify  (one thread per (m, c)): upwind/downwind role of each face of
@@ -88,7 +94,18 @@ struct BuildCtx {
     const int32_t *lam;  // [8][N] or null (no certificate: every direction is treated as cyclic)
     const int32_t *oct;  // [M]
     int32_t *cyc;        // [M]
+    const int32_t *dslot;  // [M]: the direction's state slot (see the data layout above)
 };
+
+// Index of direction m's state of cell v: [slot / 8][N][8].
+struct StateIx {
+    int64_t b;
+    __device__ __forceinline__ int64_t operator()(int32_t v) const { return b + 8 * (int64_t)v; }
+};
+__device__ __forceinline__ StateIx state_ix(const BuildCtx &c, int64_t m) {
+    const int s = c.dslot[m];
+    return StateIx{(int64_t)(s >> 3) * c.N * 8 + (s & 7)};
+}
 
 __device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, int64_t cap,
                                      int32_t *status) {
@@ -122,6 +139,37 @@ __device__ __forceinline__ void push_warp(int32_t *list, int32_t *count, int32_t
     } else {
         atomicCAS(&status[0], 0, JSWEEP_ERR_OOM);
     }
+}
+
+// Slots for na items in list A (counter ca) and nb items in list B (counter
+// cb) for every active lane; lanes with the same key use the same counters and
+// must be contiguous, and the active lanes must be a prefix of the warp.  One
+// atomic per counter and key, both in flight together.  Returns each lane's
+// first slot in ra / rb.
+__device__ __forceinline__ void warp_reserve2(int32_t *ca, int32_t *cb, int na, int nb, uint64_t key, int32_t &ra,
+                                              int32_t &rb) {
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    int xa = na, xb = nb;  // inclusive scans over the active lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ya = __shfl_up_sync(act, xa, o), yb = __shfl_up_sync(act, xb, o);
+        if (lane >= o) {
+            xa += ya;
+            xb += yb;
+        }
+    }
+    const unsigned peers = __match_any_sync(act, key);
+    const int first = __ffs(peers) - 1, last = 31 - __clz(peers);
+    const int a0 = __shfl_sync(act, xa - na, first), b0 = __shfl_sync(act, xb - nb, first);
+    const int a1 = __shfl_sync(act, xa, last), b1 = __shfl_sync(act, xb, last);
+    int32_t ba = 0, bb = 0;
+    if (lane == first) {
+        if (a1 > a0) ba = atomicAdd(ca, a1 - a0);
+        if (b1 > b0) bb = atomicAdd(cb, b1 - b0);
+    }
+    ra = __shfl_sync(act, ba, first) + (xa - na - a0);
+    rb = __shfl_sync(act, bb, first) + (xb - nb - b0);
 }
 
 __device__ __forceinline__ void load_nbr8(const BuildCtx &c, int32_t v, int32_t (&nb)[8]) {
@@ -207,7 +255,7 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const
                 out |= 1u << k;
             }
         }
-        const int64_t idx = m * c.N + v;
+        const int64_t idx = state_ix(c, m)(v);
         if (live) {
             c.msk[idx] = make_uchar4((uint8_t)in, (uint8_t)out, 0, 0);
             c.cnt[idx] = count;
@@ -246,25 +294,81 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const
         if (sh_cyc[m]) c.cyc[m] = 1;
 }
 
-// One frontier step for every direction: blockIdx.y = direction.
-__global__ void k_peel(BuildCtx c, int cur) {
-    const int64_t m = blockIdx.y;
+// Exclusive offsets off[0..M] (shared memory) of per-direction counts
+// count(m), computed by every block from the same counts, so that a step's
+// work over all directions is spread evenly over a fixed grid.
+template <class Count>
+__device__ void block_offsets(int64_t M, Count count, int64_t *off) {
+    __shared__ int64_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (M + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = (int64_t)threadIdx.x * per, hi = min(lo + per, M);
+    int64_t sum = 0;
+    for (int64_t m = lo; m < hi; ++m) sum += count(m);
+    int64_t x = sum;  // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int64_t run = x - sum + (warp ? wsum[warp - 1] : 0);
+    for (int64_t m = lo; m < hi; ++m) {
+        off[m] = run;
+        run += count(m);
+    }
+    if (threadIdx.x == blockDim.x - 1) off[M] = run;
+    __syncthreads();
+}
+
+// Direction of flat work index i: the largest m with off[m] <= i (off[M] > i).
+__device__ __forceinline__ int64_t offset_owner(const int64_t *off, int64_t M, int64_t i) {
+    int64_t lo = 0, hi = M;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One frontier step for every direction: the frontier cells of all
+// directions, concatenated in direction order, are spread over the grid
+// (dynamic shared memory: M + 1 offsets).  Block 0 also counts the step's
+// cells into nproc (every frontier cell is processed exactly once).
+__global__ void __launch_bounds__(256) k_peel(BuildCtx c, int cur) {
+    extern __shared__ int64_t peel_off[];
     const int nxt = cur ^ 1;
-    const int32_t n = c.nfront[cur * c.M + m];
-    const int64_t base = m * c.N;
-    const int32_t *fr = c.front + (int64_t)cur * c.M * c.N + base;
-    int32_t *fn = c.front + (int64_t)nxt * c.M * c.N + base;
-    int32_t *nfn = c.nfront + nxt * c.M + m;
-    const int ci = c.cidx[m];
-    int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
-    int32_t *ncl = c.ncand + ci * c.M + m;
-    const int32_t ep = c.epoch[m];
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.npend = 0;  // read by the last commit
-    const bool cyclic = c.cyc[m] != 0;
-    int processed = 0;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t v = fr[i];
-        const uchar4 mv = c.msk[base + v];
+    const int32_t *nf = c.nfront + cur * c.M;
+    const int64_t N = c.N;
+    block_offsets(c.M, [&](int64_t m) { return (int64_t)min(nf[m], (int32_t)N); }, peel_off);
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *c.npend = 0;  // read by the last commit
+        for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) c.nproc[m] += min(nf[m], (int32_t)N);
+    }
+    const int64_t total = peel_off[c.M];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = offset_owner(peel_off, c.M, i);
+        const int64_t base = m * N;
+        const StateIx g = state_ix(c, m);
+        int32_t *fn = c.front + (int64_t)nxt * c.M * N + base;
+        int32_t *nfn = c.nfront + nxt * c.M + m;
+        const int ci = c.cidx[m];
+        int32_t *cl = c.cand + (int64_t)ci * c.M * N + base;
+        int32_t *ncl = c.ncand + ci * c.M + m;
+        const int32_t ep = c.epoch[m];
+        const bool cyclic = c.cyc[m] != 0;
+        const int32_t v = c.front[(int64_t)cur * c.M * N + base + (i - peel_off[m])];
+        const uchar4 mv = c.msk[g(v)];
         const unsigned act = (unsigned)mv.x & ~(unsigned)mv.z;
         const unsigned ob = mv.y;
         int32_t nb[8];
@@ -272,40 +376,59 @@ __global__ void k_peel(BuildCtx c, int cur) {
         // all upwind levels in flight together
         int lv[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[base + nb[k]] + 1 : 0;
+        for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] + 1 : 0;
         int lev = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) lev = max(lev, lv[k]);
-        c.lvl[base + v] = lev;
+        c.lvl[g(v)] = lev;
         // all downwind decrements in flight together
         int32_t old[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) old[k] = ((ob >> k) & 1u) ? atomicSub(&c.cnt[base + nb[k]], 1) : 0;
+        for (int k = 0; k < 8; ++k) old[k] = ((ob >> k) & 1u) ? atomicSub(&c.cnt[g(nb[k])], 1) : 0;
+        // a decrement to zero makes the cell ready; any other one makes it a
+        // cycle candidate (once per epoch: all stamps in flight together)
+        unsigned rmask = 0, cpre = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if ((ob >> k) & 1u) {
+                if (old[k] == 1) rmask |= 1u << k;
+                else if (cyclic) cpre |= 1u << k;
+            }
+        int32_t sold[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sold[k] = ((cpre >> k) & 1u) ? atomicExch(&c.stamp[g(nb[k])], ep) : ep;
+        unsigned cmask = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (sold[k] != ep) cmask |= 1u << k;
+        // list slots: one atomic per list for the lanes of the same direction
+        int32_t rb, cb;
+        warp_reserve2(nfn, ncl, __popc(rmask), __popc(cmask), (uint64_t)m, rb, cb);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const bool o = ((ob >> k) & 1u) != 0;
-            const int32_t w = nb[k];
-            const bool ready = o && old[k] == 1;
-            const bool cand = o && !ready && cyclic && atomicExch(&c.stamp[base + w], ep) != ep;
-            push_warp(fn, nfn, w, ready, c.N, c.status);
-            push_warp(cl, ncl, w, cand, c.N, c.status);
+            if ((rmask >> k) & 1u) {
+                if (rb < N) fn[rb] = nb[k];
+                else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+                ++rb;
+            }
+            if ((cmask >> k) & 1u) {
+                if (cb < N) cl[cb] = nb[k];
+                else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+                ++cb;
+            }
         }
-        ++processed;
     }
-    // block total of processed cells
-    for (int off = 16; off > 0; off >>= 1) processed += __shfl_down_sync(0xffffffffu, processed, off);
-    if ((threadIdx.x & 31) == 0 && processed) atomicAdd(&c.nproc[m], processed);
 }
 
 // First unfinished active upwind cell of x (slots in increasing face id).
-__device__ __forceinline__ int32_t first_open_pred(const BuildCtx &c, int64_t base, int32_t x) {
-    const uchar4 mx = c.msk[base + x];
+__device__ __forceinline__ int32_t first_open_pred(const BuildCtx &c, StateIx g, int32_t x) {
+    const uchar4 mx = c.msk[g(x)];
     const unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
     int32_t nb[8];
     load_nbr8(c, x, nb);
     int lv[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[base + nb[k]] : 0;
+    for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] : 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if (((act >> k) & 1u) && nb[k] >= 0 && lv[k] < 0) return nb[k];
@@ -329,19 +452,19 @@ constexpr int kSeedCap = 4096;  // cycles kept per direction and step (more wait
 // owned (this epoch) by a lower walker id stops the walk, a higher id is taken
 // over.  The lowest-id walker that reaches a pointer cycle therefore owns the
 // whole cycle and comes back to a cell it owns: that cell is returned (or -1).
-__device__ int32_t claim_walk(const BuildCtx &c, int64_t base, int32_t v, uint32_t me, int32_t ep,
+__device__ int32_t claim_walk(const BuildCtx &c, StateIx g, int32_t v, uint32_t me, int32_t ep,
                               int walk_max) {
     const unsigned long long tag = ((unsigned long long)(uint32_t)ep << 32) | me;
     // a cell whose count is zero is ready (its upwind cells are all done), so
     // it is on no cycle: such a walk ends without claiming anything
     {
-        const int32_t p = first_open_pred(c, base, v);
-        if (p < 0 || c.cnt[base + p] <= 0) return -1;
+        const int32_t p = first_open_pred(c, g, v);
+        if (p < 0 || c.cnt[g(p)] <= 0) return -1;
     }
     int32_t x = v;
     for (int step = 0; step < walk_max && x >= 0; ++step) {
-        if (step > 0 && c.cnt[base + x] <= 0) return -1;
-        unsigned long long *slot = c.wclaim + base + x;
+        if (step > 0 && c.cnt[g(x)] <= 0) return -1;
+        unsigned long long *slot = c.wclaim + g(x);
         unsigned long long old = *((volatile unsigned long long *)slot);
         while (true) {
             if ((int32_t)(old >> 32) == ep) {
@@ -353,7 +476,7 @@ __device__ int32_t claim_walk(const BuildCtx &c, int64_t base, int32_t v, uint32
             if (prev == old) break;
             old = prev;
         }
-        x = first_open_pred(c, base, x);
+        x = first_open_pred(c, g, x);
     }
     return -1;
 }
@@ -378,14 +501,15 @@ __global__ void k_walk(BuildCtx c, int nxt, int walk_max) {
     bool stalled;
     if (!resolve_active(c, m, nxt, &stalled)) return;
     const int64_t base = m * c.N;
+    const StateIx g = state_ix(c, m);
     const int ci = c.cidx[m];
     const int32_t nc = min(c.ncand[ci * c.M + m], (int32_t)c.N);
     const int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
     const int32_t ep = c.epoch[m];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
         const int32_t v = cl[i];
-        if (c.lvl[base + v] >= 0 || c.cnt[base + v] <= 0) continue;
-        const int32_t x = claim_walk(c, base, v, (uint32_t)i + 1u, ep, walk_max);
+        if (c.lvl[g(v)] >= 0 || c.cnt[g(v)] <= 0) continue;
+        const int32_t x = claim_walk(c, g, v, (uint32_t)i + 1u, ep, walk_max);
         if (x >= 0) {
             const int32_t k = atomicAdd(&c.nseeds[m], 1);
             if (k < kSeedCap) c.seeds[m * kSeedCap + k] = x;
@@ -410,6 +534,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
     if (threadIdx.x == 0) new_lags = 0;
     __syncthreads();
     const int64_t base = m * c.N;
+    const StateIx g = state_ix(c, m);
     const int ci = c.cidx[m];
     const int32_t nc = min(c.ncand[ci * c.M + m], (int32_t)c.N);
     const int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
@@ -442,11 +567,11 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
             int32_t x = X[head++];
             int32_t u = -1;
             if (lane < c.FS) {
-                const uchar4 mx = c.msk[base + x];
+                const uchar4 mx = c.msk[g(x)];
                 unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
                 if ((act >> lane) & 1u) {
                     int32_t nb = c.nbr[(int64_t)x * c.FS + lane];
-                    if (nb >= 0 && c.lvl[base + nb] < 0) u = nb;
+                    if (nb >= 0 && c.lvl[g(nb)] < 0) u = nb;
                 }
             }
             unsigned todo = __ballot_sync(0xffffffffu, u >= 0);
@@ -481,7 +606,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
         while (h < ns) {
             int32_t y = X[Sidx[h++]];
             int32_t w = -1;
-            if (lane < c.FS && ((c.msk[base + y].y >> lane) & 1u)) w = c.nbr[(int64_t)y * c.FS + lane];
+            if (lane < c.FS && ((c.msk[g(y)].y >> lane) & 1u)) w = c.nbr[(int64_t)y * c.FS + lane];
             unsigned todo = __ballot_sync(0xffffffffu, w >= 0);
             while (todo) {
                 int src = __ffs(todo) - 1;
@@ -507,7 +632,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
             int32_t y = X[Sidx[t]];
             smin = min(smin, y);
             int32_t w = -1, f = INT_MAX;
-            if (lane < c.FS && ((c.msk[base + y].y >> lane) & 1u)) {
+            if (lane < c.FS && ((c.msk[g(y)].y >> lane) & 1u)) {
                 w = c.nbr[(int64_t)y * c.FS + lane];
                 f = c.sface[(int64_t)y * c.FS + lane] >> 1;
             }
@@ -527,7 +652,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
         }
         // ---- one warp per component records the lag (claimed by its smallest cell)
         if (lane == 0 && best_f != INT_MAX) {
-            if (atomicExch(&c.claim[base + smin], ep) != ep) {
+            if (atomicExch(&c.claim[g(smin)], ep) != ep) {
                 int32_t k = atomicAdd(c.npend, 1);
                 if (k < c.pend_cap) {
                     c.pend[k] = make_int4((int)m, best_f, best_u, best_v);
@@ -544,7 +669,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
             // members become candidates of the next stall
             for (int t = lane; t < ns; t += kWarp) {
                 int32_t y = X[Sidx[t]];
-                if (atomicExch(&c.stamp[base + y], ep + 1) != ep + 1) push(cn, ncn, y, c.N, c.status);
+                if (atomicExch(&c.stamp[g(y)], ep + 1) != ep + 1) push(cn, ncn, y, c.N, c.status);
             }
         }
         __syncwarp();
@@ -562,7 +687,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
             // seeds were dropped: keep this round's candidates for the next stall
             for (int32_t i = 0; i < nc; ++i) {
                 int32_t v = cl[i];
-                if (c.lvl[base + v] < 0 && atomicExch(&c.stamp[base + v], ep + 1) != ep + 1) push(cn, ncn, v, c.N, c.status);
+                if (c.lvl[g(v)] < 0 && atomicExch(&c.stamp[g(v)], ep + 1) != ep + 1) push(cn, ncn, v, c.N, c.status);
             }
         }
         c.ncand[ci * c.M + m] = 0;
@@ -604,17 +729,34 @@ __global__ void k_commit(BuildCtx c, int nxt, int cur) {
         int64_t m = e.x;
         int32_t f = e.y, up = e.z, dn = e.w;
         int64_t base = m * c.N;
+        const StateIx g = state_ix(c, m);
         int kd = slot_of(c, dn, f), ku = slot_of(c, up, f);
         if (kd < 0 || ku < 0) {
             atomicCAS(&c.status[0], 0, JSWEEP_ERR_CYCLE);
             continue;
         }
-        c.msk[base + dn].z |= (uint8_t)(1u << kd);
-        c.msk[base + up].y &= (uint8_t)~(1u << ku);
-        int32_t old = atomicSub(&c.cnt[base + dn], 1);
+        c.msk[g(dn)].z |= (uint8_t)(1u << kd);
+        c.msk[g(up)].y &= (uint8_t)~(1u << ku);
+        int32_t old = atomicSub(&c.cnt[g(dn)], 1);
         if (old == 1) push(c.front + (int64_t)nxt * c.M * c.N + base, c.nfront + nxt * c.M + m, dn, c.N, c.status);
         int32_t k = atomicAdd(c.nlag, 1);
         if (k < c.lag_cap) c.lagall[k] = e; else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+    }
+}
+
+// State words [S / 8][N][8] back to [M][N] (sdir[s] = direction of slot s, or -1
+// for a padding slot): one thread reads a cell's 8 slots (32 bytes).
+__global__ void k_ungroup(const uint32_t *src, const int32_t *sdir, int64_t N, int64_t S, uint32_t *dst) {
+    const int64_t n = S / 8 * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gi = i / N, v = i - gi * N;
+        const uint4 a = reinterpret_cast<const uint4 *>(src)[2 * i], b = reinterpret_cast<const uint4 *>(src)[2 * i + 1];
+        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int32_t m = __ldg(sdir + gi * 8 + j);
+            if (m >= 0) dst[m * N + v] = w[j];
+        }
     }
 }
 
@@ -903,6 +1045,30 @@ static std::vector<int32_t> octant_of(const Dags *d) {
     return oct;
 }
 
+// State slots of the frontier loop: the directions of each octant in index
+// order get consecutive slots; an octant's run is padded to a multiple of 8
+// when that costs at most half as many slots as it has directions (a lone
+// diagonal is not).  Returns S (a multiple of 8); sdir[s] = direction or -1.
+static int64_t state_slots(const std::vector<int32_t> &oct, std::vector<int32_t> &dslot, std::vector<int32_t> &sdir) {
+    const int64_t M = (int64_t)oct.size();
+    dslot.assign(M, -1);
+    int64_t S = 0;
+    for (int o = 0; o < 8; ++o) {
+        int64_t count = 0;
+        for (int64_t m = 0; m < M; ++m)
+            if (oct[m] == o) {
+                dslot[m] = (int32_t)S++;
+                ++count;
+            }
+        const int64_t pad = (8 - S % 8) % 8;
+        if (count > 0 && 2 * pad <= count) S += pad;
+    }
+    S = (S + 7) / 8 * 8;
+    sdir.assign(S, -1);
+    for (int64_t m = 0; m < M; ++m) sdir[dslot[m]] = (int32_t)m;
+    return S;
+}
+
 // Dependency graphs of the 8 octant diagonals (+-1, +-1, +-1)/sqrt(3) over the
 // same mesh (a nested build with longest-path levels).  Returns nullptr (and no
 // error) if that build fails: the diagonals only serve the schedule.
@@ -1029,14 +1195,21 @@ int build_dags(Dags *d, cudaStream_t s) {
     } ev_guard{pe};
     for (int i = 0; i < 6; ++i) d->timing.build_phase_ms[i] = 0.0;
 
-    // ---- scratch
-    DevBuf cnt, stamp, claim, wclaim, msk, front, cand, small, pend, lagall;
-    JS_TRY(d->level.alloc(MN * 4, s));
-    JS_TRY(cnt.alloc(MN * 4, s));
-    JS_TRY(stamp.alloc(MN * 4, s));
-    JS_TRY(claim.alloc(MN * 4, s));
-    JS_TRY(wclaim.alloc(MN * 8, s));
-    JS_TRY(msk.alloc(MN * 4, s));
+    // ---- scratch (per-(direction, cell) state in slot-grouped layout, SN words)
+    std::vector<int32_t> oct = octant_of(d);
+    std::vector<int32_t> dslot, sdir;
+    const int64_t S = state_slots(oct, dslot, sdir), SN = S * N;
+    DevBuf lvl_g, cnt, stamp, claim, wclaim, msk_g, front, cand, small, pend, lagall, dslot_d, sdir_d;
+    JS_TRY(lvl_g.alloc(SN * 4, s));
+    JS_TRY(cnt.alloc(SN * 4, s));
+    JS_TRY(stamp.alloc(SN * 4, s));
+    JS_TRY(claim.alloc(SN * 4, s));
+    JS_TRY(wclaim.alloc(SN * 8, s));
+    JS_TRY(msk_g.alloc(SN * 4, s));
+    JS_TRY(dslot_d.alloc(M * 4, s));
+    JS_TRY(sdir_d.alloc(S * 4, s));
+    JS_CUDA(cudaMemcpyAsync(dslot_d.p, dslot.data(), M * 4, cudaMemcpyHostToDevice, s));
+    JS_CUDA(cudaMemcpyAsync(sdir_d.p, sdir.data(), S * 4, cudaMemcpyHostToDevice, s));
     JS_TRY(front.alloc(2 * MN * 4, s));
     JS_TRY(cand.alloc(2 * MN * 4, s));
     // small: nfront[2M] ncand[2M] cidx[M] epoch[M] nproc[M] npend nlag status[4]
@@ -1057,11 +1230,12 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.normal = mesh->normal.as<double>();
     c.dirs = quad->dirs64.as<double>();
     c.cnt = cnt.as<int32_t>();
-    c.lvl = d->level.as<int32_t>();
+    c.lvl = lvl_g.as<int32_t>();
     c.stamp = stamp.as<int32_t>();
     c.claim = claim.as<int32_t>();
     c.wclaim = wclaim.as<unsigned long long>();
-    c.msk = msk.as<uchar4>();
+    c.msk = msk_g.as<uchar4>();
+    c.dslot = dslot_d.as<int32_t>();
     c.front = front.as<int32_t>();
     c.cand = cand.as<int32_t>();
     int32_t *sm = small.as<int32_t>();
@@ -1078,11 +1252,11 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.lagall = lagall.as<int4>();
     c.lag_cap = lag_cap;
 
-    JS_CUDA(cudaMemsetAsync(c.lvl, 0xff, MN * 4, s));
-    JS_CUDA(cudaMemsetAsync(c.stamp, 0, MN * 4, s));
-    JS_CUDA(cudaMemsetAsync(c.claim, 0, MN * 4, s));
-    JS_CUDA(cudaMemsetAsync(c.wclaim, 0, MN * 8, s));
-    JS_CUDA(cudaMemsetAsync(c.msk, 0, MN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.lvl, 0xff, SN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.stamp, 0, SN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.claim, 0, SN * 4, s));
+    JS_CUDA(cudaMemsetAsync(c.wclaim, 0, SN * 8, s));
+    JS_CUDA(cudaMemsetAsync(c.msk, 0, SN * 4, s));
     JS_CUDA(cudaMemsetAsync(sm, 0, n_small * 4, s));
     {
         std::vector<int32_t> ones(M, 1);
@@ -1091,7 +1265,6 @@ int build_dags(Dags *d, cudaStream_t s) {
     }
     // diagonals of the octants first: their levels certify acyclic directions and
     // give the octant-aligned schedule layers
-    std::vector<int32_t> oct = octant_of(d);
     DevBuf oct_d, cyc_d, seed_d, nseed_d;
     JS_TRY(oct_d.alloc(M * 4, s));
     JS_TRY(cyc_d.alloc(M * 4, s));
@@ -1133,13 +1306,20 @@ int build_dags(Dags *d, cudaStream_t s) {
     const int walk_max = 1 << 15;
     const size_t shmem = (size_t)kResolveWarps * (2 * B + (B + 3) / 4) * 4;
     JS_CUDA(cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
-    const int gx = (int)std::min<int64_t>(std::max<int64_t>(1, N / (256 * 32)), 16);
     const int64_t max_steps = 4 * N + 1024;
     int32_t status[8] = {0, 0, 1, 0, 0, 0, 0, 0};
     int64_t step = 0;
     const int check_every = 8;
     int32_t last_remaining = -1;
     int no_progress_checks = 0;
+    // peel: a grid of resident blocks over the step's frontier cells of every
+    // direction (per-direction offsets in dynamic shared memory)
+    const size_t off_shm = (size_t)(M + 1) * 8;
+    if (off_shm > 48 * 1024)
+        JS_CUDA(cudaFuncSetAttribute(k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)off_shm));
+    int peel_per_sm = 0;
+    JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&peel_per_sm, k_peel, 256, off_shm));
+    const int peel_blocks = device_sm_count() * std::max(1, peel_per_sm);
     // walks of a direction run in parallel over its candidates; a direction has
     // up to tens of thousands of them in a step on large meshes
     const int walk_blocks = (int)std::min<int64_t>(std::max<int64_t>(8, N / (256 * 16)), 64);
@@ -1166,7 +1346,7 @@ int build_dags(Dags *d, cudaStream_t s) {
         const int cur = (int)(stp & 1);
         const bool search = stp % kSearchEvery == kSearchEvery - 1;
         if (marks) prof_mark(0);
-        k_peel<<<dim3(gx, (unsigned)M), 256, 0, st>>>(c, cur);
+        k_peel<<<peel_blocks, 256, off_shm, st>>>(c, cur);
         if (marks) prof_mark(1);
         if (search) k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, st>>>(c, cur ^ 1, walk_max);
         if (marks) prof_mark(2);
@@ -1256,6 +1436,20 @@ int build_dags(Dags *d, cudaStream_t s) {
                      (long long)step, kms[0], kms[1], kms[2], kms[3]);
     }
     JS_CUDA(cudaEventRecord(pe[3], s));
+    // ---- levels and masks back to [M][N]; the loop's state is released
+    DevBuf msk;
+    JS_TRY(d->level.alloc(MN * 4, s));
+    JS_TRY(msk.alloc(MN * 4, s));
+    k_ungroup<<<grid_for(SN / 8, 256, 152 * 16), 256, 0, s>>>(lvl_g.as<uint32_t>(), sdir_d.as<int32_t>(), N, S,
+                                                              d->level.as<uint32_t>());
+    JS_LAUNCH_CHECK();
+    k_ungroup<<<grid_for(SN / 8, 256, 152 * 16), 256, 0, s>>>(msk_g.as<uint32_t>(), sdir_d.as<int32_t>(), N, S,
+                                                              msk.as<uint32_t>());
+    JS_LAUNCH_CHECK();
+    c.lvl = d->level.as<int32_t>();
+    c.msk = msk.as<uchar4>();
+    JS_CUDA(cudaStreamSynchronize(s));  // the allocator may hand the released memory to another stream
+    for (DevBuf *b : {&lvl_g, &msk_g, &cnt, &stamp, &claim, &wclaim, &front, &cand}) b->release();
     // ---- levels per direction
     DevBuf lmax;
     JS_TRY(lmax.alloc(M * 4, s));
