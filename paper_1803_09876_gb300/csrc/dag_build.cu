@@ -117,30 +117,6 @@ __device__ __forceinline__ void push(int32_t *list, int32_t *count, int32_t v, i
     }
 }
 
-// push() for the lanes of a warp at once: the active lanes that want to push
-// to the same list reserve their slots with one atomic (list order is not
-// significant: levels are maxima over upwind cells and the lag rule picks the
-// smallest face of a component, whatever order cells were found in).  Every
-// active lane must call it.
-__device__ __forceinline__ void push_warp(int32_t *list, int32_t *count, int32_t v, bool want, int64_t cap,
-                                          int32_t *status) {
-    const unsigned act = __activemask();
-    const unsigned wanted = __ballot_sync(act, want);
-    if (!want) return;
-    const unsigned peers = __match_any_sync(wanted, (unsigned long long)(uintptr_t)count);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int32_t base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    const int32_t i = base + __popc(peers & ((1u << lane) - 1u));
-    if (i < cap) {
-        list[i] = v;
-    } else {
-        atomicCAS(&status[0], 0, JSWEEP_ERR_OOM);
-    }
-}
-
 // Slots for na items in list A (counter ca) and nb items in list B (counter
 // cb) for every active lane; lanes with the same key use the same counters and
 // must be contiguous, and the active lanes must be a prefix of the warp.  One
@@ -172,10 +148,19 @@ __device__ __forceinline__ void warp_reserve2(int32_t *ca, int32_t *cb, int na, 
     rb = __shfl_sync(act, bb, first) + (xb - nb - b0);
 }
 
-__device__ __forceinline__ void load_nbr8(const BuildCtx &c, int32_t v, int32_t (&nb)[8]) {
-    const int4 a = __ldg(c.nbr8 + 2 * (int64_t)v), b = __ldg(c.nbr8 + 2 * (int64_t)v + 1);
+// The first F neighbour slots of cell v (F <= 8; kernels are compiled for the
+// mesh's face slots rounded up to 4, 6 or 7).
+template <int F>
+__device__ __forceinline__ void load_nbr(const BuildCtx &c, int32_t v, int32_t (&nb)[F]) {
+    static_assert(F >= 4 && F <= 8, "face slots");
+    const int4 a = __ldg(c.nbr8 + 2 * (int64_t)v);
     nb[0] = a.x; nb[1] = a.y; nb[2] = a.z; nb[3] = a.w;
-    nb[4] = b.x; nb[5] = b.y; nb[6] = b.z; nb[7] = b.w;
+    if constexpr (F > 4) {
+        const int4 b = __ldg(c.nbr8 + 2 * (int64_t)v + 1);
+        const int32_t bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int j = 4; j < F; ++j) nb[j] = bb[j - 4];
+    }
 }
 
 // Face classification, cell by cell (one thread per cell v, a loop over the
@@ -189,16 +174,16 @@ __device__ __forceinline__ void load_nbr8(const BuildCtx &c, int32_t v, int32_t 
 // so the sign of the FP64 evaluation (whose error is below 1e-15); otherwise the
 // FP64 expression itself decides.  The signs are those of the FP64 evaluation
 // in every case.
-// Per-block lists: the pushes of a block for a direction reserve their slots
-// with one atomic (list order carries no meaning; see push_warp).
+// List pushes: the pushes of a warp for a direction reserve their slots with
+// one atomic (list order carries no meaning: levels are maxima over
+// upwind cells and the lag rule picks the smallest face of a component,
+// whatever order cells were found in).
 constexpr int kClassifyThreads = 256;
 
 __global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const float *dirs32) {
     extern __shared__ unsigned char cls_smem[];
     uint8_t *sh_cyc = cls_smem;  // [M]: a back edge of the certificate seen in this block
-    __shared__ int wcnt[2][2][kClassifyThreads / 32];
-    __shared__ int gbase[2][2];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) sh_cyc[m] = 0;
     const int64_t v64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = v64 < c.N;
@@ -263,30 +248,24 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const
             const unsigned interior_in = in & (unsigned)(back >> (8 * (c.lam ? c.oct[m] : 0))) & 0xffu;
             if (interior_in) sh_cyc[m] = 1;  // an active edge against the diagonal's levels
         }
-        // block-wide slots for the frontier (sources) and candidate lists
+        // slots for the frontier (sources) and candidate lists: one atomic per
+        // warp and list, only in the few warps that push
         const bool pf = live && count == 0, pc = live && count != 0 && bin;
         const unsigned bf = __ballot_sync(0xffffffffu, pf), bc = __ballot_sync(0xffffffffu, pc);
-        const int par = (int)(i & 1);
-        if (lane == 0) {
-            wcnt[par][0][warp] = __popc(bf);
-            wcnt[par][1][warp] = __popc(bc);
-        }
-        __syncthreads();
-        if (threadIdx.x < 2) {
-            int tot = 0;
-            for (int w = 0; w < kClassifyThreads / 32; ++w) tot += wcnt[par][threadIdx.x][w];
-            int32_t *cnt = threadIdx.x == 0 ? c.nfront + m : c.ncand + m;
-            gbase[par][threadIdx.x] = tot ? atomicAdd(cnt, tot) : 0;
-        }
-        __syncthreads();
-        if (pf || pc) {
-            const int t = pf ? 0 : 1;
-            int off = gbase[par][t];
-            for (int w = 0; w < warp; ++w) off += wcnt[par][t][w];
-            off += __popc((pf ? bf : bc) & lanemask_lt());
-            int32_t *list = (pf ? c.front : c.cand) + m * c.N;
-            if (off < c.N) list[off] = v;
-            else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+        if (bf | bc) {
+            int gf = 0, gc = 0;
+            if (lane == 0) {
+                if (bf) gf = atomicAdd(c.nfront + m, __popc(bf));
+                if (bc) gc = atomicAdd(c.ncand + m, __popc(bc));
+            }
+            gf = __shfl_sync(0xffffffffu, gf, 0);
+            gc = __shfl_sync(0xffffffffu, gc, 0);
+            if (pf || pc) {
+                const int off = pf ? gf + __popc(bf & lanemask_lt()) : gc + __popc(bc & lanemask_lt());
+                int32_t *list = (pf ? c.front : c.cand) + m * c.N;
+                if (off < c.N) list[off] = v;
+                else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+            }
         }
     }
     __syncthreads();
@@ -345,7 +324,8 @@ __device__ __forceinline__ int64_t offset_owner(const int64_t *off, int64_t M, i
 // directions, concatenated in direction order, are spread over the grid
 // (dynamic shared memory: M + 1 offsets).  Block 0 also counts the step's
 // cells into nproc (every frontier cell is processed exactly once).
-__global__ void __launch_bounds__(256) k_peel(BuildCtx c, int cur) {
+template <int F>
+__global__ void __launch_bounds__(256, 5) k_peel(BuildCtx c, int cur) {
     extern __shared__ int64_t peel_off[];
     const int nxt = cur ^ 1;
     const int32_t *nf = c.nfront + cur * c.M;
@@ -371,41 +351,41 @@ __global__ void __launch_bounds__(256) k_peel(BuildCtx c, int cur) {
         const uchar4 mv = c.msk[g(v)];
         const unsigned act = (unsigned)mv.x & ~(unsigned)mv.z;
         const unsigned ob = mv.y;
-        int32_t nb[8];
-        load_nbr8(c, v, nb);
+        int32_t nb[F];
+        load_nbr<F>(c, v, nb);
         // all upwind levels in flight together
-        int lv[8];
+        int lv[F];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] + 1 : 0;
+        for (int k = 0; k < F; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] + 1 : 0;
         int lev = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) lev = max(lev, lv[k]);
+        for (int k = 0; k < F; ++k) lev = max(lev, lv[k]);
         c.lvl[g(v)] = lev;
         // all downwind decrements in flight together
-        int32_t old[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) old[k] = ((ob >> k) & 1u) ? atomicSub(&c.cnt[g(nb[k])], 1) : 0;
+        int32_t old[F];
         // a decrement to zero makes the cell ready; any other one makes it a
-        // cycle candidate (once per epoch: all stamps in flight together)
-        unsigned rmask = 0, cpre = 0;
+        // cycle candidate, once per epoch (stamp).  The stamps are exchanged
+        // together with the decrements: a stamp left on a cell that became
+        // ready only keeps it out of the candidates, where a walk would drop it.
+        int32_t sold[F];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < F; ++k) {
+            const bool o = ((ob >> k) & 1u) != 0;
+            old[k] = o ? atomicSub(&c.cnt[g(nb[k])], 1) : 0;
+            sold[k] = (o && cyclic) ? atomicExch(&c.stamp[g(nb[k])], ep) : ep;
+        }
+        unsigned rmask = 0, cmask = 0;
+#pragma unroll
+        for (int k = 0; k < F; ++k)
             if ((ob >> k) & 1u) {
                 if (old[k] == 1) rmask |= 1u << k;
-                else if (cyclic) cpre |= 1u << k;
+                else if (sold[k] != ep) cmask |= 1u << k;
             }
-        int32_t sold[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sold[k] = ((cpre >> k) & 1u) ? atomicExch(&c.stamp[g(nb[k])], ep) : ep;
-        unsigned cmask = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (sold[k] != ep) cmask |= 1u << k;
         // list slots: one atomic per list for the lanes of the same direction
         int32_t rb, cb;
         warp_reserve2(nfn, ncl, __popc(rmask), __popc(cmask), (uint64_t)m, rb, cb);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < F; ++k) {
             if ((rmask >> k) & 1u) {
                 if (rb < N) fn[rb] = nb[k];
                 else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
@@ -418,21 +398,6 @@ __global__ void __launch_bounds__(256) k_peel(BuildCtx c, int cur) {
             }
         }
     }
-}
-
-// First unfinished active upwind cell of x (slots in increasing face id).
-__device__ __forceinline__ int32_t first_open_pred(const BuildCtx &c, StateIx g, int32_t x) {
-    const uchar4 mx = c.msk[g(x)];
-    const unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
-    int32_t nb[8];
-    load_nbr8(c, x, nb);
-    int lv[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] : 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (((act >> k) & 1u) && nb[k] >= 0 && lv[k] < 0) return nb[k];
-    return -1;
 }
 
 // Index of value v in X[0..size), or -1 (warp-cooperative).
@@ -448,58 +413,74 @@ __device__ __forceinline__ int warp_find(const int32_t *X, int size, int32_t v, 
 constexpr int kResolveWarps = 16;
 constexpr int kSeedCap = 4096;  // cycles kept per direction and step (more wait for the next round)
 
-// Walk x -> first_open_pred(x) from candidate `i` with claimed cells: a cell
+// Walk from candidate v to the first unfinished active upwind cell (in
+// increasing face-slot order), again and again, claiming cells: a cell
 // owned (this epoch) by a lower walker id stops the walk, a higher id is taken
 // over.  The lowest-id walker that reaches a pointer cycle therefore owns the
 // whole cycle and comes back to a cell it owns: that cell is returned (or -1).
+// A cell whose count is zero is ready (its upwind cells are all done), so it
+// is on no cycle: the walk ends there.  Per cell, the count, the claim word,
+// the masks and the neighbours are loaded together, then the upwind levels
+// together with the claim's compare-and-swap (levels and counts do not change
+// while walks run).
+template <int F>
 __device__ int32_t claim_walk(const BuildCtx &c, StateIx g, int32_t v, uint32_t me, int32_t ep,
                               int walk_max) {
     const unsigned long long tag = ((unsigned long long)(uint32_t)ep << 32) | me;
-    // a cell whose count is zero is ready (its upwind cells are all done), so
-    // it is on no cycle: such a walk ends without claiming anything
-    {
-        const int32_t p = first_open_pred(c, g, v);
-        if (p < 0 || c.cnt[g(p)] <= 0) return -1;
-    }
     int32_t x = v;
-    for (int step = 0; step < walk_max && x >= 0; ++step) {
-        if (step > 0 && c.cnt[g(x)] <= 0) return -1;
+    for (int step = 0; step < walk_max; ++step) {
         unsigned long long *slot = c.wclaim + g(x);
+        const int32_t cx = c.cnt[g(x)];
         unsigned long long old = *((volatile unsigned long long *)slot);
+        const uchar4 mx = c.msk[g(x)];
+        int32_t nb[F];
+        load_nbr<F>(c, x, nb);
+        if (cx <= 0) return -1;
+        const unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
+        int lv[F];
+#pragma unroll
+        for (int k = 0; k < F; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] : 0;
         while (true) {
             if ((int32_t)(old >> 32) == ep) {
-                uint32_t owner = (uint32_t)old;
+                const uint32_t owner = (uint32_t)old;
                 if (owner == me) return x;  // closed a cycle of our own
                 if (owner < me) return -1;  // a lower walker owns this path
             }
-            unsigned long long prev = atomicCAS(slot, old, tag);
+            const unsigned long long prev = atomicCAS(slot, old, tag);
             if (prev == old) break;
             old = prev;
         }
-        x = first_open_pred(c, g, x);
+        // first unfinished active upwind cell (slots in increasing face id)
+        int32_t p = -1;
+#pragma unroll
+        for (int k = F - 1; k >= 0; --k)
+            if (((act >> k) & 1u) && nb[k] >= 0 && lv[k] < 0) p = nb[k];
+        if (p < 0) return -1;
+        x = p;
     }
     return -1;
 }
 
-// Cycle resolution runs every step for every unfinished direction that is not
-// certified acyclic and has new candidates (or has stalled).  A component is
-// resolved as soon as a walk can close it, not only when the whole direction
-// has stalled, so that the cells behind it are not held back until the rest of
-// the front drains.  The closure test only ever accepts a set closed under
-// unfinished upwind cells, which contains the whole component whatever the
-// frontier holds.
-__device__ __forceinline__ bool resolve_active(const BuildCtx &c, int64_t m, int nxt, bool *stalled) {
+// Cycle resolution runs in every unfinished direction that has stalled and,
+// in an eager search, also in every one that is not certified acyclic and has
+// new candidates.  A component is then resolved as soon as a walk can close
+// it, not only when the whole direction has stalled, so that the cells behind
+// it are not held back until the rest of the front drains.  The closure test
+// only ever accepts a set closed under unfinished upwind cells, which contains
+// the whole component whatever the frontier holds.
+__device__ __forceinline__ bool resolve_active(const BuildCtx &c, int64_t m, int nxt, bool eager, bool *stalled) {
     if (c.nproc[m] >= c.N) return false;  // direction finished
     *stalled = c.nfront[nxt * c.M + m] == 0;
-    return *stalled || (c.cyc[m] != 0 && c.ncand[c.cidx[m] * c.M + m] != 0);
+    return *stalled || (eager && c.cyc[m] != 0 && c.ncand[c.cidx[m] * c.M + m] != 0);
 }
 
 // Walks (grid (blocks, direction)): every thread walks candidates with
 // claim_walk and records the cells at which it closed a pointer cycle.
-__global__ void k_walk(BuildCtx c, int nxt, int walk_max) {
+template <int F>
+__global__ void k_walk(BuildCtx c, int nxt, int eager, int walk_max) {
     const int64_t m = blockIdx.y;
     bool stalled;
-    if (!resolve_active(c, m, nxt, &stalled)) return;
+    if (!resolve_active(c, m, nxt, eager != 0, &stalled)) return;
     const int64_t base = m * c.N;
     const StateIx g = state_ix(c, m);
     const int ci = c.cidx[m];
@@ -507,9 +488,8 @@ __global__ void k_walk(BuildCtx c, int nxt, int walk_max) {
     const int32_t *cl = c.cand + (int64_t)ci * c.M * c.N + base;
     const int32_t ep = c.epoch[m];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-        const int32_t v = cl[i];
-        if (c.lvl[g(v)] >= 0 || c.cnt[g(v)] <= 0) continue;
-        const int32_t x = claim_walk(c, g, v, (uint32_t)i + 1u, ep, walk_max);
+        // a finished or ready candidate (count zero) ends its walk at once
+        const int32_t x = claim_walk<F>(c, g, cl[i], (uint32_t)i + 1u, ep, walk_max);
         if (x >= 0) {
             const int32_t k = atomicAdd(&c.nseeds[m], 1);
             if (k < kSeedCap) c.seeds[m * kSeedCap + k] = x;
@@ -524,10 +504,10 @@ __global__ void k_walk(BuildCtx c, int nxt, int walk_max) {
 // through its smallest cell).  Then the direction's candidate lists are
 // rotated.  Dynamic shared memory: per warp X[B] (int32), Sidx[B] (int32),
 // inS[B] (uint8).
-__global__ void k_resolve(BuildCtx c, int nxt, int B, int Beager) {
+__global__ void k_resolve(BuildCtx c, int nxt, int eager, int B, int Beager) {
     const int64_t m = blockIdx.x;
     bool stalled;
-    if (!resolve_active(c, m, nxt, &stalled)) return;
+    if (!resolve_active(c, m, nxt, eager != 0, &stalled)) return;
     extern __shared__ int32_t sh[];
     __shared__ int32_t new_lags;
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
@@ -1309,16 +1289,20 @@ int build_dags(Dags *d, cudaStream_t s) {
     const int64_t max_steps = 4 * N + 1024;
     int32_t status[8] = {0, 0, 1, 0, 0, 0, 0, 0};
     int64_t step = 0;
-    const int check_every = 8;
+    const int check_every = 16;
     int32_t last_remaining = -1;
     int no_progress_checks = 0;
     // peel: a grid of resident blocks over the step's frontier cells of every
     // direction (per-direction offsets in dynamic shared memory)
+    // (kernels compiled for the mesh's face slots rounded up to 4, 6 or 7)
+    const int fs = mesh->FS;
+    void (*peel_k)(BuildCtx, int) = fs <= 4 ? k_peel<4> : fs <= 6 ? k_peel<6> : k_peel<7>;
+    void (*walk_k)(BuildCtx, int, int, int) = fs <= 4 ? k_walk<4> : fs <= 6 ? k_walk<6> : k_walk<7>;
     const size_t off_shm = (size_t)(M + 1) * 8;
     if (off_shm > 48 * 1024)
-        JS_CUDA(cudaFuncSetAttribute(k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)off_shm));
+        JS_CUDA(cudaFuncSetAttribute(peel_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)off_shm));
     int peel_per_sm = 0;
-    JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&peel_per_sm, k_peel, 256, off_shm));
+    JS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&peel_per_sm, peel_k, 256, off_shm));
     const int peel_blocks = device_sm_count() * std::max(1, peel_per_sm);
     // walks of a direction run in parallel over its candidates; a direction has
     // up to tens of thousands of them in a step on large meshes
@@ -1336,21 +1320,25 @@ int build_dags(Dags *d, cudaStream_t s) {
         pev.push_back(e);
         (void)k;
     };
-    // Cycles are searched for every kSearchEvery steps (the candidates of the
-    // steps in between accumulate): the lags found do not depend on when a
-    // component is found, only how long the cells behind it wait.
-    constexpr int kSearchEvery = 4;
-    static_assert(check_every % kSearchEvery == 0 && check_every % 2 == 0, "a check period repeats the steps");
+    // Cycles are searched for every kSearchEvery steps in the directions that
+    // have stalled, and every kEagerEvery steps in every cyclic direction with
+    // candidates (the candidates of the steps in between accumulate): the lags
+    // found do not depend on when a component is found, only how long the cells
+    // behind it wait.
+    constexpr int kSearchEvery = 16, kEagerEvery = 16;
+    static_assert(check_every % kEagerEvery == 0 && kEagerEvery % kSearchEvery == 0 && check_every % 2 == 0,
+                  "a check period repeats the steps");
     const int Beager = d->eager_cap > 0 ? d->eager_cap : B;
     auto launch_step = [&](cudaStream_t st, int64_t stp, bool marks) {
         const int cur = (int)(stp & 1);
         const bool search = stp % kSearchEvery == kSearchEvery - 1;
+        const int eager = stp % kEagerEvery == kEagerEvery - 1 ? 1 : 0;
         if (marks) prof_mark(0);
-        k_peel<<<peel_blocks, 256, off_shm, st>>>(c, cur);
+        peel_k<<<peel_blocks, 256, off_shm, st>>>(c, cur);
         if (marks) prof_mark(1);
-        if (search) k_walk<<<dim3(walk_blocks, (unsigned)M), 256, 0, st>>>(c, cur ^ 1, walk_max);
+        if (search) walk_k<<<dim3(walk_blocks, (unsigned)M), 256, 0, st>>>(c, cur ^ 1, eager, walk_max);
         if (marks) prof_mark(2);
-        if (search) k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, st>>>(c, cur ^ 1, B, Beager);
+        if (search) k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, st>>>(c, cur ^ 1, eager, B, Beager);
         if (marks) prof_mark(3);
         k_commit<<<64, 256, 0, st>>>(c, cur ^ 1, cur);
         if (marks) prof_mark(4);
