@@ -57,6 +57,14 @@ __device__ __forceinline__ double dot_rn(const double *n, const double *o) {
     return __dadd_rn(__dadd_rn(a, b), c);
 }
 
+// Sign of dot_rn(n, o).  Out of line: called only where the FP32 evaluation
+// cannot decide the sign, so the (slow) FP64 arithmetic is not issued for
+// every face and direction.
+__device__ __noinline__ int sign_dot_rn(const double *n, const double *o) {
+    const double d = dot_rn(n, o);
+    return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -85,6 +93,7 @@ struct BuildCtx {
     int64_t lag_cap;
     int32_t *status;  // [0] error code, [1] error info, [2] remaining (clamped), [3] step counter,
                       // [4] stall rounds, [5] cycles found by walks, [6] components lagged
+    int32_t *ticket;  // blocks of the running peel that have read its frontier counts
     unsigned long long *wclaim;  // [M][N]: (epoch << 32) | (walker + 1) of the walk that owns the cell
     // acyclicity certificate: a direction in which the level of its octant's
     // diagonal (lam) increases along every edge has no cycle, so it needs no
@@ -95,6 +104,8 @@ struct BuildCtx {
     const int32_t *oct;  // [M]
     int32_t *cyc;        // [M]
     const int32_t *dslot;  // [M]: the direction's state slot (see the data layout above)
+    const int32_t *sdir;   // [S]: direction of a slot, or -1 (padding)
+    int64_t S;             // state slots (a multiple of 8)
 };
 
 // Index of direction m's state of cell v: [slot / 8][N][8].
@@ -164,9 +175,8 @@ __device__ __forceinline__ void load_nbr(const BuildCtx &c, int32_t v, int32_t (
 }
 
 // Face classification, cell by cell (one thread per cell v, a loop over the
-// directions; block b starts at direction b mod M so that the blocks' list
-// counters are spread over the directions).  The cell's faces, neighbours and
-// normals are read once for all directions.
+// directions in their state-slot groups of 8).  The cell's faces, neighbours
+// and normals are read once for all directions.
 // Sign of the FP64 expression ((n_x O_x) + (n_y O_y)) + (n_z O_z): the FP32
 // evaluation of the same expression on the rounded inputs differs from the
 // exact dot product by at most about 6 * 2^-24 * sum |n_i O_i| <= 4e-7 for unit
@@ -213,59 +223,88 @@ __global__ void __launch_bounds__(kClassifyThreads) k_classify(BuildCtx c, const
         }
     }
     __syncthreads();
-    const int64_t m0 = blockIdx.x % c.M;
-    for (int64_t i = 0; i < c.M; ++i) {
-        const int64_t m = m0 + i < c.M ? m0 + i : m0 + i - c.M;
-        const float ox = __ldg(dirs32 + 3 * m), oy = __ldg(dirs32 + 3 * m + 1), oz = __ldg(dirs32 + 3 * m + 2);
-        unsigned in = 0, out = 0;
-        int count = 0;
-        bool bin = false;
+    // slot groups of 8 directions (block b starts at group b mod G, so that the
+    // blocks' list counters are spread over the directions); the cell's masks
+    // and counts of a group are stored as two full 32-byte sectors each
+    const int64_t G = c.S / 8;
+    const int64_t g0 = blockIdx.x % G;
+    for (int64_t gi = 0; gi < G; ++gi) {
+        const int64_t grp = g0 + gi < G ? g0 + gi : g0 + gi - G;
+        uint32_t wm[8], wc[8];
 #pragma unroll
-        for (int k = 0; k < kMaxFaces; ++k) {
-            if (sf[k] < 0) continue;
-            float d32 = __fadd_rn(__fadd_rn(__fmul_rn(nx[k], ox), __fmul_rn(ny[k], oy)), __fmul_rn(nz[k], oz));
-            int sg;  // sign of the FP64 expression, outward from the face's cell0
-            if (fabsf(d32) > 1e-6f) {
-                sg = d32 > 0.f ? 1 : -1;
-            } else {
-                const double d = dot_rn(c.normal + 3 * (int64_t)(sf[k] >> 1), c.dirs + 3 * m);
-                sg = d > 0.0 ? 1 : (d < 0.0 ? -1 : 0);
+        for (int j = 0; j < 8; ++j) {
+            wm[j] = 0;
+            wc[j] = 0;
+            const int64_t m = c.sdir[grp * 8 + j];
+            if (m < 0) continue;  // padding slot (uniform over the block)
+            const float ox = __ldg(dirs32 + 3 * m), oy = __ldg(dirs32 + 3 * m + 1), oz = __ldg(dirs32 + 3 * m + 2);
+            // signs of the FP64 expression, outward from each face's cell0: the
+            // FP32 evaluation decides unless |d32| <= 1e-6 (bits of unc)
+            int sgk[kMaxFaces];
+            unsigned unc = 0;
+#pragma unroll
+            for (int k = 0; k < kMaxFaces; ++k) {
+                const float d32 =
+                    __fadd_rn(__fadd_rn(__fmul_rn(nx[k], ox), __fmul_rn(ny[k], oy)), __fmul_rn(nz[k], oz));
+                sgk[k] = d32 > 0.f ? 1 : -1;
+                if (sf[k] >= 0 && !(fabsf(d32) > 1e-6f)) unc |= 1u << k;
             }
-            if (sf[k] & 1) sg = -sg;  // outward from v
-            if (sg < 0) {
-                in |= 1u << k;
-                if (nb[k] >= 0) ++count;
-                else bin = true;
-            } else if (sg > 0 && nb[k] >= 0) {
-                out |= 1u << k;
+            if (unc) {
+#pragma unroll
+                for (int k = 0; k < kMaxFaces; ++k)
+                    if ((unc >> k) & 1u) sgk[k] = sign_dot_rn(c.normal + 3 * (int64_t)(sf[k] >> 1), c.dirs + 3 * m);
+            }
+            unsigned in = 0, out = 0;
+            int count = 0;
+            bool bin = false;
+#pragma unroll
+            for (int k = 0; k < kMaxFaces; ++k) {
+                if (sf[k] < 0) continue;
+                int sg = sgk[k];
+                if (sf[k] & 1) sg = -sg;  // outward from v
+                if (sg < 0) {
+                    in |= 1u << k;
+                    if (nb[k] >= 0) ++count;
+                    else bin = true;
+                } else if (sg > 0 && nb[k] >= 0) {
+                    out |= 1u << k;
+                }
+            }
+            wm[j] = in | (out << 8);  // uchar4 (in, out, 0, 0)
+            wc[j] = (uint32_t)count;
+            if (live) {
+                if (count != 0 && bin) c.stamp[state_ix(c, m)(v)] = 1;  // epoch 1 is the first stall's candidate list
+                const unsigned interior_in = in & (unsigned)(back >> (8 * (c.lam ? c.oct[m] : 0))) & 0xffu;
+                if (interior_in) sh_cyc[m] = 1;  // an active edge against the diagonal's levels
+            }
+            // slots for the frontier (sources) and candidate lists: one atomic
+            // per warp and list, only in the few warps that push
+            const bool pf = live && count == 0, pc = live && count != 0 && bin;
+            const unsigned bf = __ballot_sync(0xffffffffu, pf), bc = __ballot_sync(0xffffffffu, pc);
+            if (bf | bc) {
+                int gf = 0, gc = 0;
+                if (lane == 0) {
+                    if (bf) gf = atomicAdd(c.nfront + m, __popc(bf));
+                    if (bc) gc = atomicAdd(c.ncand + m, __popc(bc));
+                }
+                gf = __shfl_sync(0xffffffffu, gf, 0);
+                gc = __shfl_sync(0xffffffffu, gc, 0);
+                if (pf || pc) {
+                    const int off = pf ? gf + __popc(bf & lanemask_lt()) : gc + __popc(bc & lanemask_lt());
+                    int32_t *list = (pf ? c.front : c.cand) + m * c.N;
+                    if (off < c.N) list[off] = v;
+                    else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
+                }
             }
         }
-        const int64_t idx = state_ix(c, m)(v);
         if (live) {
-            c.msk[idx] = make_uchar4((uint8_t)in, (uint8_t)out, 0, 0);
-            c.cnt[idx] = count;
-            if (count != 0 && bin) c.stamp[idx] = 1;  // epoch 1 is the first stall's candidate list
-            const unsigned interior_in = in & (unsigned)(back >> (8 * (c.lam ? c.oct[m] : 0))) & 0xffu;
-            if (interior_in) sh_cyc[m] = 1;  // an active edge against the diagonal's levels
-        }
-        // slots for the frontier (sources) and candidate lists: one atomic per
-        // warp and list, only in the few warps that push
-        const bool pf = live && count == 0, pc = live && count != 0 && bin;
-        const unsigned bf = __ballot_sync(0xffffffffu, pf), bc = __ballot_sync(0xffffffffu, pc);
-        if (bf | bc) {
-            int gf = 0, gc = 0;
-            if (lane == 0) {
-                if (bf) gf = atomicAdd(c.nfront + m, __popc(bf));
-                if (bc) gc = atomicAdd(c.ncand + m, __popc(bc));
-            }
-            gf = __shfl_sync(0xffffffffu, gf, 0);
-            gc = __shfl_sync(0xffffffffu, gc, 0);
-            if (pf || pc) {
-                const int off = pf ? gf + __popc(bf & lanemask_lt()) : gc + __popc(bc & lanemask_lt());
-                int32_t *list = (pf ? c.front : c.cand) + m * c.N;
-                if (off < c.N) list[off] = v;
-                else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
-            }
+            const int64_t w0 = (grp * c.N + v) * 8;
+            uint4 *pm = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(c.msk) + w0);
+            uint4 *pc4 = reinterpret_cast<uint4 *>(c.cnt + w0);
+            pm[0] = make_uint4(wm[0], wm[1], wm[2], wm[3]);
+            pm[1] = make_uint4(wm[4], wm[5], wm[6], wm[7]);
+            pc4[0] = make_uint4(wc[0], wc[1], wc[2], wc[3]);
+            pc4[1] = make_uint4(wc[4], wc[5], wc[6], wc[7]);
         }
     }
     __syncthreads();
@@ -323,7 +362,9 @@ __device__ __forceinline__ int64_t offset_owner(const int64_t *off, int64_t M, i
 // One frontier step for every direction: the frontier cells of all
 // directions, concatenated in direction order, are spread over the grid
 // (dynamic shared memory: M + 1 offsets).  Block 0 also counts the step's
-// cells into nproc (every frontier cell is processed exactly once).
+// cells into nproc (every frontier cell is processed exactly once), and the
+// last block to have read the frontier counts clears them (the list they
+// count is consumed) and stores the number of cells still to be processed.
 template <int F>
 __global__ void __launch_bounds__(256, 5) k_peel(BuildCtx c, int cur) {
     extern __shared__ int64_t peel_off[];
@@ -332,10 +373,39 @@ __global__ void __launch_bounds__(256, 5) k_peel(BuildCtx c, int cur) {
     const int64_t N = c.N;
     block_offsets(c.M, [&](int64_t m) { return (int64_t)min(nf[m], (int32_t)N); }, peel_off);
     if (blockIdx.x == 0) {
-        if (threadIdx.x == 0) *c.npend = 0;  // read by the last commit
+        if (threadIdx.x == 0) *c.npend = 0;  // read by the last lag commit
         for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) c.nproc[m] += min(nf[m], (int32_t)N);
+        __threadfence();  // the counts before block 0's ticket
     }
     const int64_t total = peel_off[c.M];
+    {
+        __shared__ int last;
+        __shared__ long long rem_w[8];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(c.ticket, 1) == (int)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            long long rem = 0;
+            for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) {
+                rem += N - __ldcg(c.nproc + m);
+                c.nfront[cur * c.M + m] = 0;
+            }
+            for (int o = 16; o > 0; o >>= 1) rem += __shfl_down_sync(0xffffffffu, rem, o);
+            if ((threadIdx.x & 31) == 0) rem_w[threadIdx.x >> 5] = rem;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                long long t = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += rem_w[w];
+                c.status[2] = (int32_t)min(t, (long long)INT_MAX);
+                c.status[3] += 1;
+                *c.ticket = 0;
+            }
+        }
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = offset_owner(peel_off, c.M, i);
         const int64_t base = m * N;
@@ -683,26 +753,9 @@ __device__ __forceinline__ int slot_of(const BuildCtx &c, int32_t cell, int32_t 
     return -1;
 }
 
-// Applies this step's lags; block 0 also clears the consumed frontier and
-// counts the cells still to be processed (the pending list is cleared by the
-// next step's peel, after every block here has read its length).
-__global__ void k_commit(BuildCtx c, int nxt, int cur) {
-    if (blockIdx.x == 0) {
-        __shared__ unsigned long long rem;
-        if (threadIdx.x == 0) rem = 0;
-        __syncthreads();
-        unsigned long long mine = 0;
-        for (int64_t m = threadIdx.x; m < c.M; m += blockDim.x) {
-            c.nfront[cur * c.M + m] = 0;
-            mine += (unsigned long long)(c.N - c.nproc[m]);
-        }
-        atomicAdd(&rem, mine);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            c.status[2] = (int32_t)min(rem, (unsigned long long)INT_MAX);
-            c.status[3] += 1;
-        }
-    }
+// Applies the lags of a cycle search (the pending list is cleared by the next
+// step's peel, after every block here has read its length).
+__global__ void k_commit(BuildCtx c, int nxt) {
     const int32_t n = min(*c.npend, (int32_t)c.pend_cap);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int4 e = c.pend[i];
@@ -1216,6 +1269,8 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.wclaim = wclaim.as<unsigned long long>();
     c.msk = msk_g.as<uchar4>();
     c.dslot = dslot_d.as<int32_t>();
+    c.sdir = sdir_d.as<int32_t>();
+    c.S = S;
     c.front = front.as<int32_t>();
     c.cand = cand.as<int32_t>();
     int32_t *sm = small.as<int32_t>();
@@ -1227,6 +1282,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.npend = sm + 7 * M;
     c.nlag = sm + 7 * M + 1;
     c.status = sm + 7 * M + 4;
+    c.ticket = sm + 7 * M + 12;
     c.pend = pend.as<int4>();
     c.pend_cap = pend_cap;
     c.lagall = lagall.as<int4>();
@@ -1340,9 +1396,9 @@ int build_dags(Dags *d, cudaStream_t s) {
         if (marks) prof_mark(2);
         if (search) k_resolve<<<(unsigned)M, kResolveWarps * 32, shmem, st>>>(c, cur ^ 1, eager, B, Beager);
         if (marks) prof_mark(3);
-        k_commit<<<64, 256, 0, st>>>(c, cur ^ 1, cur);
+        if (search) k_commit<<<64, 256, 0, st>>>(c, cur ^ 1);
         if (marks) prof_mark(4);
-        return search ? 4 : 2;
+        return search ? 4 : 1;
     };
     // One check period (check_every steps) is captured once into a CUDA graph and
     // replayed: the steps of a period are the same launches every time (the
