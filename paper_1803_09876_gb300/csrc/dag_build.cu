@@ -497,10 +497,13 @@ template <int F>
 __device__ int32_t claim_walk(const BuildCtx &c, StateIx g, int32_t v, uint32_t me, int32_t ep,
                               int walk_max) {
     const unsigned long long tag = ((unsigned long long)(uint32_t)ep << 32) | me;
+    // most candidates are ready by the time of the search: their count alone
+    // ends the walk
+    if (c.cnt[g(v)] <= 0) return -1;
     int32_t x = v;
     for (int step = 0; step < walk_max; ++step) {
         unsigned long long *slot = c.wclaim + g(x);
-        const int32_t cx = c.cnt[g(x)];
+        const int32_t cx = step == 0 ? 1 : c.cnt[g(x)];
         unsigned long long old = *((volatile unsigned long long *)slot);
         const uchar4 mx = c.msk[g(x)];
         int32_t nb[F];
@@ -574,7 +577,7 @@ __global__ void k_walk(BuildCtx c, int nxt, int eager, int walk_max) {
 // through its smallest cell).  Then the direction's candidate lists are
 // rotated.  Dynamic shared memory: per warp X[B] (int32), Sidx[B] (int32),
 // inS[B] (uint8).
-__global__ void k_resolve(BuildCtx c, int nxt, int eager, int B, int Beager) {
+__global__ void __launch_bounds__(kResolveWarps * 32, 2) k_resolve(BuildCtx c, int nxt, int eager, int B, int Beager) {
     const int64_t m = blockIdx.x;
     bool stalled;
     if (!resolve_active(c, m, nxt, eager != 0, &stalled)) return;
@@ -608,35 +611,50 @@ __global__ void k_resolve(BuildCtx c, int nxt, int eager, int B, int Beager) {
     const int Bcap = stalled ? B : min(B, Beager);
     for (int si = warp; si < ns_total; si += kResolveWarps) {
         const int32_t seed = seeds[si];
-        // ---- backward closure of the seed over unfinished cells, capped at B
+        // ---- backward closure of the seed over unfinished cells, capped at B.
+        // Breadth first: the lanes take up to 32 cells of the current front at
+        // once (their loads in flight together); new cells are appended one by
+        // one (shared memory only).  Whether the closure fits under the cap
+        // does not depend on the order cells are found in.
         if (lane == 0) X[0] = seed;
         __syncwarp();
         int size = 1, head = 0;
         bool closed = true;
         while (head < size && closed) {
-            int32_t x = X[head++];
-            int32_t u = -1;
-            if (lane < c.FS) {
+            const int nfr = min(size - head, kWarp);
+            int32_t up[kMaxFaces];
+            unsigned upm = 0;
+            if (lane < nfr) {
+                const int32_t x = X[head + lane];
                 const uchar4 mx = c.msk[g(x)];
-                unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
-                if ((act >> lane) & 1u) {
-                    int32_t nb = c.nbr[(int64_t)x * c.FS + lane];
-                    if (nb >= 0 && c.lvl[g(nb)] < 0) u = nb;
-                }
+                const unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
+                int lv[kMaxFaces];
+#pragma unroll
+                for (int k = 0; k < kMaxFaces; ++k)
+                    up[k] = (k < c.FS && ((act >> k) & 1u)) ? c.nbr[(int64_t)x * c.FS + k] : -1;
+#pragma unroll
+                for (int k = 0; k < kMaxFaces; ++k) lv[k] = up[k] >= 0 ? c.lvl[g(up[k])] : 0;
+#pragma unroll
+                for (int k = 0; k < kMaxFaces; ++k)
+                    if (up[k] >= 0 && lv[k] < 0) upm |= 1u << k;
             }
-            unsigned todo = __ballot_sync(0xffffffffu, u >= 0);
-            while (todo) {
-                int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                int32_t uu = __shfl_sync(0xffffffffu, u, src);
-                if (warp_find(X, size, uu, lane) < 0) {
-                    if (size == Bcap) {
-                        closed = false;
-                        break;
+            head += nfr;
+#pragma unroll
+            for (int k = 0; k < kMaxFaces; ++k) {
+                unsigned todo = __ballot_sync(0xffffffffu, (upm >> k) & 1u);
+                while (todo && closed) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int32_t uu = __shfl_sync(0xffffffffu, up[k], src);
+                    if (warp_find(X, size, uu, lane) < 0) {
+                        if (size == Bcap) {
+                            closed = false;
+                        } else {
+                            if (lane == 0) X[size] = uu;
+                            __syncwarp();
+                            ++size;
+                        }
                     }
-                    if (lane == 0) X[size] = uu;
-                    __syncwarp();
-                    ++size;
                 }
             }
         }
@@ -644,7 +662,7 @@ __global__ void k_resolve(BuildCtx c, int nxt, int eager, int B, int Beager) {
 
         // ---- strongly connected component of the seed inside the closure:
         // every cell of X reaches the seed, so the cells reached from the seed
-        // within X form its component.
+        // within X form its component (breadth first, lanes over the front).
         for (int j = lane; j < size; j += kWarp) inS[j] = 0;
         __syncwarp();
         if (lane == 0) {
@@ -654,52 +672,81 @@ __global__ void k_resolve(BuildCtx c, int nxt, int eager, int B, int Beager) {
         __syncwarp();
         int ns = 1, h = 0;
         while (h < ns) {
-            int32_t y = X[Sidx[h++]];
-            int32_t w = -1;
-            if (lane < c.FS && ((c.msk[g(y)].y >> lane) & 1u)) w = c.nbr[(int64_t)y * c.FS + lane];
-            unsigned todo = __ballot_sync(0xffffffffu, w >= 0);
-            while (todo) {
-                int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                int32_t ww = __shfl_sync(0xffffffffu, w, src);
-                int j = warp_find(X, size, ww, lane);
-                if (j >= 0 && !inS[j]) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        inS[j] = 1;
-                        Sidx[ns] = j;
+            const int nfr = min(ns - h, kWarp);
+            int32_t dn[kMaxFaces];
+            unsigned dnm = 0;
+            if (lane < nfr) {
+                const int32_t y = X[Sidx[h + lane]];
+                const unsigned ob = c.msk[g(y)].y;
+#pragma unroll
+                for (int k = 0; k < kMaxFaces; ++k) {
+                    dn[k] = (k < c.FS && ((ob >> k) & 1u)) ? c.nbr[(int64_t)y * c.FS + k] : -1;
+                    if (dn[k] >= 0) dnm |= 1u << k;
+                }
+            }
+            __syncwarp();
+            h += nfr;
+#pragma unroll
+            for (int k = 0; k < kMaxFaces; ++k) {
+                unsigned todo = __ballot_sync(0xffffffffu, (dnm >> k) & 1u);
+                while (todo) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int32_t ww = __shfl_sync(0xffffffffu, dn[k], src);
+                    const int j = warp_find(X, size, ww, lane);
+                    if (j >= 0 && !inS[j]) {
+                        __syncwarp();
+                        if (lane == 0) {
+                            inS[j] = 1;
+                            Sidx[ns] = j;
+                        }
+                        __syncwarp();
+                        ++ns;
                     }
-                    __syncwarp();
-                    ++ns;
                 }
             }
         }
         if (ns < 2) continue;
 
-        // ---- smallest active face inside the component, and its smallest cell
+        // ---- smallest active face inside the component (each face is the
+        // outgoing face of exactly one of its cells, so the minimum is unique),
+        // and the component's smallest cell; lanes load 32 cells at once
         int32_t best_f = INT_MAX, best_u = -1, best_v = -1, smin = INT_MAX;
-        for (int t = 0; t < ns; ++t) {
-            int32_t y = X[Sidx[t]];
-            smin = min(smin, y);
-            int32_t w = -1, f = INT_MAX;
-            if (lane < c.FS && ((c.msk[g(y)].y >> lane) & 1u)) {
-                w = c.nbr[(int64_t)y * c.FS + lane];
-                f = c.sface[(int64_t)y * c.FS + lane] >> 1;
+        for (int t0 = 0; t0 < ns; t0 += kWarp) {
+            int32_t dn[kMaxFaces], fk[kMaxFaces];
+            unsigned dnm = 0;
+            int32_t y = -1;
+            if (t0 + lane < ns) {
+                y = X[Sidx[t0 + lane]];
+                smin = min(smin, y);
+                const unsigned ob = c.msk[g(y)].y;
+#pragma unroll
+                for (int k = 0; k < kMaxFaces; ++k) {
+                    const bool o = k < c.FS && ((ob >> k) & 1u);
+                    dn[k] = o ? c.nbr[(int64_t)y * c.FS + k] : -1;
+                    fk[k] = o ? (c.sface[(int64_t)y * c.FS + k] >> 1) : INT_MAX;
+                    if (dn[k] >= 0) dnm |= 1u << k;
+                }
             }
-            unsigned todo = __ballot_sync(0xffffffffu, w >= 0);
-            while (todo) {
-                int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                int32_t ww = __shfl_sync(0xffffffffu, w, src);
-                int32_t ff = __shfl_sync(0xffffffffu, f, src);
-                int j = warp_find(X, size, ww, lane);
-                if (j >= 0 && inS[j] && ff < best_f) {
-                    best_f = ff;
-                    best_u = y;
-                    best_v = ww;
+#pragma unroll
+            for (int k = 0; k < kMaxFaces; ++k) {
+                unsigned todo = __ballot_sync(0xffffffffu, (dnm >> k) & 1u);
+                while (todo) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    const int32_t ww = __shfl_sync(0xffffffffu, dn[k], src);
+                    const int32_t ff = __shfl_sync(0xffffffffu, fk[k], src);
+                    const int32_t yy = __shfl_sync(0xffffffffu, y, src);
+                    const int j = warp_find(X, size, ww, lane);
+                    if (j >= 0 && inS[j] && ff < best_f) {
+                        best_f = ff;
+                        best_u = yy;
+                        best_v = ww;
+                    }
                 }
             }
         }
+        for (int o = 16; o > 0; o >>= 1) smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
         // ---- one warp per component records the lag (claimed by its smallest cell)
         if (lane == 0 && best_f != INT_MAX) {
             if (atomicExch(&c.claim[g(smin)], ep) != ep) {
