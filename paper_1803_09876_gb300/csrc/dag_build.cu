@@ -1000,18 +1000,23 @@ __global__ void k_scan_apply(const int64_t *in, int64_t n, const int64_t *offs, 
 
 // ---- stable LSD radix sort of equal-length segments (8-bit digits) -----------------
 constexpr int kRsTile = 1024;  // elements per tile; one warp per tile
-
-__global__ void k_rs_hist(const uint32_t *keys, int64_t seg_len, int shift, int32_t *hist, int64_t tiles) {
-    __shared__ int32_t h[256];
-    const int64_t s = blockIdx.y, t = blockIdx.x;
-    for (int b = threadIdx.x; b < 256; b += 32) h[b] = 0;
+constexpr int kRsWarps = 4;    // tiles (warps) per block
+__global__ void __launch_bounds__(kRsWarps * 32)
+    k_rs_hist(const uint32_t *keys, int64_t seg_len, int shift, int32_t *hist, int64_t tiles) {
+    __shared__ int32_t hs[kRsWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t s = blockIdx.y, t = (int64_t)blockIdx.x * kRsWarps + w;
+    int32_t *h = hs[w];
+    for (int b = lane; b < 256; b += 32) h[b] = 0;
     __syncwarp();
-    for (int i = 0; i < kRsTile / 32; ++i) {
-        int64_t e = t * kRsTile + i * 32 + threadIdx.x;
-        if (e < seg_len) atomicAdd(&h[(keys[s * seg_len + e] >> shift) & 255u], 1);
+    if (t < tiles) {
+        for (int i = 0; i < kRsTile / 32; ++i) {
+            int64_t e = t * kRsTile + i * 32 + lane;
+            if (e < seg_len) atomicAdd(&h[(keys[s * seg_len + e] >> shift) & 255u], 1);
+        }
+        __syncwarp();
+        for (int b = lane; b < 256; b += 32) hist[(s * 256 + b) * tiles + t] = h[b];
     }
-    __syncwarp();
-    for (int b = threadIdx.x; b < 256; b += 32) hist[(s * 256 + b) * tiles + t] = h[b];
 }
 
 // In-place exclusive scan of each segment's [256][tiles] histogram (one block per segment).
@@ -1032,12 +1037,14 @@ __global__ void k_rs_scan(int32_t *hist, int64_t len) {
     }
 }
 
-__global__ void k_rs_scatter(const uint32_t *keys, const int32_t *vals, int64_t seg_len, int shift,
-                             const int32_t *hist, int64_t tiles, uint32_t *keys_out,
-                             int32_t *vals_out) {
-    __shared__ int32_t run[256];
-    const int64_t s = blockIdx.y, t = blockIdx.x;
-    const int lane = threadIdx.x;
+__global__ void __launch_bounds__(kRsWarps * 32)
+    k_rs_scatter(const uint32_t *keys, const int32_t *vals, int64_t seg_len, int shift, const int32_t *hist,
+                 int64_t tiles, uint32_t *keys_out, int32_t *vals_out) {
+    __shared__ int32_t runs[kRsWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t s = blockIdx.y, t = (int64_t)blockIdx.x * kRsWarps + w;
+    if (t >= tiles) return;
+    int32_t *run = runs[w];
     for (int b = lane; b < 256; b += 32) run[b] = hist[(s * 256 + b) * tiles + t];
     __syncwarp();
     for (int i = 0; i < kRsTile / 32; ++i) {
@@ -1053,7 +1060,7 @@ __global__ void k_rs_scatter(const uint32_t *keys, const int32_t *vals, int64_t 
         if (valid && rank == 0) run[d] += __popc(peers);
         __syncwarp();
         if (valid) {
-            keys_out[s * seg_len + pos] = key;
+            if (keys_out) keys_out[s * seg_len + pos] = key;
             vals_out[s * seg_len + pos] = val;
         }
     }
@@ -1090,27 +1097,28 @@ int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len,
     DevBuf hist, kb[2], vb[2];
     JS_TRY(hist.alloc((size_t)n_seg * 256 * tiles * 4, s));
     size_t ne = (size_t)n_seg * seg_len;
-    JS_TRY(kb[0].alloc(ne * 4, s));
-    JS_TRY(kb[1].alloc(ne * 4, s));
-    JS_TRY(vb[0].alloc(ne * 4, s));
-    JS_TRY(vb[1].alloc(ne * 4, s));
+    // passes before the last ping-pong between scratch buffers; the last one
+    // writes the outputs (keys only where asked for)
+    for (int b = 0; b < std::min(passes - 1, 2); ++b) {
+        JS_TRY(kb[b].alloc(ne * 4, s));
+        JS_TRY(vb[b].alloc(ne * 4, s));
+    }
     const uint32_t *kin = keys_in;
     const int32_t *vin = vals_in;
-    dim3 grid((unsigned)tiles, (unsigned)n_seg);
+    dim3 grid((unsigned)((tiles + kRsWarps - 1) / kRsWarps), (unsigned)n_seg);
     for (int p = 0; p < passes; ++p) {
-        uint32_t *ko = kb[p & 1].as<uint32_t>();
-        int32_t *vo = vb[p & 1].as<int32_t>();
-        k_rs_hist<<<grid, 32, 0, s>>>(kin, seg_len, 8 * p, hist.as<int32_t>(), tiles);
+        const bool last = p == passes - 1;
+        uint32_t *ko = last ? keys_out : kb[p & 1].as<uint32_t>();
+        int32_t *vo = last ? vals_out : vb[p & 1].as<int32_t>();
+        k_rs_hist<<<grid, kRsWarps * 32, 0, s>>>(kin, seg_len, 8 * p, hist.as<int32_t>(), tiles);
         JS_LAUNCH_CHECK();
         k_rs_scan<<<(unsigned)n_seg, 1024, 0, s>>>(hist.as<int32_t>(), 256 * tiles);
         JS_LAUNCH_CHECK();
-        k_rs_scatter<<<grid, 32, 0, s>>>(kin, vin, seg_len, 8 * p, hist.as<int32_t>(), tiles, ko, vo);
+        k_rs_scatter<<<grid, kRsWarps * 32, 0, s>>>(kin, vin, seg_len, 8 * p, hist.as<int32_t>(), tiles, ko, vo);
         JS_LAUNCH_CHECK();
         kin = ko;
         vin = vo;
     }
-    JS_CUDA(cudaMemcpyAsync(vals_out, vin, ne * 4, cudaMemcpyDeviceToDevice, s));
-    if (keys_out) JS_CUDA(cudaMemcpyAsync(keys_out, kin, ne * 4, cudaMemcpyDeviceToDevice, s));
     JS_CUDA(cudaStreamSynchronize(s));
     return JSWEEP_OK;
 }
