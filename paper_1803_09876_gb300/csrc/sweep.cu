@@ -47,10 +47,10 @@ namespace {
 // Level-synchronous sweep: one launch per time slot; a warp handles one unit
 // of 32 / SPLIT cells.
 template <class T, int R, int SPLIT, int MAXF>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T> a, int64_t u0, int64_t nu) {
+__global__ void __launch_bounds__(kLevelWarps * 32) k_sweep_level(SweepArgs<T> a, int64_t u0, int64_t nu) {
     pdl_launch_next();
     const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t t = (int64_t)blockIdx.x * kLevelWarps + (threadIdx.x >> 5);
     if (t >= nu) return;
     const int4 u = a.units[u0 + t];
     const int cell = lane / SPLIT, sub = lane % SPLIT;
@@ -65,15 +65,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_sweep_level(SweepArgs<T
 // records hold upwind positions and psi has a sweep-order copy, see
 // solve_cell_coef).
 // The kernel is bound by how many warps have memory requests in flight: it
-// is compiled for 6 resident blocks of 8 warps per SM (40 registers), which
-// measured faster than 5 (48 registers) or 8 (32 registers, with spills).
+// is compiled for 48 resident warps per SM (40 registers), which measured
+// faster than 40 (48 registers) or 64 (32 registers, with spills).
 template <class T, int R, int SPLIT, int MAXF, bool SEQ, bool MG>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 6)
+__global__ void __launch_bounds__(kLevelWarps * 32, 48 / kLevelWarps)
     k_sweep_level_coef(SweepArgs<T> a, int64_t u0, int64_t nu, const unsigned char *coef) {
     pdl_launch_next();
     constexpr int RB = coef_record_bytes<T, MAXF>();
     const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t t = (int64_t)blockIdx.x * kLevelWarps + (threadIdx.x >> 5);
     if (t >= nu) return;
     const uint64_t pol_stream = l2_evict_first();
     const int4 u = ldg_hint(a.units + u0 + t, pol_stream);
@@ -1047,10 +1047,10 @@ void capture_levels(Dags *d, const SweepArgs<T> &a, cudaStream_t cs, const unsig
     for (int64_t l = 0; l < std::min(S, Tn); ++l) {
         const int64_t nu = sp[l + 1] - sp[l];
         if (nu <= 0) continue;
-        const int64_t blocks = (nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const int64_t blocks = (nu + kLevelWarps - 1) / kLevelWarps;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)blocks);
-        cfg.blockDim = dim3(kWarpsPerBlock * 32);
+        cfg.blockDim = dim3(kLevelWarps * 32);
         cfg.stream = cs;
         // slots after the first start early (programmatic dependent launch); the
         // first keeps a full dependency on whatever preceded the sweep
