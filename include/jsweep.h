@@ -101,6 +101,13 @@ extern "C" {
  * LEVEL); JSWEEP_ERR_UNIMPLEMENTED if the directions outnumber the resident
  * warps. */
 #define JSWEEP_PRIO_PATCH 3
+/* Patch tasks with SLBD vertex priority (Sec. V-D, Shortest Local Boundary
+ * Distance): within every (direction, patch) task's layer, the units whose
+ * cells lie closest to the patch's boundary (breadth-first distance in faces
+ * to the nearest cell of another patch) run first, so the warps of the
+ * neighbouring patches that wait on them are released sooner.  Same results
+ * as every other order; persistent schedule only (others treat it as LEVEL). */
+#define JSWEEP_PRIO_PATCH_SLBD 4
 
 typedef struct jsweep_mesh_s *jsweep_mesh_t;
 typedef struct jsweep_quad_s *jsweep_quad_t;

@@ -501,7 +501,7 @@ int check_options(const jsweep_options *opt, jsweep_options *o) {
         return JSWEEP_ERR_INVALID_ARG;
     }
     if (opt->sweep_mode < 0 || opt->sweep_mode > JSWEEP_MODE_PATCH || opt->priority < 0 ||
-        opt->priority > JSWEEP_PRIO_PATCH || opt->cluster_cells > 32 ||
+        opt->priority > JSWEEP_PRIO_PATCH_SLBD || opt->cluster_cells > 32 ||
         opt->cycle_search_max > 1024 || opt->blocks_per_sm > 32) {
         set_error("jsweep_options: value out of range");
         return JSWEEP_ERR_INVALID_ARG;

@@ -483,7 +483,9 @@ int handle_units(const Batch *b, Dags *d, int max_cells, cudaStream_t s) {
     d->opt.cluster_cells = b->opt.cluster_cells;
     d->opt.unit_order = b->opt.unit_order;
     // patch tasks are a single-problem schedule: batches merge slot-ordered tables
-    d->opt.priority = b->opt.priority == JSWEEP_PRIO_PATCH ? JSWEEP_PRIO_LEVEL : b->opt.priority;
+    d->opt.priority = (b->opt.priority == JSWEEP_PRIO_PATCH || b->opt.priority == JSWEEP_PRIO_PATCH_SLBD)
+                          ? JSWEEP_PRIO_LEVEL
+                          : b->opt.priority;
     d->opt.octant_stagger = b->opt.octant_stagger;
     const int rc = ensure_units(d, JSWEEP_MODE_PERSISTENT, max_cells, s);
     d->opt = saved;

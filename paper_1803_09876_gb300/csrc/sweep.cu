@@ -368,6 +368,8 @@ __global__ void k_unit_fill_dir(const int32_t *lp, const int64_t *lp_off, const 
 }
 
 // ---- patch tasks ------------------------------------------------------------------------
+inline bool patch_prio(int p) { return p == JSWEEP_PRIO_PATCH || p == JSWEEP_PRIO_PATCH_SLBD; }
+
 // Triple i = (direction m, patch s, layer l), task-major: i = tri_off[m] + s * L_m + l.
 __device__ __forceinline__ void patch_triple(int64_t i, const int64_t *tri_off, int64_t M, const int32_t *nlev,
                                              int64_t &m, int &s, int &l) {
@@ -441,6 +443,89 @@ __global__ void k_patch_fill(const int32_t *order, const int32_t *lp, const int6
         const int64_t k0 = uoff[i] - uoff[tri_off[m] + (int64_t)s * nlev[m]];
         for (int j = 0; a + j * U < b; ++j)
             units[task + W * (k0 + j)] = make_int4((int)m, a + j * U, min(U, b - a - j * U), 0);
+    }
+}
+
+// ---- SLBD order of patch tasks (Sec. V-D) ----------------------------------------------
+// Patch of cell c: the largest s with floor(s N / nslab) <= c (patches are id ranges).
+__device__ __forceinline__ int patch_of(int64_t c, int64_t N, int nslab) {
+    int s = (int)(c * nslab / N);
+    while (s + 1 < nslab && (int64_t)(s + 1) * N / nslab <= c) ++s;
+    while (s > 0 && (int64_t)s * N / nslab > c) --s;
+    return s;
+}
+
+// Local boundary distance, breadth first: 0 for a cell with a face neighbour
+// in another patch, else 1 + the smallest distance among its neighbours; -1
+// until reached (a patch without another patch beside it keeps -1).
+__global__ void k_bdist_init(const int32_t *nbr, int FS, int64_t N, int nslab, int32_t *dist) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        const int ps = patch_of(c, N, nslab);
+        int32_t d = -1;
+        for (int k = 0; k < FS; ++k) {
+            const int32_t nb = nbr[c * FS + k];
+            if (nb >= 0 && patch_of(nb, N, nslab) != ps) d = 0;
+        }
+        dist[c] = d;
+    }
+}
+
+// One breadth-first round: cells not yet reached that touch a cell at distance
+// r get r + 1 (writes of r + 1 do not disturb the reads of r).
+__global__ void k_bdist_step(const int32_t *nbr, int FS, int64_t N, int32_t r, int32_t *dist, int *changed) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        if (dist[c] >= 0) continue;
+        bool hit = false;
+        for (int k = 0; k < FS; ++k) {
+            const int32_t nb = nbr[c * FS + k];
+            if (nb >= 0 && dist[nb] == r) hit = true;
+        }
+        if (hit) {
+            dist[c] = r + 1;
+            *changed = 1;
+        }
+    }
+}
+
+// Units of every (direction, patch, layer) run in id order, densely (unit j of
+// triple i at uoff[i] + j), each with the sort key (i << 8) | the smallest
+// local boundary distance of its cells (unreached: 255).
+__global__ void k_patch_dense(const int32_t *order, const int32_t *lp, const int64_t *lp_off, const int32_t *nlev,
+                              const int64_t *tri_off, int64_t M, int64_t N, int nslab, int U, int64_t total,
+                              const int64_t *uoff, const int32_t *dist, int4 *du, uint32_t *dkey) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m;
+        int s, l, a, b;
+        patch_triple(i, tri_off, M, nlev, m, s, l);
+        patch_run(order, lp, lp_off, N, nslab, m, s, l, a, b);
+        for (int j = 0; a + j * U < b; ++j) {
+            const int p0 = a + j * U, z = min(U, b - p0);
+            int key = 255;
+            for (int q = 0; q < z; ++q) {
+                const int32_t dv = dist[order[m * N + p0 + q]];
+                if (dv >= 0) key = min(key, min(dv, 254));
+            }
+            du[uoff[i] + j] = make_int4((int)m, p0, z, 0);
+            dkey[uoff[i] + j] = ((uint32_t)i << 8) | (uint32_t)key;
+        }
+    }
+}
+
+// The dense units in key order (a stable sort: within a run, by distance,
+// then id) into the task table: the q-th sorted unit is the (q - uoff[i])-th of
+// its run i.
+__global__ void k_patch_scatter(const int4 *du, const uint32_t *dkey, const int32_t *perm, int64_t n,
+                                const int64_t *uoff, const int64_t *tri_off, const int32_t *nlev, int64_t M,
+                                int nslab, int64_t W, int4 *units) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = perm[q];
+        const int64_t i = dkey[e] >> 8;
+        int64_t m;
+        int s, l;
+        patch_triple(i, tri_off, M, nlev, m, s, l);
+        const int64_t task = m * nslab + s;
+        const int64_t k0 = uoff[i] - uoff[tri_off[m] + (int64_t)s * nlev[m]];
+        units[task + W * (k0 + (q - uoff[i]))] = du[e];
     }
 }
 
@@ -604,9 +689,12 @@ int pad_rhs(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8
 }  // namespace
 
 // ---- unit tables ------------------------------------------------------------------------
-// Patch-task table (JSWEEP_PRIO_PATCH): patches are id ranges; as many as
-// resident warps allow (directions x patches <= resident_warps).
-static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream_t s) {
+// Patch-task table (JSWEEP_PRIO_PATCH, JSWEEP_PRIO_PATCH_SLBD): patches are id
+// ranges; as many as resident warps allow (directions x patches <=
+// resident_warps).  With SLBD the units of every (task, layer) run are
+// ordered by their cells' local boundary distance (Sec. V-D), provided the
+// runs can be numbered in 24 bits (else they keep id order).
+static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream_t s, int prio) {
     const int64_t M = d->M, N = d->N;
     if (resident_warps < M) {
         set_error("patch tasks need at least one resident warp per direction (%lld directions, %lld warps)",
@@ -617,7 +705,7 @@ static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream
     const int64_t tasks = M * nslab;
     const int64_t W = (tasks + kWarpsPerBlock - 1) / kWarpsPerBlock * kWarpsPerBlock;
     UnitTable &ut = d->ut;
-    if (ut.mode == JSWEEP_MODE_PERSISTENT && ut.priority == JSWEEP_PRIO_PATCH && ut.cluster == U && ut.warps == W)
+    if (ut.mode == JSWEEP_MODE_PERSISTENT && ut.priority == prio && ut.cluster == U && ut.warps == W)
         return JSWEEP_OK;
     std::vector<int64_t> tri(M + 1, 0);
     std::vector<int32_t> nl32(M);
@@ -652,17 +740,65 @@ static int ensure_units_patch(Dags *d, int U, int64_t resident_warps, cudaStream
     const int64_t n_units = W * (int64_t)kmax;
     JS_TRY(ut.units.alloc((size_t)std::max<int64_t>(n_units, 1) * 16, s));
     JS_CUDA(cudaMemsetAsync(ut.units.p, 0, (size_t)std::max<int64_t>(n_units, 1) * 16, s));  // empty units pad
-    k_patch_fill<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(d->s_order, d->s_lp, lpoff_d.as<int64_t>(),
-                                                                nlev_d.as<int32_t>(), tri_d.as<int64_t>(), M, N, nslab,
-                                                                U, total, uoff.as<int64_t>(), W, ut.units.as<int4>());
-    JS_LAUNCH_CHECK();
-    JS_CUDA(cudaStreamSynchronize(s));
+    if (prio == JSWEEP_PRIO_PATCH_SLBD && total < (1ll << 24)) {
+        // local boundary distances, then the runs' units sorted by (run, distance)
+        const int FS = d->mesh->FS;
+        const int32_t *nbr = d->mesh->nbr.as<int32_t>();
+        DevBuf dist, flag, du, dkey, perm;
+        JS_TRY(dist.alloc(N * 4, s));
+        JS_TRY(flag.alloc(4, s));
+        k_bdist_init<<<grid_for(N, 256, 152 * 32), 256, 0, s>>>(nbr, FS, N, nslab, dist.as<int32_t>());
+        JS_LAUNCH_CHECK();
+        for (int32_t r = 0; r < (int32_t)std::min<int64_t>(N, INT32_MAX - 1); ++r) {
+            int changed = 0;
+            JS_CUDA(cudaMemsetAsync(flag.p, 0, 4, s));
+            k_bdist_step<<<grid_for(N, 256, 152 * 32), 256, 0, s>>>(nbr, FS, N, r, dist.as<int32_t>(), flag.as<int>());
+            JS_LAUNCH_CHECK();
+            JS_CUDA(cudaMemcpyAsync(&changed, flag.p, 4, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaStreamSynchronize(s));
+            if (!changed) break;
+        }
+        int64_t n_dense = 0;
+        {
+            int64_t last_off = 0, last_cnt = 0;
+            JS_CUDA(cudaMemcpyAsync(&last_off, uoff.as<int64_t>() + total - 1, 8, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaMemcpyAsync(&last_cnt, cnt.as<int64_t>() + total - 1, 8, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaStreamSynchronize(s));
+            n_dense = last_off + last_cnt;
+        }
+        if (n_dense >= (1ll << 31)) {
+            set_error("patch tasks: %lld units exceed the SLBD sort", (long long)n_dense);
+            return JSWEEP_ERR_UNIMPLEMENTED;
+        }
+        JS_TRY(du.alloc((size_t)std::max<int64_t>(n_dense, 1) * 16, s));
+        JS_TRY(dkey.alloc((size_t)std::max<int64_t>(n_dense, 1) * 4, s));
+        JS_TRY(perm.alloc((size_t)std::max<int64_t>(n_dense, 1) * 4, s));
+        k_patch_dense<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(
+            d->s_order, d->s_lp, lpoff_d.as<int64_t>(), nlev_d.as<int32_t>(), tri_d.as<int64_t>(), M, N, nslab, U,
+            total, uoff.as<int64_t>(), dist.as<int32_t>(), du.as<int4>(), dkey.as<uint32_t>());
+        JS_LAUNCH_CHECK();
+        if (n_dense > 0) {
+            JS_TRY(radix_sort_segments(dkey.as<uint32_t>(), 1, n_dense, 32, nullptr, perm.as<int32_t>(), nullptr, s));
+            k_patch_scatter<<<grid_for(n_dense, 256, 152 * 32), 256, 0, s>>>(
+                du.as<int4>(), dkey.as<uint32_t>(), perm.as<int32_t>(), n_dense, uoff.as<int64_t>(),
+                tri_d.as<int64_t>(), nlev_d.as<int32_t>(), M, nslab, W, ut.units.as<int4>());
+            JS_LAUNCH_CHECK();
+        }
+        JS_CUDA(cudaStreamSynchronize(s));
+    } else {
+        k_patch_fill<<<grid_for(total, 256, 152 * 32), 256, 0, s>>>(d->s_order, d->s_lp, lpoff_d.as<int64_t>(),
+                                                                    nlev_d.as<int32_t>(), tri_d.as<int64_t>(), M, N,
+                                                                    nslab, U, total, uoff.as<int64_t>(), W,
+                                                                    ut.units.as<int4>());
+        JS_LAUNCH_CHECK();
+        JS_CUDA(cudaStreamSynchronize(s));
+    }
     ut.n_units = n_units;
     ut.warps = W;
     ut.slot_ptr.assign({0, n_units});
     ut.dirmajor = false;
     ut.mode = JSWEEP_MODE_PERSISTENT;
-    ut.priority = JSWEEP_PRIO_PATCH;
+    ut.priority = prio;
     ut.cluster = U;
     ut.stagger = 0;
     ut.order = d->opt.unit_order;
@@ -733,8 +869,8 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resid
     if (mode == JSWEEP_MODE_PATCH) return JSWEEP_OK;  // patch programs have their own schedule
     const int U = std::max(1, std::min(d->opt.cluster_cells, max_cells));
     int prio = d->opt.priority;
-    if (prio == JSWEEP_PRIO_PATCH && mode != JSWEEP_MODE_PERSISTENT) prio = JSWEEP_PRIO_LEVEL;
-    if (prio == JSWEEP_PRIO_PATCH) return ensure_units_patch(d, U, resident_warps, s);
+    if (patch_prio(prio) && mode != JSWEEP_MODE_PERSISTENT) prio = JSWEEP_PRIO_LEVEL;
+    if (patch_prio(prio)) return ensure_units_patch(d, U, resident_warps, s, prio);
     if (dirmajor) return ensure_units_dir(d, U, s);
     int stagger = d->opt.octant_stagger > 0 ? d->opt.octant_stagger : (int)std::max<int64_t>(1, d->Smax / 4);
     if (prio != JSWEEP_PRIO_OCTANT) stagger = 0;
@@ -864,7 +1000,7 @@ int resolve_mode(const Dags *d) {
 // (k_sweep_queue) unless the face stream or the sweep-order psi is switched
 // off or was refused, or the priority is patch tasks.
 bool use_queues(const Dags *d, int mode) {
-    return mode == JSWEEP_MODE_PERSISTENT && d->opt.priority != JSWEEP_PRIO_PATCH && !d->opt.no_face_stream &&
+    return mode == JSWEEP_MODE_PERSISTENT && !patch_prio(d->opt.priority) && !d->opt.no_face_stream &&
            !d->opt.no_sweep_order_psi && !d->psi_seq_failed;
 }
 
@@ -973,7 +1109,7 @@ int launch_dd(Dags *d, const SweepArgs<T> &a, cudaStream_t s) {
     int64_t grid = (int64_t)device_sm_count() * bps;
     const int64_t maxg = (d->ut.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (grid > maxg) grid = std::max<int64_t>(1, maxg);
-    if (d->ut.priority == JSWEEP_PRIO_PATCH) {
+    if (patch_prio(d->ut.priority)) {
         // one warp per patch task: the table was laid out for exactly this many warps
         if (d->ut.warps > (int64_t)device_sm_count() * bps * kWarpsPerBlock) {
             set_error("patch tasks: %lld warps cannot all be resident", (long long)d->ut.warps);
@@ -1020,7 +1156,7 @@ template <class T, int R> int64_t dd_resident_warps(const Dags *d) {
 }
 
 template <class T, int R> int64_t patch_warps(const Dags *d, int mode) {
-    return (mode == JSWEEP_MODE_PERSISTENT && d->opt.priority == JSWEEP_PRIO_PATCH) ? dd_resident_warps<T, R>(d) : 0;
+    return (mode == JSWEEP_MODE_PERSISTENT && patch_prio(d->opt.priority)) ? dd_resident_warps<T, R>(d) : 0;
 }
 
 // First slot of the tail: the slots from it to the end each hold fewer than

@@ -47,6 +47,7 @@ JSWEEP_PRIO_LEVEL = 0
 JSWEEP_PRIO_DEPTH = 1
 JSWEEP_PRIO_OCTANT = 2
 JSWEEP_PRIO_PATCH = 3
+JSWEEP_PRIO_PATCH_SLBD = 4
 
 # every symbol include/jsweep.h declares
 EXPORTED = [

@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 MODES = [dict(sweep_mode=1), dict(sweep_mode=2), dict(sweep_mode=2, priority=1, cluster_cells=7),
          dict(sweep_mode=2, priority=2, cluster_cells=1), dict(sweep_mode=1, cluster_cells=5),
          dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=3, cluster_cells=3),
+         dict(sweep_mode=2, priority=4), dict(sweep_mode=2, priority=4, cluster_cells=3),
          dict(sweep_mode=3), dict(sweep_mode=3, patch_cells=64), dict(sweep_mode=1, tail_units=64),
          dict(sweep_mode=1, no_sweep_order_psi=1)]
 
@@ -389,7 +390,8 @@ def test_face_stream_and_every_schedule_give_the_same_bits(prec):
                      dict(sweep_mode=1, no_sweep_order_psi=1),
                      dict(sweep_mode=1, tail_units=1 << 30), dict(sweep_mode=1, tail_units=40),
                      dict(sweep_mode=1, tail_units=40, no_sweep_order_psi=1),
-                     dict(sweep_mode=2), dict(sweep_mode=3, patch_cells=64)):
+                     dict(sweep_mode=2), dict(sweep_mode=2, priority=3), dict(sweep_mode=2, priority=4),
+                     dict(sweep_mode=3, patch_cells=64)):
             g = build(mesh, dirs, w, **opts)
             outs.append([J().jsweep_sweep(g, tensor(sig, dt), tensor(s, dt)).cpu() for s in srcs])
         for o in outs[1:]:
