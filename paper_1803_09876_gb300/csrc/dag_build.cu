@@ -40,6 +40,7 @@
 //      LSD radix sort; level_ptr from the sorted keys; the incoming mask is
 //      gathered into level order (bit 7 flags a cell with a lagged face).
 #include <climits>
+#include <cstring>
 #include <memory>
 
 #include "common.cuh"
@@ -1478,12 +1479,72 @@ int build_dags(Dags *d, cudaStream_t s) {
         }
         cudaGetLastError();  // a failed capture falls back to launches step by step
     }
-    while (true) {
-        if (period.exec) {
+    // one status check: false to go on; true when done (rc = 0) or failed (rc)
+    auto check_status = [&](int &rc) -> bool {
+        rc = JSWEEP_OK;
+        if (status[0] != 0) {
+            if (status[0] == JSWEEP_ERR_CYCLE)
+                set_error("dependency cycle in direction %d could not be broken within the search "
+                          "cap of %d cells (raise jsweep_options.cycle_search_max)", status[1], B);
+            else
+                set_error("dag build: internal list capacity exceeded (status %d)", status[0]);
+            rc = status[0];
+            return true;
+        }
+        if (status[2] == 0) return true;
+        // every step either processes cells or lags faces whose cells are
+        // processed in the next one; a long run without progress is a bug
+        no_progress_checks = status[2] == last_remaining ? no_progress_checks + 1 : 0;
+        last_remaining = status[2];
+        if (no_progress_checks > 16 || step > max_steps) {
+            set_error("dag build did not finish after %lld steps", (long long)step);
+            rc = JSWEEP_ERR_CYCLE;
+            return true;
+        }
+        return false;
+    };
+    if (period.exec) {
+        // Pipelined checks: period k + 1 is queued before period k's status is
+        // read, so the device never waits for the host.  A period queued after
+        // the last one needed finds every frontier empty and does nothing.
+        struct HostStatus {
+            int32_t *p = nullptr;
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            ~HostStatus() {
+                if (p) cudaFreeHost(p);
+                for (auto e : ev)
+                    if (e) cudaEventDestroy(e);
+            }
+        } hs;
+        JS_CUDA(cudaMallocHost(&hs.p, 2 * 32));
+        for (auto &e : hs.ev) JS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        int64_t launched = 0, checked = 0;
+        auto launch_period = [&]() -> int {
+            const int sl = (int)(launched & 1);
             JS_CUDA(cudaGraphLaunch(period.exec, s));
             note_launches(period_launches);
-            step += check_every;
-        } else {
+            JS_CUDA(cudaMemcpyAsync(hs.p + 8 * sl, c.status, 32, cudaMemcpyDeviceToHost, s));
+            JS_CUDA(cudaEventRecord(hs.ev[sl], s));
+            ++launched;
+            return JSWEEP_OK;
+        };
+        JS_TRY(launch_period());
+        while (true) {
+            JS_TRY(launch_period());
+            const int sl = (int)(checked & 1);
+            JS_CUDA(cudaEventSynchronize(hs.ev[sl]));
+            ++checked;
+            step = checked * check_every;
+            std::memcpy(status, hs.p + 8 * sl, 32);
+            int rc = JSWEEP_OK;
+            if (check_status(rc)) {
+                JS_CUDA(cudaStreamSynchronize(s));  // the period queued ahead
+                if (rc != JSWEEP_OK) return rc;
+                break;
+            }
+        }
+    } else {
+        while (true) {
             note_launches(launch_step(s, step, prof));
             if (prof && pev.size() >= 500) {  // fold the events of a few steps into the totals
                 cudaStreamSynchronize(s);
@@ -1498,26 +1559,14 @@ int build_dags(Dags *d, cudaStream_t s) {
             }
             JS_CUDA(cudaGetLastError());
             ++step;
-        }
-        if (step % check_every == 0) {
-            JS_CUDA(cudaMemcpyAsync(status, c.status, 32, cudaMemcpyDeviceToHost, s));
-            JS_CUDA(cudaStreamSynchronize(s));
-            if (status[0] != 0) {
-                if (status[0] == JSWEEP_ERR_CYCLE)
-                    set_error("dependency cycle in direction %d could not be broken within the search "
-                              "cap of %d cells (raise jsweep_options.cycle_search_max)", status[1], B);
-                else
-                    set_error("dag build: internal list capacity exceeded (status %d)", status[0]);
-                return status[0];
-            }
-            if (status[2] == 0) break;
-            // every step either processes cells or lags faces whose cells are
-            // processed in the next one; a long run without progress is a bug
-            no_progress_checks = status[2] == last_remaining ? no_progress_checks + 1 : 0;
-            last_remaining = status[2];
-            if (no_progress_checks > 16 || step > max_steps) {
-                set_error("dag build did not finish after %lld steps", (long long)step);
-                return JSWEEP_ERR_CYCLE;
+            if (step % check_every == 0) {
+                JS_CUDA(cudaMemcpyAsync(status, c.status, 32, cudaMemcpyDeviceToHost, s));
+                JS_CUDA(cudaStreamSynchronize(s));
+                int rc = JSWEEP_OK;
+                if (check_status(rc)) {
+                    if (rc != JSWEEP_OK) return rc;
+                    break;
+                }
             }
         }
     }

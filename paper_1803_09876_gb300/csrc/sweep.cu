@@ -318,8 +318,11 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
                             const int64_t *wscan, const int64_t *base2, const int64_t *cnt2, const int32_t *off,
                             int64_t M, int64_t Lmax, int U, const int32_t *gmem, const int32_t *gstart,
                             const int32_t *gof, const int32_t *qpos, int interleave, int4 *units) {
+    // one warp per (direction, layer), lanes over its units
     const int64_t total = M * Lmax;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < total; i += warps) {
         int64_t m = i / Lmax, l = i - m * Lmax;
         if (l >= nlev[m]) continue;
         int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
@@ -328,7 +331,7 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
         int32_t wait = (int32_t)(wscan[i] - wscan[m * Lmax]);
         if (!interleave) {
             const int64_t b = base2[t * M + qpos[m]];
-            for (int64_t j = 0; j < nu; ++j) {
+            for (int64_t j = lane; j < nu; j += 32) {
                 int32_t s = p0 + (int32_t)(j * U);
                 units[b + j] = make_int4((int)m, s, min(U, p1 - s), wait);
             }
@@ -336,7 +339,7 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
         }
         const int g = gof[m];
         const int64_t gb = base2[t * M + gstart[g]];
-        for (int64_t j = 0; j < nu; ++j) {
+        for (int64_t j = lane; j < nu; j += 32) {
             int64_t pos = gb;
             for (int q = gstart[g]; q < gstart[g + 1]; ++q) {
                 const int64_t uq = cnt2[t * M + q];
@@ -354,13 +357,16 @@ __global__ void k_unit_fill(const int32_t *lp, const int64_t *lp_off, const int3
 // each waits for the units of m's layers before l.
 __global__ void k_unit_fill_dir(const int32_t *lp, const int64_t *lp_off, const int32_t *nlev, const int64_t *ucnt,
                                 const int64_t *wscan, int64_t M, int64_t Lmax, int U, int4 *units) {
+    // one warp per (direction, layer), lanes over its units
     const int64_t total = M * Lmax;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < total; i += warps) {
         const int64_t m = i / Lmax, l = i - m * Lmax;
         if (l >= nlev[m]) continue;
         const int32_t p0 = lp[lp_off[m] + l], p1 = lp[lp_off[m] + l + 1];
         const int32_t wait = (int32_t)(wscan[i] - wscan[m * Lmax]);
-        for (int64_t j = 0; j < ucnt[i]; ++j) {
+        for (int64_t j = lane; j < ucnt[i]; j += 32) {
             const int32_t s = p0 + (int32_t)(j * U);
             units[wscan[i] + j] = make_int4((int)m, s, min(U, p1 - s), wait);
         }
@@ -842,7 +848,7 @@ static int ensure_units_dir(Dags *d, int U, cudaStream_t s) {
     JS_TRY(ut.units.alloc(std::max<int64_t>(n_units, 1) * 16, s));
     JS_TRY(ut.dir_ptr.alloc((M + 1) * 8, s));
     JS_CUDA(cudaMemcpyAsync(ut.dir_ptr.p, dp.data(), (M + 1) * 8, cudaMemcpyHostToDevice, s));
-    k_unit_fill_dir<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
+    k_unit_fill_dir<<<grid_for(M * Lmax * 32, 256, 152 * 64), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
                                                                   nlev_d.as<int32_t>(), ucnt.as<int64_t>(),
                                                                   wscan.as<int64_t>(), M, Lmax, U,
                                                                   ut.units.as<int4>());
@@ -945,7 +951,7 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resid
     JS_CUDA(cudaStreamSynchronize(s));
     const int64_t n_units = last_base + last_cnt;
     JS_TRY(ut.units.alloc(std::max<int64_t>(n_units, 1) * 16, s));
-    k_unit_fill<<<grid_for(M * Lmax, 256, 4096), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
+    k_unit_fill<<<grid_for(M * Lmax * 32, 256, 152 * 64), 256, 0, s>>>(d->s_lp, lpoff_d.as<int64_t>(),
                                                               nlev_d.as<int32_t>(), ucnt.as<int64_t>(),
                                                               wscan.as<int64_t>(), base2.as<int64_t>(),
                                                               cnt2.as<int64_t>(), off_d.as<int32_t>(), M, Lmax, U,
