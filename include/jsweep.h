@@ -356,11 +356,14 @@ JSWEEP_API int jsweep_source_iterate_mg(jsweep_dags_t dags, int n_groups, int pr
  *
  *   jsweep_batch_create: precision and nrhs shared by the batch's problems;
  *     opt (may be NULL) sets cluster_cells, angles_per_warp, unit_order,
- *     priority, spin_timeout_s, debug_block_waits and no_face_stream of the
- *     batched launch.  A level-synchronous batch whose problems all have one
- *     face-slot count reads each handle's face-coefficient stream (built at the
- *     first step that needs it, kept with the handle and shared by every
- *     problem and sweep on it: N x M x 32..96 bytes); otherwise it reads the
+ *     priority, spin_timeout_s, debug_block_waits, no_face_stream and
+ *     no_sweep_order_psi of the batched launch.  A level-synchronous batch
+ *     whose problems all have one face-slot count reads each handle's
+ *     face-coefficient stream (built at the first step that needs it, kept with
+ *     the handle and shared by every problem and sweep on it: N x M x 32..96
+ *     bytes); with no_sweep_order_psi = 0 every problem also keeps a copy of its
+ *     psi in sweep order (allocated by jsweep_batch_add) and the stream holds
+ *     upwind positions, as in a single-problem sweep.  Otherwise it reads the
  *     cell geometry.  Results are bit-identical either way.
  *   jsweep_batch_problem_bytes: device bytes that jsweep_batch_add will
  *     allocate for a problem on this handle (its workspaces: psi, epoch flags,

@@ -12,9 +12,10 @@
 //   k_phi_resid_batch   phi = sum_m w_m psi_m and the FP64 residual accumulators
 //   k_advance           each problem's convergence test, iteration count, epoch
 //   k_deliver_batch     phi of the problems that finished into the callers' arrays
-// Each problem owns its workspaces (psi, epoch flags, source records, lagged
-// values, phi ping-pong), so problems that share a mesh and its graphs (one
-// handle) are independent.  The per-cell solve and the phi reduction are the
+// Each problem owns its workspaces (psi and, for level-synchronous batches, its
+// copy in sweep order, epoch flags, source records, lagged values, phi
+// ping-pong), so problems that share a mesh and its graphs (one handle) are
+// independent.  The per-cell solve and the phi reduction are the
 // device functions of the single-problem path, so a problem's results in a
 // batch are bit-identical to its results alone.
 //
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 
 // Level-synchronous batched sweep: one launch per merged schedule slot; the
 // units of a slot are independent, so no waits and no flags.
-template <class T, int R, int SPLIT, int MAXF, int A, bool COEF>
+template <class T, int R, int SPLIT, int MAXF, int A, bool COEF, bool SEQ>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_sweep_level_batch(const ProbArgs<T> *__restrict__ P, const ProbState *__restrict__ S, const int4 *units,
                         const int32_t *uprob, int64_t u0, int64_t nu) {
@@ -147,12 +148,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             JS_IN_RANGE(P[p].a, (int64_t)u.y + cell, P[p].a.N, 4)) {
             const ProbArgs<T> &pp = P[p];
             const int64_t idx = (int64_t)u.x * pp.a.N + u.y + cell;
-            solve_cell_coef<T, R, SPLIT, MAXF>(pp.a, u.x, ldg_hint(pp.a.order + idx, pol_stream),
-                                               ldg_hint(pp.a.mask + idx, pol_stream), sub,
-                                               pp.coef + idx * coef_record_bytes<T, MAXF>(), pol_stream, [] {
-                                                   pdl_wait_prev();  // upwind values come from earlier slots
-                                                   return true;
-                                               });
+            solve_cell_coef<T, R, SPLIT, MAXF, SEQ>(pp.a, u.x, ldg_hint(pp.a.order + idx, pol_stream),
+                                                    ldg_hint(pp.a.mask + idx, pol_stream), sub,
+                                                    pp.coef + idx * coef_record_bytes<T, MAXF>(), pol_stream,
+                                                    [] {
+                                                        pdl_wait_prev();  // upwind values come from earlier slots
+                                                        return true;
+                                                    },
+                                                    idx);
         }
     } else {
         const int4 u = units[u0 + t];
@@ -350,7 +353,7 @@ struct BatchProb {
     void *phi_out = nullptr;
     double tol = 0.0;
     int max_iters = 1;
-    DevBuf psi, srcv, inflow, psi_lag, phi0, phi1, flags;
+    DevBuf psi, psi_seq, srcv, inflow, psi_lag, phi0, phi1, flags;
     ProbState st{};
     ~BatchProb() { dags_release(d); }
 };
@@ -367,6 +370,7 @@ struct Batch {
     int64_t n_units = 0, ncells = 0, nlags = 0;
     int maxf = 4, apw = 1, mode = JSWEEP_MODE_LEVEL_SYNC;
     bool coef_all = false;  // every problem in the tables has its face stream (and one MAXF)
+    bool seq_all = false;   // ... with upwind positions, and its sweep-order copy of psi
     std::vector<int64_t> mslot;  // merged table: slot t is [mslot[t], mslot[t + 1])
     std::vector<int64_t> tab_units;  // units of each problem in the table (by position in act)
     // the captured iteration
@@ -403,11 +407,18 @@ template <class T, int R> constexpr int split_for() {
 
 int pad_rhs_b(int nrhs) { return nrhs <= 1 ? 1 : nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : 8; }
 
+// Level-synchronous batches with the face stream keep a sweep-order copy of
+// each problem's psi (as the single-problem path does).
+bool wants_psi_seq(const Batch *b) {
+    return b->opt.sweep_mode != JSWEEP_MODE_PERSISTENT && !b->opt.no_face_stream && !b->opt.no_sweep_order_psi;
+}
+
 int64_t problem_bytes(const Batch *b, const Dags *d, bool has_inflow) {
     const int64_t es = b->prec == JSWEEP_F64 ? 8 : 4, R = b->Rp, N = d->N, M = d->M;
     const int64_t RS = R >= 4 ? 2 * R : (R == 2 ? 4 : 2);
     int64_t bytes = M * N * R * es + M * N * 4 + N * RS * es + std::max<int64_t>(d->T, 1) * R * es +
                     2 * N * b->nrhs * es;
+    if (wants_psi_seq(b)) bytes += M * N * R * es;
     if (has_inflow) bytes += std::max<int64_t>(d->mesh->Fb, 1) * R * es;
     return bytes;
 }
@@ -452,7 +463,7 @@ template <class T> ProbArgs<T> prob_args(const Batch *b, BatchProb &p) {
     a.srcv = p.srcv.as<T>();
     a.inflow = p.has_inflow ? p.inflow.as<T>() : nullptr;
     a.psi = p.psi.as<T>();
-    a.psi_seq = nullptr;
+    a.psi_seq = p.psi_seq.p ? p.psi_seq.as<T>() : nullptr;  // used only by the sweep-order level kernel
     a.psi_lag = p.psi_lag.as<T>();
     a.lag_ptr = d->lag_ptr.as<int32_t>();
     a.lag_face = d->lag_face.as<int32_t>();
@@ -555,17 +566,28 @@ template <class T, int R> int build_tables(Batch *b, cudaStream_t s) {
     for (int k = 0; k < K; ++k) b->tab_units[k] = uoff[k + 1] - uoff[k];
     b->mode = b->opt.sweep_mode == JSWEEP_MODE_PERSISTENT ? JSWEEP_MODE_PERSISTENT : JSWEEP_MODE_LEVEL_SYNC;
     // level-synchronous batches read the handles' face streams when all have one
-    // built for the batch's face slot count (the records' layout depends on it)
-    b->coef_all = b->mode == JSWEEP_MODE_LEVEL_SYNC && !b->opt.no_face_stream;
+    // built for the batch's face slot count (the records' layout depends on it):
+    // the streams with upwind positions and the problems' sweep-order psi when
+    // every problem has both, else the streams with upwind cell ids
     const int mf = FS <= 4 ? 4 : FS <= 6 ? 6 : 7;
-    for (int k = 0; k < K && b->coef_all; ++k) {
-        Dags *d = b->probs[b->act[k]]->d;
-        const int dmf = d->mesh->FS <= 4 ? 4 : d->mesh->FS <= 6 ? 6 : 7;
-        P[k].coef = dmf == mf ? ensure_face_stream(d, b->prec, s) : nullptr;
-        b->coef_all = P[k].coef != nullptr;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool seq = pass == 0;
+        b->seq_all = seq;
+        b->coef_all = b->mode == JSWEEP_MODE_LEVEL_SYNC && !b->opt.no_face_stream;
+        for (int k = 0; k < K && b->coef_all; ++k) {
+            BatchProb &pr = *b->probs[b->act[k]];
+            Dags *d = pr.d;
+            const int dmf = d->mesh->FS <= 4 ? 4 : d->mesh->FS <= 6 ? 6 : 7;
+            P[k].coef = (dmf == mf && (!seq || pr.psi_seq.p)) ? ensure_face_stream(d, b->prec, s, seq) : nullptr;
+            b->coef_all = P[k].coef != nullptr;
+        }
+        if (b->coef_all) break;
     }
-    if (!b->coef_all)
-        for (int k = 0; k < K; ++k) P[k].coef = nullptr;
+    if (!b->coef_all) b->seq_all = false;
+    for (int k = 0; k < K; ++k) {
+        if (!b->coef_all) P[k].coef = nullptr;
+        if (!b->seq_all) P[k].a.psi_seq = nullptr;
+    }
     b->ncells = cpre[K];
     b->nlags = lpre[K];
     b->maxf = FS <= 4 ? 4 : FS <= 6 ? 6 : 7;
@@ -622,17 +644,18 @@ template <class T, int R, int SPLIT, int MAXF> void *dd_kernel_a(int A) {
     return dd_kernel<T, R, SPLIT, MAXF, 1>();
 }
 
-template <class T, int R, int SPLIT, int MAXF, int A> void *level_kernel(bool coef) {
-    return coef ? reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, true>)
-                : reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, false>);
+template <class T, int R, int SPLIT, int MAXF, int A> void *level_kernel(bool coef, bool seq) {
+    if (coef && seq) return reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, true, true>);
+    return coef ? reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, true, false>)
+                : reinterpret_cast<void *>(k_sweep_level_batch<T, R, SPLIT, MAXF, A, false, false>);
 }
 
-template <class T, int R, int SPLIT, int MAXF> void *level_kernel_a(int A, bool coef) {
+template <class T, int R, int SPLIT, int MAXF> void *level_kernel_a(int A, bool coef, bool seq) {
     if constexpr (SPLIT == 1) {
-        if (A == 2) return level_kernel<T, R, SPLIT, MAXF, 2>(coef);
-        if (A == 4) return level_kernel<T, R, SPLIT, MAXF, 4>(coef);
+        if (A == 2) return level_kernel<T, R, SPLIT, MAXF, 2>(coef, seq);
+        if (A == 4) return level_kernel<T, R, SPLIT, MAXF, 4>(coef, seq);
     }
-    return level_kernel<T, R, SPLIT, MAXF, 1>(coef);
+    return level_kernel<T, R, SPLIT, MAXF, 1>(coef, seq);
 }
 
 // Queue one batched iteration on stream cs (captured into the graph).
@@ -644,9 +667,9 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
     k_emission_batch<T, R><<<grid_for(b->ncells, 256, 152 * 16), 256, 0, cs>>>(P, S, b->cpre.as<int64_t>(), K,
                                                                                b->ncells);
     if (b->mode == JSWEEP_MODE_LEVEL_SYNC) {
-        void *lk = b->maxf == 4 ? level_kernel_a<T, R, SPLIT, 4>(b->apw, b->coef_all)
-                 : b->maxf == 6 ? level_kernel_a<T, R, SPLIT, 6>(b->apw, b->coef_all)
-                                : level_kernel_a<T, R, SPLIT, 7>(b->apw, b->coef_all);
+        void *lk = b->maxf == 4 ? level_kernel_a<T, R, SPLIT, 4>(b->apw, b->coef_all, b->seq_all)
+                 : b->maxf == 6 ? level_kernel_a<T, R, SPLIT, 6>(b->apw, b->coef_all, b->seq_all)
+                                : level_kernel_a<T, R, SPLIT, 7>(b->apw, b->coef_all, b->seq_all);
         const int4 *units = b->units.as<int4>();
         const int32_t *uprob = b->uprob.as<int32_t>();
         JS_CUDA(cudaEventRecordWithFlags(b->ev[0], cs, cudaEventRecordExternal));
@@ -929,6 +952,7 @@ JSWEEP_API int jsweep_batch_add(jsweep_batch_t batch, jsweep_dags_t dags, const 
     const int64_t N = d->N, M = d->M, R = b->Rp;
     const int64_t RS = R >= 4 ? 2 * R : (R == 2 ? 4 : 2);
     JS_TRY(p->psi.alloc((size_t)M * N * R * es, s));
+    if (js::wants_psi_seq(b)) JS_TRY(p->psi_seq.alloc((size_t)M * N * R * es, s));
     JS_TRY(p->flags.alloc((size_t)M * N * 4, s));
     JS_TRY(p->srcv.alloc((size_t)N * RS * es, s));
     JS_TRY(p->psi_lag.alloc((size_t)std::max<int64_t>(d->T, 1) * R * es, s));

@@ -235,7 +235,7 @@ int ensure_units(Dags *d, int mode, int max_cells, cudaStream_t s, int64_t resid
 int ensure_dirs64x4(Dags *d, DevBuf &buf, cudaStream_t s);  // FP64 directions as [M][4]
 // Face-coefficient stream of a handle (level-synchronous sweeps), built on
 // first use; nullptr when the option is off or its allocation was refused.
-const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s);
+const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s, bool positions = false);
 int run_sweep(Dags *d, int nrhs, int prec, const void *sigma_t, const void *ang_source,
               const void *inflow, void *phi_out, void *psi_out, cudaStream_t s);
 int run_source_iteration(Dags *d, int nrhs, int prec, const void *sigma_t, const void *c_ratio,

@@ -1432,8 +1432,10 @@ int one_sweep(Dags *d, int mode, bool has_inflow, const T *wts, T *phi_dst, int 
 
 // The handle's face-coefficient stream for precision prec, built from the
 // handle's own geometry and directions (the ones its sweeps and batches use),
-// or nullptr when switched off or refused.
-const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s) {
+// or nullptr when switched off or refused.  positions: the variant whose
+// interior neighbours are positions in the handle's sweep order (read with a
+// sweep-order copy of psi).
+const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s, bool positions) {
     if (prec == JSWEEP_F64) {
         if (ensure_dirs64x4(d, d->dirs4_64, s) != JSWEEP_OK) {
             clear_error();
@@ -1444,14 +1446,14 @@ const unsigned char *ensure_face_stream(Dags *d, int prec, cudaStream_t s) {
         a.GS = d->mesh->GS;
         a.geo = d->mesh->geo64.as<double4>();
         a.dirs = d->dirs4_64.as<double>();
-        return ensure_coef<double>(d, a, s);
+        return ensure_coef<double>(d, a, s, positions);
     }
     SweepArgs<float> a{};
     a.FS = d->mesh->FS;
     a.GS = d->mesh->GS;
     a.geo = d->mesh->geo32.as<float4>();
     a.dirs = reinterpret_cast<const float *>(d->quad->dirs32.p);
-    return ensure_coef<float>(d, a, s);
+    return ensure_coef<float>(d, a, s, positions);
 }
 
 // FP64 directions in [M][4] layout (the FP32 copy lives in the quadrature).

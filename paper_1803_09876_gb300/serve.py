@@ -396,13 +396,14 @@ class GpuBackend:
         return 104 * M * N + 256 * N + 64 * F + (64 << 20) + self.resident_extra_bytes(key)
 
     def request_bytes_estimate(self, key):
-        """Batch workspaces, inputs and output, and the request's share of the
+        """Batch workspaces (psi and its sweep-order copy, epoch flags, source
+        records, phi), inputs and output, and the request's share of the
         merged unit table (at most one 20-byte unit per 8 (direction, cell)
         pairs, plus the handle's own table)."""
         N, F, M, _, _ = self._shape(key)
         es = 8 if self.dtype == self.torch.float64 else 4
         R = self._rhs_padded()
-        return M * N * (R * es + 4 + 5) + N * (2 * R + 3 * self.nrhs + 4) * es + F * R * es + (1 << 20)
+        return M * N * (2 * R * es + 4 + 5) + N * (2 * R + 3 * self.nrhs + 4) * es + F * R * es + (1 << 20)
 
     def build_mesh(self, key):
         torch = self.torch
