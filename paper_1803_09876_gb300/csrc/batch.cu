@@ -130,14 +130,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // Level-synchronous batched sweep: one launch per merged schedule slot; the
 // units of a slot are independent, so no waits and no flags.
 template <class T, int R, int SPLIT, int MAXF, int A, bool COEF, bool SEQ>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kLevelWarps * 32)
     k_sweep_level_batch(const ProbArgs<T> *__restrict__ P, const ProbState *__restrict__ S, const int4 *units,
                         const int32_t *uprob, int64_t u0, int64_t nu) {
     pdl_launch_next();
     const int lane = threadIdx.x & 31;
     constexpr int LPU = 32 / A;
     const int a_ix = lane / LPU, ll = lane % LPU, cell = ll / SPLIT, sub = ll % SPLIT;
-    const int64_t t = ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * A + a_ix;
+    const int64_t t = ((int64_t)blockIdx.x * kLevelWarps + (threadIdx.x >> 5)) * A + a_ix;
     if (t >= nu) return;
     if constexpr (COEF) {
         // every problem has its face stream: sequential coefficient records
@@ -681,8 +681,8 @@ template <class T, int R> int queue_iteration(Batch *b, cudaStream_t cs) {
             void *args[] = {(void *)&P, (void *)&S, (void *)&units, (void *)&uprob, (void *)&u0, (void *)&nu};
             // programmatic dependent launch: the next slot starts while this one drains
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock));
-            cfg.blockDim = dim3(kWarpsPerBlock * 32);
+            cfg.gridDim = dim3((unsigned)((warps + kLevelWarps - 1) / kLevelWarps));
+            cfg.blockDim = dim3(kLevelWarps * 32);
             cfg.stream = cs;
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
