@@ -48,11 +48,11 @@ METRIC = "cell-angle updates/s"
 # processes).  The figure belongs to the kernel sources it was taken on (SHA-256 of the files
 # below, first 16 hex digits); when they differ the line reports no traffic.
 SWEEP_TRAFFIC = {
-    "sources_sha16": "67fe4bf5a0a62888",
-    "bytes_per_cell_dir": 167.6,
+    "sources_sha16": "e8f84ecc5b6630a0",
+    "bytes_per_cell_dir": 166.7,
     "capture": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none -k "
                 "regex:k_sweep_level_coef -s 101 -c 3 on bench.py --n 64 --sweeps 1 (the three largest slots): "
-                "230.6 MB over 1,376,323 cell-directions (95.4 B read + 72.2 B written per cell-direction), scaled "
+                "229.4 MB over 1,376,323 cell-directions (94.8 B read + 71.9 B written per cell-direction), scaled "
                 "to the 128^3 sweep; the smaller mesh keeps more of a slot in L2, so this is a lower bound"),
 }
 SWEEP_SOURCES = ("paper_1803_09876_gb300/csrc/sweep.cu", "paper_1803_09876_gb300/csrc/sweep_cell.cuh")
@@ -74,8 +74,8 @@ def parse(argv=None):
     p.add_argument("--mode", type=int, default=1, help="1 level-synchronous (CUDA graph), 2 data-driven persistent")
     p.add_argument("--priority", type=int, default=0)
     p.add_argument("--layering", type=int, default=1,
-                   help="1 longest-path levels (default: the octant-aligned layers of 0 cost more to build than "
-                        "the 22 sweeps of a step win back)")
+                   help="1 longest-path levels (default, every workload: the octant-aligned layers of 0 cost more "
+                        "to build than a step's sweeps win back)")
     p.add_argument("--cluster", type=int, default=32)
     p.add_argument("--no-face-stream", action="store_true",
                    help="level-synchronous sweeps read the cell geometry instead of the precomputed face stream")
@@ -872,7 +872,7 @@ def run_small(args):
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
     opt = J.jsweep_options_default(sweep_mode=args.mode, no_face_stream=int(args.no_face_stream),
-                                   tail_units=args.tail_units)
+                                   tail_units=args.tail_units, layering=args.layering)
     sig = torch.as_tensor(wl["sigma_t"], dtype=dtype, device="cuda")
     cr = torch.as_tensor(wl["c_ratio"], dtype=dtype, device="cuda")
     q = torch.as_tensor(wl["q"], dtype=dtype, device="cuda").contiguous()
@@ -946,7 +946,8 @@ def run_mg(args):
     M = len(dirs)
     mesh = J.mesh_from_dict(wl)
     quad = J.jsweep_quadrature_create(dirs, w)
-    opt = J.jsweep_options_default(sweep_mode=args.mode, no_face_stream=int(args.no_face_stream))
+    opt = J.jsweep_options_default(sweep_mode=args.mode, no_face_stream=int(args.no_face_stream),
+                                   layering=args.layering)
     dt = torch.float32
     sig = torch.as_tensor(sig_np, dtype=dt, device="cuda").contiguous()
     ss = torch.as_tensor(ss_np, dtype=dt, device="cuda").contiguous()

@@ -60,6 +60,21 @@ def test_small_meshes_bit_exact(kind, n, jit, seed, quad):
         assert n_lag > 0
 
 
+@pytest.mark.parametrize("n_dirs,seed", [(13, 1), (29, 2), (8, 3)])
+def test_uneven_octants_bit_exact(n_dirs, seed):
+    # the build groups each octant's directions into slots of 8 (padded when
+    # cheap): random direction sets leave octants empty, short and uneven,
+    # and a few axis-aligned directions sit on octant borders
+    rng = np.random.default_rng(seed)
+    dirs = rng.normal(size=(n_dirs, 3))
+    dirs[:2] = [[1.0, 0.0, 0.0], [0.0, -1.0, 0.0]]
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    w = np.full(n_dirs, 4 * np.pi / n_dirs)
+    for mesh in (hex_grid(6, 0.3, 5), kuhn_tets(4, 0.2, 6)):
+        compare_all(mesh, dirs, w)
+        compare_all(mesh, dirs, w, layering=1)
+
+
 def test_workload1_full_size_bit_exact():
     wl = make_workload(1)
     dirs, w = oracle.product_quadrature(*wl["spec"]["quad"])
