@@ -1508,14 +1508,17 @@ int build_dags(Dags *d, cudaStream_t s) {
         // read, so the device never waits for the host.  A period queued after
         // the last one needed finds every frontier empty and does nothing.
         struct HostStatus {
+            cudaStream_t s = nullptr;
             int32_t *p = nullptr;
             cudaEvent_t ev[2] = {nullptr, nullptr};
             ~HostStatus() {
+                if (s) cudaStreamSynchronize(s);  // a queued copy may still target p (early error return)
                 if (p) cudaFreeHost(p);
                 for (auto e : ev)
                     if (e) cudaEventDestroy(e);
             }
         } hs;
+        hs.s = s;
         JS_CUDA(cudaMallocHost(&hs.p, 2 * 32));
         for (auto &e : hs.ev) JS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         int64_t launched = 0, checked = 0;
