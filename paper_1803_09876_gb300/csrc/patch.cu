@@ -660,8 +660,9 @@ __device__ __forceinline__ int solve_cell_staged(const SweepArgs<T> &a, int m, i
         }
     }
     T out[RH];
+    const T inv = rcp_rn(den);  // the form every solve uses (sweep_cell.cuh)
 #pragma unroll
-    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
+    for (int r = 0; r < RH; ++r) out[r] = mul_rn(num[r], inv);
     store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
     return 0;
 }

@@ -213,6 +213,13 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+// psi = num / den as num * (1 / den), both correctly rounded: one reciprocal
+// serves every right-hand side of a cell (GB300's FP64 division is costly),
+// and every solve uses this same form, so all schedules give the same bits.
+__device__ __forceinline__ float rcp_rn(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_rn(double a) { return __drcp_rn(a); }
 
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -325,8 +332,9 @@ __device__ __forceinline__ bool solve_cell(const SweepArgs<T> &a, int m, int c, 
         }
     }
     T out[RH];
+    const T inv = rcp_rn(den);
 #pragma unroll
-    for (int r = 0; r < RH; ++r) out[r] = num[r] / den;
+    for (int r = 0; r < RH; ++r) out[r] = mul_rn(num[r], inv);
     store_cg<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out);
     return true;
 }
@@ -429,8 +437,9 @@ __device__ __forceinline__ bool solve_cell_coef(const SweepArgs<T> &a, int m, in
         }
     }
     T out[RH];
+    const T inv0 = rcp_rn(den[0]);
 #pragma unroll
-    for (int r = 0; r < RH; ++r) out[r] = num[r] / den[MG ? r : 0];
+    for (int r = 0; r < RH; ++r) out[r] = mul_rn(num[r], MG ? rcp_rn(den[r]) : inv0);
     if constexpr (SEQ) {
         store_cg<T, RH>(a.psi_seq + idx * R + sub * RH, out);
         store_hint<T, RH>(a.psi + ((int64_t)c * a.M + m) * R + sub * RH, out, pol_stream);
