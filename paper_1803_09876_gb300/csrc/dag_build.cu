@@ -231,6 +231,24 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) k_classify(BuildCtx c, co
     const int64_t g0 = blockIdx.x % G;
     for (int64_t gi = 0; gi < G; ++gi) {
         const int64_t grp = g0 + gi < G ? g0 + gi : g0 + gi - G;
+        if (live) {
+            // the frontier loop's other state starts here too (whole sectors):
+            // levels unset (-1), stamps, component claims and walk claims
+            const int64_t w0 = (grp * c.N + v) * 8;
+            uint4 *pl = reinterpret_cast<uint4 *>(c.lvl + w0);
+            uint4 *ps = reinterpret_cast<uint4 *>(c.stamp + w0);
+            uint4 *pcl = reinterpret_cast<uint4 *>(c.claim + w0);
+            uint4 *pw = reinterpret_cast<uint4 *>(c.wclaim + w0);
+            const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u), zero = make_uint4(0u, 0u, 0u, 0u);
+            pl[0] = ones;
+            pl[1] = ones;
+            ps[0] = zero;
+            ps[1] = zero;
+            pcl[0] = zero;
+            pcl[1] = zero;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pw[q] = zero;
+        }
         uint32_t wm[8], wc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -274,7 +292,8 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) k_classify(BuildCtx c, co
             wm[j] = in | (out << 8);  // uchar4 (in, out, 0, 0)
             wc[j] = (uint32_t)count;
             if (live) {
-                if (count != 0 && bin) c.stamp[state_ix(c, m)(v)] = 1;  // epoch 1 is the first stall's candidate list
+                // stamp (after the zeros above, same thread): epoch 1 is the first stall's candidate list
+                if (count != 0 && bin) c.stamp[(grp * c.N + v) * 8 + j] = 1;
                 const unsigned interior_in = in & (unsigned)(back >> (8 * (c.lam ? c.oct[m] : 0))) & 0xffu;
                 if (interior_in) sh_cyc[m] = 1;  // an active edge against the diagonal's levels
             }
@@ -1344,11 +1363,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.lagall = lagall.as<int4>();
     c.lag_cap = lag_cap;
 
-    JS_CUDA(cudaMemsetAsync(c.lvl, 0xff, SN * 4, s));
-    JS_CUDA(cudaMemsetAsync(c.stamp, 0, SN * 4, s));
-    JS_CUDA(cudaMemsetAsync(c.claim, 0, SN * 4, s));
-    JS_CUDA(cudaMemsetAsync(c.wclaim, 0, SN * 8, s));
-    JS_CUDA(cudaMemsetAsync(c.msk, 0, SN * 4, s));
+    // masks, counts, levels, stamps and claims: every word is written by k_classify
     JS_CUDA(cudaMemsetAsync(sm, 0, n_small * 4, s));
     {
         std::vector<int32_t> ones(M, 1);
