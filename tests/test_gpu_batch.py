@@ -93,8 +93,9 @@ def test_batch_equals_solo_bitwise(prec, mode):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_batch_of_one_cell_shape_reads_face_streams_bitwise(prec):
     # all problems on tetrahedra: the level-synchronous batch reads every
-    # handle's face-coefficient stream; with the stream off it reads the cell
-    # geometry; both give the single-problem bits
+    # handle's face-coefficient stream (with upwind positions and sweep-order
+    # psi by default, with cell ids when that copy is off); with the stream off
+    # it reads the cell geometry; all give the single-problem bits
     torch = _torch()
     dtype = torch.float64 if prec == "f64" else torch.float32
     tol = 1e-8 if prec == "f64" else 1e-6
@@ -109,8 +110,9 @@ def test_batch_of_one_cell_shape_reads_face_streams_bitwise(prec):
                          c=tensor(np.full(N, 0.5), dtype), q=tensor(rng.uniform(0.0, 1.0, (2, N)), dtype),
                          inflow=None, N=N))
     solo = [js.jsweep_source_iterate(d["g"], d["sig"], d["c"], d["q"], tol=tol, max_iters=500) for d in data]
-    for no_stream in (0, 1):
-        b = js.Batch(dtype, 2, js.jsweep_options_default(sweep_mode=1, no_face_stream=no_stream))
+    for no_stream, no_seq in ((0, 0), (0, 1), (1, 0)):
+        b = js.Batch(dtype, 2, js.jsweep_options_default(sweep_mode=1, no_face_stream=no_stream,
+                                                         no_sweep_order_psi=no_seq))
         ids = [b.add(d["g"], d["sig"], d["c"], d["q"], tol=tol, max_iters=500) for d in data]
         its, _ = b.source_iterate()
         for k, pid in enumerate(ids):
