@@ -1019,67 +1019,117 @@ __global__ void k_scan_apply(const int64_t *in, int64_t n, const int64_t *offs, 
 }
 
 // ---- stable LSD radix sort of equal-length segments (8-bit digits) -----------------
-constexpr int kRsTile = 1024;  // elements per tile; one warp per tile
-constexpr int kRsWarps = 4;    // tiles (warps) per block
+// A block sorts one tile of kRsTile keys per pass: each of its warps loads its
+// kRsWarpKeys keys into registers at once (all loads in flight together), the
+// tile's digit counts go to a [256][tiles] histogram, and after its scan each
+// warp ranks its keys in order (lanes with equal digits by __match_any_sync),
+// starting where the earlier tiles and the block's earlier warps end: the
+// order of equal digits is the order of the input (stable).
+constexpr int kRsWarps = 4;                       // warps per block
+constexpr int kRsWarpKeys = 1024;                 // keys per warp, 32 per lane
+constexpr int kRsTile = kRsWarps * kRsWarpKeys;   // keys per block tile
+constexpr int kRsPerLane = kRsWarpKeys / 32;
 __global__ void __launch_bounds__(kRsWarps * 32)
     k_rs_hist(const uint32_t *keys, int64_t seg_len, int shift, int32_t *hist, int64_t tiles) {
-    __shared__ int32_t hs[kRsWarps][256];
+    __shared__ int32_t hs[256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t s = blockIdx.y, t = (int64_t)blockIdx.x * kRsWarps + w;
-    int32_t *h = hs[w];
-    for (int b = lane; b < 256; b += 32) h[b] = 0;
-    __syncwarp();
-    if (t < tiles) {
-        for (int i = 0; i < kRsTile / 32; ++i) {
-            int64_t e = t * kRsTile + i * 32 + lane;
-            if (e < seg_len) atomicAdd(&h[(keys[s * seg_len + e] >> shift) & 255u], 1);
-        }
-        __syncwarp();
-        for (int b = lane; b < 256; b += 32) hist[(s * 256 + b) * tiles + t] = h[b];
-    }
+    const int64_t s = blockIdx.y, t = blockIdx.x;
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hs[b] = 0;
+    __syncthreads();
+    const int64_t e0 = t * kRsTile + (int64_t)w * kRsWarpKeys;  // first key of this warp in the segment
+    const int64_t rem = seg_len - e0;
+    uint32_t kr[kRsPerLane];
+#pragma unroll
+    for (int i = 0; i < kRsPerLane; ++i) kr[i] = i * 32 + lane < rem ? __ldg(keys + s * seg_len + e0 + i * 32 + lane) : 0u;
+#pragma unroll
+    for (int i = 0; i < kRsPerLane; ++i)
+        if (i * 32 + lane < rem) atomicAdd(&hs[(kr[i] >> shift) & 255u], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[(s * 256 + b) * tiles + t] = hs[b];
 }
 
-// In-place exclusive scan of each segment's [256][tiles] histogram (one block per segment).
+// In-place exclusive scan of each segment's [256][tiles] histogram (one block
+// per segment, four entries per thread and round; len is a multiple of 256).
 __global__ void k_rs_scan(int32_t *hist, int64_t len) {
-    int32_t *h = hist + blockIdx.x * len;
+    int4 *h = reinterpret_cast<int4 *>(hist + blockIdx.x * len);
+    const int64_t n4 = len / 4;
     __shared__ int64_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < len; base += blockDim.x) {
-        int64_t i = base + threadIdx.x;
-        int64_t v = i < len ? h[i] : 0;
+    for (int64_t base = 0; base < n4; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int4 v = i < n4 ? h[i] : make_int4(0, 0, 0, 0);
         int64_t tot;
-        int64_t ex = block_exclusive_scan(v, &tot);
-        if (i < len) h[i] = (int32_t)(carry + ex);
+        const int64_t ex = block_exclusive_scan((int64_t)v.x + v.y + v.z + v.w, &tot);
+        int64_t p = carry + ex;
+        if (i < n4) {
+            int4 o;
+            o.x = (int32_t)p;
+            p += v.x;
+            o.y = (int32_t)p;
+            p += v.y;
+            o.z = (int32_t)p;
+            p += v.z;
+            o.w = (int32_t)p;
+            h[i] = o;
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry += tot;
         __syncthreads();
     }
 }
 
+// VALS: values come from vals[]; otherwise a key's value is its index in the segment.
+template <bool VALS>
 __global__ void __launch_bounds__(kRsWarps * 32)
     k_rs_scatter(const uint32_t *keys, const int32_t *vals, int64_t seg_len, int shift, const int32_t *hist,
                  int64_t tiles, uint32_t *keys_out, int32_t *vals_out) {
-    __shared__ int32_t runs[kRsWarps][256];
+    __shared__ int32_t runs[kRsWarps][256];  // this warp's digit counts, then its next position per digit
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t s = blockIdx.y, t = (int64_t)blockIdx.x * kRsWarps + w;
-    if (t >= tiles) return;
+    const int64_t s = blockIdx.y, t = blockIdx.x;
     int32_t *run = runs[w];
-    for (int b = lane; b < 256; b += 32) run[b] = hist[(s * 256 + b) * tiles + t];
+    for (int b = lane; b < 256; b += 32) run[b] = 0;
+    const int64_t e0 = t * kRsTile + (int64_t)w * kRsWarpKeys;
+    const int64_t rem = seg_len - e0;
+    uint32_t kr[kRsPerLane];
+    int32_t vr[VALS ? kRsPerLane : 1];
+#pragma unroll
+    for (int i = 0; i < kRsPerLane; ++i) kr[i] = i * 32 + lane < rem ? __ldg(keys + s * seg_len + e0 + i * 32 + lane) : 0u;
+    if constexpr (VALS) {
+#pragma unroll
+        for (int i = 0; i < kRsPerLane; ++i) vr[i] = i * 32 + lane < rem ? __ldg(vals + s * seg_len + e0 + i * 32 + lane) : 0;
+    }
     __syncwarp();
-    for (int i = 0; i < kRsTile / 32; ++i) {
-        int64_t e = t * kRsTile + i * 32 + lane;
-        bool valid = e < seg_len;
-        uint32_t key = valid ? keys[s * seg_len + e] : 0u;
-        int32_t val = valid ? (vals ? vals[s * seg_len + e] : (int32_t)e) : 0;
-        unsigned d = valid ? ((key >> shift) & 255u) : (256u + lane);
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int rank = __popc(peers & lanemask_lt());
-        int pos = valid ? run[d] + rank : 0;
+#pragma unroll
+    for (int i = 0; i < kRsPerLane; ++i)
+        if (i * 32 + lane < rem) atomicAdd(&run[(kr[i] >> shift) & 255u], 1);
+    __syncthreads();
+    // a warp's run of digit b starts after the tile's earlier tiles and earlier warps
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+        int32_t p = hist[(s * 256 + b) * tiles + t];
+#pragma unroll
+        for (int w2 = 0; w2 < kRsWarps; ++w2) {
+            const int32_t c = runs[w2][b];
+            runs[w2][b] = p;
+            p += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRsPerLane; ++i) {
+        const bool valid = i * 32 + lane < rem;
+        const uint32_t key = kr[i];
+        const unsigned d = valid ? ((key >> shift) & 255u) : (256u + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lanemask_lt());
+        const int pos = valid ? run[d] + rank : 0;
         __syncwarp();
         if (valid && rank == 0) run[d] += __popc(peers);
         __syncwarp();
         if (valid) {
+            int32_t val;
+            if constexpr (VALS) val = vr[i];
+            else val = (int32_t)(e0 + i * 32 + lane);
             if (keys_out) keys_out[s * seg_len + pos] = key;
             vals_out[s * seg_len + pos] = val;
         }
@@ -1125,7 +1175,7 @@ int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len,
     }
     const uint32_t *kin = keys_in;
     const int32_t *vin = vals_in;
-    dim3 grid((unsigned)((tiles + kRsWarps - 1) / kRsWarps), (unsigned)n_seg);
+    dim3 grid((unsigned)tiles, (unsigned)n_seg);
     for (int p = 0; p < passes; ++p) {
         const bool last = p == passes - 1;
         uint32_t *ko = last ? keys_out : kb[p & 1].as<uint32_t>();
@@ -1134,7 +1184,10 @@ int radix_sort_segments(const uint32_t *keys_in, int64_t n_seg, int64_t seg_len,
         JS_LAUNCH_CHECK();
         k_rs_scan<<<(unsigned)n_seg, 1024, 0, s>>>(hist.as<int32_t>(), 256 * tiles);
         JS_LAUNCH_CHECK();
-        k_rs_scatter<<<grid, kRsWarps * 32, 0, s>>>(kin, vin, seg_len, 8 * p, hist.as<int32_t>(), tiles, ko, vo);
+        if (vin)
+            k_rs_scatter<true><<<grid, kRsWarps * 32, 0, s>>>(kin, vin, seg_len, 8 * p, hist.as<int32_t>(), tiles, ko, vo);
+        else
+            k_rs_scatter<false><<<grid, kRsWarps * 32, 0, s>>>(kin, vin, seg_len, 8 * p, hist.as<int32_t>(), tiles, ko, vo);
         JS_LAUNCH_CHECK();
         kin = ko;
         vin = vo;
