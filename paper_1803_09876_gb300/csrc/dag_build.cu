@@ -78,7 +78,8 @@ struct BuildCtx {
     const int32_t *sface, *nbr;
     const int4 *nbr8;  // [N][2]: neighbour ids padded to 8 slots
     const double *normal, *dirs;
-    int32_t *cnt, *lvl, *stamp, *claim;
+    int32_t *st;  // state words (st_count, st_level)
+    int32_t *stamp, *claim;
     uchar4 *msk;  // [M][N]: x = incoming-face bits, y = outgoing active-edge bits, z = lagged-face bits
                   // (one 4-byte record, so a cell's three masks cost one scattered access)
     int32_t *front;   // [2][M][N]
@@ -108,6 +109,16 @@ struct BuildCtx {
     const int32_t *sdir;   // [S]: direction of a slot, or -1 (padding)
     int64_t S;             // state slots (a multiple of 8)
 };
+
+// State word of a (direction, cell) in the frontier loop: bits 0-3 hold the
+// number of its active upwind faces not yet processed, bits 4-31 its level,
+// all ones (a negative word) until the cell is processed.  The count and the
+// level of a cell then share one sector with the other directions of its
+// group: the decrements by its upwind cells, its own level store and the
+// level reads by its downwind cells all touch that one sector.
+constexpr int32_t kStUnset = (int32_t)0xFFFFFFF0u;
+__device__ __forceinline__ int32_t st_count(int32_t w) { return w & 15; }
+__device__ __forceinline__ int32_t st_level(int32_t w) { return w < 0 ? -1 : w >> 4; }
 
 // Index of direction m's state of cell v: [slot / 8][N][8].
 struct StateIx {
@@ -233,15 +244,12 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) k_classify(BuildCtx c, co
         const int64_t grp = g0 + gi < G ? g0 + gi : g0 + gi - G;
         if (live) {
             // the frontier loop's other state starts here too (whole sectors):
-            // levels unset (-1), stamps, component claims and walk claims
+            // stamps, component claims and walk claims
             const int64_t w0 = (grp * c.N + v) * 8;
-            uint4 *pl = reinterpret_cast<uint4 *>(c.lvl + w0);
             uint4 *ps = reinterpret_cast<uint4 *>(c.stamp + w0);
             uint4 *pcl = reinterpret_cast<uint4 *>(c.claim + w0);
             uint4 *pw = reinterpret_cast<uint4 *>(c.wclaim + w0);
-            const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u), zero = make_uint4(0u, 0u, 0u, 0u);
-            pl[0] = ones;
-            pl[1] = ones;
+            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
             ps[0] = zero;
             ps[1] = zero;
             pcl[0] = zero;
@@ -320,11 +328,12 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) k_classify(BuildCtx c, co
         if (live) {
             const int64_t w0 = (grp * c.N + v) * 8;
             uint4 *pm = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(c.msk) + w0);
-            uint4 *pc4 = reinterpret_cast<uint4 *>(c.cnt + w0);
+            uint4 *pc4 = reinterpret_cast<uint4 *>(c.st + w0);  // level unset, count
+            const uint32_t u = (uint32_t)kStUnset;
             pm[0] = make_uint4(wm[0], wm[1], wm[2], wm[3]);
             pm[1] = make_uint4(wm[4], wm[5], wm[6], wm[7]);
-            pc4[0] = make_uint4(wc[0], wc[1], wc[2], wc[3]);
-            pc4[1] = make_uint4(wc[4], wc[5], wc[6], wc[7]);
+            pc4[0] = make_uint4(u | wc[0], u | wc[1], u | wc[2], u | wc[3]);
+            pc4[1] = make_uint4(u | wc[4], u | wc[5], u | wc[6], u | wc[7]);
         }
     }
     __syncthreads();
@@ -446,11 +455,11 @@ __global__ void __launch_bounds__(256, 5) k_peel(BuildCtx c, int cur) {
         // all upwind levels in flight together
         int lv[F];
 #pragma unroll
-        for (int k = 0; k < F; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] + 1 : 0;
+        for (int k = 0; k < F; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? st_level(c.st[g(nb[k])]) + 1 : 0;
         int lev = 0;
 #pragma unroll
         for (int k = 0; k < F; ++k) lev = max(lev, lv[k]);
-        c.lvl[g(v)] = lev;
+        c.st[g(v)] = lev << 4;  // count 0, level set
         // all downwind decrements in flight together
         int32_t old[F];
         // a decrement to zero makes the cell ready; any other one makes it a
@@ -461,7 +470,7 @@ __global__ void __launch_bounds__(256, 5) k_peel(BuildCtx c, int cur) {
 #pragma unroll
         for (int k = 0; k < F; ++k) {
             const bool o = ((ob >> k) & 1u) != 0;
-            old[k] = o ? atomicSub(&c.cnt[g(nb[k])], 1) : 0;
+            old[k] = o ? st_count(atomicSub(&c.st[g(nb[k])], 1)) : 0;
             sold[k] = (o && cyclic) ? atomicExch(&c.stamp[g(nb[k])], ep) : ep;
         }
         unsigned rmask = 0, cmask = 0;
@@ -519,11 +528,11 @@ __device__ int32_t claim_walk(const BuildCtx &c, StateIx g, int32_t v, uint32_t 
     const unsigned long long tag = ((unsigned long long)(uint32_t)ep << 32) | me;
     // most candidates are ready by the time of the search: their count alone
     // ends the walk
-    if (c.cnt[g(v)] <= 0) return -1;
+    if (st_count(c.st[g(v)]) == 0) return -1;
     int32_t x = v;
     for (int step = 0; step < walk_max; ++step) {
         unsigned long long *slot = c.wclaim + g(x);
-        const int32_t cx = step == 0 ? 1 : c.cnt[g(x)];
+        const int32_t cx = step == 0 ? 1 : st_count(c.st[g(x)]);
         unsigned long long old = *((volatile unsigned long long *)slot);
         const uchar4 mx = c.msk[g(x)];
         int32_t nb[F];
@@ -532,7 +541,7 @@ __device__ int32_t claim_walk(const BuildCtx &c, StateIx g, int32_t v, uint32_t 
         const unsigned act = (unsigned)mx.x & ~(unsigned)mx.z;
         int lv[F];
 #pragma unroll
-        for (int k = 0; k < F; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? c.lvl[g(nb[k])] : 0;
+        for (int k = 0; k < F; ++k) lv[k] = (((act >> k) & 1u) && nb[k] >= 0) ? st_level(c.st[g(nb[k])]) : 0;
         while (true) {
             if ((int32_t)(old >> 32) == ep) {
                 const uint32_t owner = (uint32_t)old;
@@ -653,7 +662,7 @@ __global__ void __launch_bounds__(kResolveWarps * 32, 2) k_resolve(BuildCtx c, i
                 for (int k = 0; k < kMaxFaces; ++k)
                     up[k] = (k < c.FS && ((act >> k) & 1u)) ? c.nbr[(int64_t)x * c.FS + k] : -1;
 #pragma unroll
-                for (int k = 0; k < kMaxFaces; ++k) lv[k] = up[k] >= 0 ? c.lvl[g(up[k])] : 0;
+                for (int k = 0; k < kMaxFaces; ++k) lv[k] = up[k] >= 0 ? st_level(c.st[g(up[k])]) : 0;
 #pragma unroll
                 for (int k = 0; k < kMaxFaces; ++k)
                     if (up[k] >= 0 && lv[k] < 0) upm |= 1u << k;
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(kResolveWarps * 32, 2) k_resolve(BuildCtx c, i
             // seeds were dropped: keep this round's candidates for the next stall
             for (int32_t i = 0; i < nc; ++i) {
                 int32_t v = cl[i];
-                if (c.lvl[g(v)] < 0 && atomicExch(&c.stamp[g(v)], ep + 1) != ep + 1) push(cn, ncn, v, c.N, c.status);
+                if (c.st[g(v)] < 0 && atomicExch(&c.stamp[g(v)], ep + 1) != ep + 1) push(cn, ncn, v, c.N, c.status);
             }
         }
         c.ncand[ci * c.M + m] = 0;
@@ -837,7 +846,7 @@ __global__ void k_commit(BuildCtx c, int nxt) {
         }
         c.msk[g(dn)].z |= (uint8_t)(1u << kd);
         c.msk[g(up)].y &= (uint8_t)~(1u << ku);
-        int32_t old = atomicSub(&c.cnt[g(dn)], 1);
+        const int32_t old = st_count(atomicSub(&c.st[g(dn)], 1));
         if (old == 1) push(c.front + (int64_t)nxt * c.M * c.N + base, c.nfront + nxt * c.M + m, dn, c.N, c.status);
         int32_t k = atomicAdd(c.nlag, 1);
         if (k < c.lag_cap) c.lagall[k] = e; else atomicCAS(&c.status[0], 0, JSWEEP_ERR_OOM);
@@ -845,7 +854,9 @@ __global__ void k_commit(BuildCtx c, int nxt) {
 }
 
 // State words [S / 8][N][8] back to [M][N] (sdir[s] = direction of slot s, or -1
-// for a padding slot): one thread reads a cell's 8 slots (32 bytes).
+// for a padding slot): one thread reads a cell's 8 slots (32 bytes).  LEVEL:
+// the words are frontier-loop state words and the level is stored.
+template <bool LEVEL>
 __global__ void k_ungroup(const uint32_t *src, const int32_t *sdir, int64_t N, int64_t S, uint32_t *dst) {
     const int64_t n = S / 8 * N;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -855,7 +866,7 @@ __global__ void k_ungroup(const uint32_t *src, const int32_t *sdir, int64_t N, i
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int32_t m = __ldg(sdir + gi * 8 + j);
-            if (m >= 0) dst[m * N + v] = w[j];
+            if (m >= 0) dst[m * N + v] = LEVEL ? (uint32_t)st_level((int32_t)w[j]) : w[j];
         }
     }
 }
@@ -1360,9 +1371,8 @@ int build_dags(Dags *d, cudaStream_t s) {
     std::vector<int32_t> oct = octant_of(d);
     std::vector<int32_t> dslot, sdir;
     const int64_t S = state_slots(oct, dslot, sdir), SN = S * N;
-    DevBuf lvl_g, cnt, stamp, claim, wclaim, msk_g, front, cand, small, pend, lagall, dslot_d, sdir_d;
-    JS_TRY(lvl_g.alloc(SN * 4, s));
-    JS_TRY(cnt.alloc(SN * 4, s));
+    DevBuf st_g, stamp, claim, wclaim, msk_g, front, cand, small, pend, lagall, dslot_d, sdir_d;
+    JS_TRY(st_g.alloc(SN * 4, s));
     JS_TRY(stamp.alloc(SN * 4, s));
     JS_TRY(claim.alloc(SN * 4, s));
     JS_TRY(wclaim.alloc(SN * 8, s));
@@ -1390,8 +1400,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.nbr8 = mesh->nbr8.as<int4>();
     c.normal = mesh->normal.as<double>();
     c.dirs = quad->dirs64.as<double>();
-    c.cnt = cnt.as<int32_t>();
-    c.lvl = lvl_g.as<int32_t>();
+    c.st = st_g.as<int32_t>();
     c.stamp = stamp.as<int32_t>();
     c.claim = claim.as<int32_t>();
     c.wclaim = wclaim.as<unsigned long long>();
@@ -1659,21 +1668,21 @@ int build_dags(Dags *d, cudaStream_t s) {
     DevBuf msk;
     JS_TRY(d->level.alloc(MN * 4, s));
     JS_TRY(msk.alloc(MN * 4, s));
-    k_ungroup<<<grid_for(SN / 8, 256, 152 * 16), 256, 0, s>>>(lvl_g.as<uint32_t>(), sdir_d.as<int32_t>(), N, S,
-                                                              d->level.as<uint32_t>());
+    k_ungroup<true><<<grid_for(SN / 8, 256, 152 * 16), 256, 0, s>>>(st_g.as<uint32_t>(), sdir_d.as<int32_t>(), N, S,
+                                                                    d->level.as<uint32_t>());
     JS_LAUNCH_CHECK();
-    k_ungroup<<<grid_for(SN / 8, 256, 152 * 16), 256, 0, s>>>(msk_g.as<uint32_t>(), sdir_d.as<int32_t>(), N, S,
-                                                              msk.as<uint32_t>());
+    k_ungroup<false><<<grid_for(SN / 8, 256, 152 * 16), 256, 0, s>>>(msk_g.as<uint32_t>(), sdir_d.as<int32_t>(), N,
+                                                                     S, msk.as<uint32_t>());
     JS_LAUNCH_CHECK();
-    c.lvl = d->level.as<int32_t>();
+    const int32_t *lvl = d->level.as<int32_t>();
     c.msk = msk.as<uchar4>();
     JS_CUDA(cudaStreamSynchronize(s));  // the allocator may hand the released memory to another stream
-    for (DevBuf *b : {&lvl_g, &msk_g, &cnt, &stamp, &claim, &wclaim, &front, &cand}) b->release();
+    for (DevBuf *b : {&st_g, &msk_g, &stamp, &claim, &wclaim, &front, &cand}) b->release();
     // ---- levels per direction
     DevBuf lmax;
     JS_TRY(lmax.alloc(M * 4, s));
     JS_CUDA(cudaMemsetAsync(lmax.p, 0xff, M * 4, s));
-    k_level_max<<<dim3(std::min<int64_t>(64, (N + 255) / 256), (unsigned)M), 256, 0, s>>>(c.lvl, N, M, lmax.as<int32_t>());
+    k_level_max<<<dim3(std::min<int64_t>(64, (N + 255) / 256), (unsigned)M), 256, 0, s>>>(lvl, N, M, lmax.as<int32_t>());
     JS_LAUNCH_CHECK();
     std::vector<int32_t> lm(M);
     JS_CUDA(cudaMemcpyAsync(lm.data(), lmax.p, M * 4, cudaMemcpyDeviceToHost, s));
@@ -1700,7 +1709,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     DevBuf skeys;
     JS_TRY(d->order.alloc(MN * 4, s));
     JS_TRY(skeys.alloc(MN * 4, s));
-    JS_TRY(radix_sort_segments(reinterpret_cast<const uint32_t *>(c.lvl), M, N, key_bits, nullptr,
+    JS_TRY(radix_sort_segments(reinterpret_cast<const uint32_t *>(lvl), M, N, key_bits, nullptr,
                                d->order.as<int32_t>(), skeys.as<uint32_t>(), s));
     DevBuf lpoff_d, nlev_d;
     JS_TRY(d->lp.alloc(d->lp_off[M] * 4, s));
