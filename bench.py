@@ -42,18 +42,20 @@ if ROOT not in sys.path:
 
 METRIC = "cell-angle updates/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell-direction of the
-# level-synchronous sweep kernel, from one ncu capture of three consecutive mid-sweep slot
-# launches on the 64^3 jittered hex with the benchmark's directions, right-hand sides and
-# options (a smaller case than the timed 128^3 one, scaled by the cell-directions a launch
-# processes).  The figure belongs to the kernel sources it was taken on (SHA-256 of the files
-# below, first 16 hex digits); when they differ the line reports no traffic.
+# level-synchronous sweep kernel on the 128^3 benchmark mesh with the benchmark's directions,
+# right-hand sides and options: one-pass ncu captures of three consecutive slot launches in each
+# of five slot-size classes, weighted by the share of the sweep's cell-directions in each class.
+# The figure belongs to the kernel sources it was taken on (SHA-256 of the files below, first 16
+# hex digits); when they differ the line reports no traffic.
 SWEEP_TRAFFIC = {
     "sources_sha16": "2b221597501659f5",
-    "bytes_per_cell_dir": 166.9,
+    "bytes_per_cell_dir": 286.4,
     "capture": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none -k "
-                "regex:k_sweep_level_coef -s 101 -c 3 on bench.py --n 64 --sweeps 1 (the three largest slots): "
-                "229.8 MB over 1,376,323 cell-directions (95.0 B read + 71.9 B written per cell-direction), scaled "
-                "to the 128^3 sweep; the smaller mesh keeps more of a slot in L2, so this is a lower bound"),
+                "regex:k_sweep_level_coef -s S -c 3 on bench.py --n 128 --sweeps 1, for S = 205, 285, 362, 665, "
+                "920 of 1,452 launches (slots of 1.78M, 1.19M, 0.75M, 0.35M, 0.10M cell-directions: 223.3, "
+                "272.1, 330.6, 347.9, 236.2 B per cell-direction), weighted by the cell-directions of the slots "
+                "of each size class (0.284, 0.181, 0.327, 0.147, 0.060): 220.4 B read + 66.0 B written per "
+                "cell-direction"),
 }
 SWEEP_SOURCES = ("paper_1803_09876_gb300/csrc/sweep.cu", "paper_1803_09876_gb300/csrc/sweep_cell.cuh")
 # source-iteration sweeps of one benchmark step (128^3, tol 1e-6): the count the GPU arm
@@ -380,12 +382,16 @@ def run_gpu(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     sha = sources_sha16()
     traffic, traffic_src = None, None
-    if (SWEEP_TRAFFIC and SWEEP_TRAFFIC["sources_sha16"] == sha and args.mode == 1
+    if (SWEEP_TRAFFIC and SWEEP_TRAFFIC["sources_sha16"] == sha and args.mode == 1 and args.n == 128
             and sweep_options(args) == sweep_options(parse([]))):
         traffic = SWEEP_TRAFFIC["bytes_per_cell_dir"] * N * M
         traffic_src = SWEEP_TRAFFIC["capture"]
+    # the DRAM traffic's own rate over the sweep kernels (what the memory system moves, against
+    # the model's bytes in `achieved`)
+    traffic_gbs = traffic / (sw_ms / 1e3) / 1e9 if traffic else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
+            "traffic_gbs": traffic_gbs, "traffic_frac": traffic_gbs / peak if traffic_gbs else None,
             "traffic_unit": "bytes per sweep (one launch sequence of the CUDA graph)",
             "traffic_source": traffic_src, "kernel_sources_sha16": sha,
             "kernel": (("sweep (level-synchronous CUDA graph, "
