@@ -4,8 +4,9 @@
 // reorder.
 //
 // Data layout: the frontier and candidate lists are per direction ([M][N]).
-// The per-(direction, cell) state of the frontier loop (masks, counts, levels,
-// stamps, claims) is [S / 8][N][8] over direction slots: the directions of an
+// The per-(direction, cell) state of the frontier loop (masks, state words
+// holding the count and the level, stamps, claims) is [S / 8][N][8] over
+// direction slots: the directions of an
 // octant get consecutive slots (each octant padded to a multiple of 8), so one
 // 32-byte sector holds a cell's state in 8 directions of one octant.  Those
 // directions peel nearly the same cells at nearly the same step, so their
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kClassifyThreads, 3) k_classify(BuildCtx c, co
     __syncthreads();
     // slot groups of 8 directions (block b starts at group b mod G, so that the
     // blocks' list counters are spread over the directions); the cell's masks
-    // and counts of a group are stored as two full 32-byte sectors each
+    // and state words of a group are stored as two full 32-byte sectors each
     const int64_t G = c.S / 8;
     const int64_t g0 = blockIdx.x % G;
     for (int64_t gi = 0; gi < G; ++gi) {
@@ -1425,7 +1426,7 @@ int build_dags(Dags *d, cudaStream_t s) {
     c.lagall = lagall.as<int4>();
     c.lag_cap = lag_cap;
 
-    // masks, counts, levels, stamps and claims: every word is written by k_classify
+    // masks, state words, stamps and claims: every word is written by k_classify
     JS_CUDA(cudaMemsetAsync(sm, 0, n_small * 4, s));
     {
         std::vector<int32_t> ones(M, 1);
