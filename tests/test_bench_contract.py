@@ -40,3 +40,16 @@ def test_multigroup_reference_line():
     assert d["config"]["workload"] == "tet48x6_128dirs_4groups_fp32_si_tol1e-6"
     assert d["cpu_baseline"]["kind"] == "oracle" and "4-group iteration" in d["cpu_baseline"]["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_recorded_sweep_traffic_belongs_to_the_committed_kernel():
+    """The DRAM traffic the benchmark line reports was captured on the slot
+    kernel's current sources (their hash is the key), and lies between the
+    model's algorithmic bytes and a few times them."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    t = bench.SWEEP_TRAFFIC
+    assert t["sources_sha16"] == bench.sources_sha16(), "kernel sources changed: recapture the traffic"
+    model = 2 * 8 * 4 + 5 + (128 + 2 * 8 * 4) / 288  # 128^3 hex, 288 directions, 8 rhs, FP32
+    assert model < t["bytes_per_cell_dir"] < 10 * model
