@@ -116,7 +116,9 @@ struct BuildCtx {
 // all ones (a negative word) until the cell is processed.  The count and the
 // level of a cell then share one sector with the other directions of its
 // group: the decrements by its upwind cells, its own level store and the
-// level reads by its downwind cells all touch that one sector.
+// level reads by its downwind cells all touch that one sector.  Levels fit
+// while below 2^27; a longest path that long passes through the levels 2^24
+// and above, which the build rejects after the loop ("too many levels").
 constexpr int32_t kStUnset = (int32_t)0xFFFFFFF0u;
 __device__ __forceinline__ int32_t st_count(int32_t w) { return w & 15; }
 __device__ __forceinline__ int32_t st_level(int32_t w) { return w < 0 ? -1 : w >> 4; }
