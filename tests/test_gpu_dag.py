@@ -89,6 +89,22 @@ def test_many_cycles_several_tiles_bit_exact():
     assert n_lag > 1000
 
 
+def test_deep_graphs_and_partial_sort_tiles_bit_exact():
+    # the level sort with two and three radix passes over segments that end in
+    # a partial tile (4,096 keys per tile), and a lag list longer than a tile:
+    # a long jittered slab (6,000 cells; 1,500-2,100 levels and ~9,000 lagged
+    # faces over 48 directions; components of at most 19 cells) and a
+    # 70,000-cell column (70,000 levels)
+    slab = hex_grid(jitter=0.2, seed=9, shape=(300, 5, 4))
+    dirs, w = oracle.product_quadrature(2, 3)
+    g, n_lag = compare_all(slab, dirs, w)
+    assert min(g.nlevels(m) for m in range(dirs.shape[0])) > 256 and n_lag > 4096
+    col = column_mesh(70000)
+    dirs = np.array([[1.0, 0.0, 0.0], [-0.6, 0.8, 0.0], [0.36, 0.48, 0.8]])
+    g, _ = compare_all(col, dirs, np.full(3, 4 * np.pi / 3))
+    assert all(g.nlevels(m) == 70000 for m in range(3))
+
+
 def test_unstructured_tets_bit_exact():
     mesh = kuhn_tets(12, 0.2, 2)
     dirs, w = oracle.product_quadrature(4, 4)
